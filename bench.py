@@ -1,0 +1,320 @@
+"""Throughput of the moist DG time step on GB300: DOF-stage updates per second.
+
+One bench "step" is one SSPRK(4,3) time step (four right-hand sides and
+stage updates: split, volume and face terms, sources, stage combination) of
+the 3-D warm-rain bubble on 64 x 64 x 32 hexahedra, Q4 (125 nodes/element,
+7 fields, 114,688,000 DOFs), float64.  value = DOFs x 4 stages x steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the plain float64 restatement of the
+paper) on a bounded sample of the same workload.  Under torchrun every rank
+runs an independent replica (the method needs no exchange between
+independent problems); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+# The reference arm and the cpu baseline time the oracle single-threaded:
+# pin the BLAS thread pools before numpy loads.
+if "reference" in sys.argv and os.environ.get("DG_ORACLE_THREADS") != "1":
+    os.execve(sys.executable, [sys.executable] + sys.argv,
+              dict(os.environ, DG_ORACLE_THREADS="1", OMP_NUM_THREADS="1",
+                   OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1"))
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "rain3d_q4"
+STAGES = 4
+METRIC = "DG DOF-stage updates/s (FP64 vs FP32-bulk) and % HBM roofline, 1 GB300"
+UNIT = "DOF-stage/s"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# algorithmic bytes per node and stage: read U_s, write U_{s+1}, read U^n on one
+# stage in four, write + read the derived T, rho_v, p' once: (2.25 n_f + 6) words
+def algorithmic_bytes_per_node(n_fields, word):
+    return (2.25 * n_fields + 6.0) * word
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / cpu baseline: the oracle on a bounded sample
+# ---------------------------------------------------------------------------
+SAMPLE_COLUMNS = (4, 4)     # sample: a 4 x 4 block of full element columns
+
+
+class OracleSample:
+    """Oracle RHS + stage update on a 4 x 4 x 32 column block of the workload."""
+
+    def __init__(self):
+        from oracle import dg, initial
+        from oracle.mesh import Mesh
+        from paper_2305_13847_gb300 import inputs
+        self.dg = dg
+        w = inputs.workload(WORKLOAD)
+        mesh = Mesh(w["dim"], w["n"], w["L"], w["order"], w["periodic"])
+        node, face, _ = initial.base_tables(mesh, H=w["H"])
+        self.prob = dg.Problem(mesh, node, face, rain=w["rain"])
+        nx, ny = SAMPLE_COLUMNS
+        ix0, iy0 = mesh.n[0] // 2 - nx // 2, mesh.n[1] // 2 - ny // 2
+        sel = [mesh.elem_index([np.array(ix), np.array(iy), np.array(iz)])
+               for iz in range(mesh.n[2]) for iy in range(iy0, iy0 + ny) for ix in range(ix0, ix0 + nx)]
+        self.sel = np.array(sel, dtype=np.int64).ravel()
+        noise = inputs.node_noise(w, mesh.Ne, mesh.Np)
+        self.U = initial.bubble_state(self.prob, w["A"], w["centre"], w["radius"], noise=noise, H=w["H"])
+        self.dofs = self.sel.size * mesh.Np * self.prob.nf
+        self.desc = ("oracle float64 RHS + stage update on a %dx%dx%d column block (%d elements, "
+                     "%d DOFs) of the 64x64x32 Q4 mesh" % (nx, ny, mesh.n[2], self.sel.size, self.dofs))
+
+    def run(self, repeats, dt=0.01):
+        """repeats x (RHS + stage update) on the block; returns seconds."""
+        t0 = time.perf_counter()
+        for _ in range(repeats):
+            R = self.dg.rhs(self.prob, self.U, elements=self.sel)
+            self.U[:, self.sel] = self.U[:, self.sel] + dt * R
+        return time.perf_counter() - t0
+
+
+def oracle_sample_rate(repeats):
+    s = OracleSample()
+    sec = s.run(repeats)
+    return s.dofs * repeats / sec, sec, s.desc + ", %d repeats" % repeats
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = OracleSample()
+    sample.run(args.warmup)
+    secs = [sample.run(STAGES) for _ in range(args.steps)]      # one step = four stages
+    rates = [sample.dofs * STAGES / s for s in secs]
+    value = float(np.median(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * float(np.median(secs)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "rain3d_q4: 3-D warm-rain bubble, 64x64x32 hex, Q4, 7 fields",
+                   "sample": sample.desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample.desc + ", 4 stages per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def cpu_baseline_subprocess(timeout=600):
+    """The oracle as it stands, single-threaded, in a child process."""
+    code = ("import json,sys; sys.path.insert(0,%r); import bench; "
+            "r,s,d = bench.oracle_sample_rate(60); print(json.dumps([r,s,d]))" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           timeout=timeout, env=env, cwd=ROOT)
+        rate, sec, desc = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": desc + " (%.1f s)" % sec}
+    except Exception as e:  # reported, not hidden
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "oracle run failed: %s" % (str(e)[:200])}
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+def run_gb300(args):
+    import torch
+    from paper_2305_13847_gb300 import dgmoist as dm
+    from paper_2305_13847_gb300 import inputs, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    w = inputs.workload(WORKLOAD)
+    ctx = workloads.open_workload(w, stream=stream, precision=args.precision)
+    info = dm.dg_get_info(ctx)
+    red = dm.dg_reduce(ctx)
+    dt = w["cfl"] * min(L / n for L, n in zip(w["L"], w["n"])) / red[5]
+    word = 4 if args.precision == "fp32_bulk" else 8
+
+    # warm-up (also the first split + traces of the initial state)
+    dm.dg_step(ctx, dt, args.warmup)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    barrier()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        dm.dg_step_async(ctx, dt, 1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    st, counts = dm.dg_check_status(ctx)
+    if st != dm.DG_OK:
+        raise RuntimeError("step failed: %s %s" % (dm.dg_strerror(st), counts.tolist()))
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t_local = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    t_max = float(t_local.item()) / 1000.0
+    units = world * info.n_dofs * STAGES * args.steps
+    value = units / t_max
+
+    # end to end through the C interface with host buffers: upload the state
+    # from pinned memory, one step, download the state, every step
+    host = torch.empty(info.state_bytes // word, dtype=torch.float64 if word == 8 else torch.float32,
+                       pin_memory=True)
+    dm.dg_get_state(ctx, host, dm.DG_HOST)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dm.dg_set_state(ctx, host, dm.DG_HOST)
+        dm.dg_step(ctx, dt, 1)
+        dm.dg_get_state(ctx, host, dm.DG_HOST)
+    torch.cuda.synchronize()
+    e2e_local = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
+    e2e_value = world * info.n_dofs * STAGES * e2e_steps / float(e2e_local.item())
+
+    # roofline of the dominant kernel (the fused stage kernel: four launches per step)
+    peak, peak_kind = measured_peaks()
+    launch_s = (total_ms / 1000.0) / (STAGES * args.steps)
+    bytes_per_launch = algorithmic_bytes_per_node(info.n_fields, word) * info.n_nodes
+    achieved = bytes_per_launch / launch_s / 1e9
+    dm.dg_free(ctx)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if word == 4 else "f64", "data": "synthetic",
+            "config": {"workload": "rain3d_q4: 3-D warm-rain bubble, 64x64x32 hex, Q4 (125 nodes/elem), "
+                                   "7 fields, %d DOFs, dt %.4g s" % (info.n_dofs, dt),
+                       "precision": args.precision, "l2": "inputs larger than L2 (state %.0f MB)"
+                       % (info.state_bytes / 1e6), "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "step_ms": {"median": float(np.median(step_ms)), "min": float(np.min(step_ms)),
+                        "max": float(np.max(step_ms))},
+            "roofline": {"bound": "hbm", "kernel": "k_stage (fused RHS + SSPRK stage + next split)",
+                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(info.state_bytes),
+                    "d2h_bytes_per_step": int(info.state_bytes), "steps": e2e_steps},
+            "gpu_launches": STAGES * args.steps,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_subprocess()
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

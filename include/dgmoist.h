@@ -1,0 +1,210 @@
+/*
+ * dgmoist.h -- C interface of the GB300 library for the moist compressible
+ * Euler discontinuous Galerkin method with implicit condensation
+ * (Hittmeir, Lederer, Schoeberl, von Wahl, arXiv 2305.13847).
+ *
+ * What the library computes (the hot path of the method):
+ *   - the pointwise implicit-condensation split, Eq. (2.8) solved by Newton's
+ *     method at every node (Section 3.4);
+ *   - the explicit DG right-hand side of Eq. (3.2)/(3.3): volume integrals of
+ *     the flux of Eq. (2.11), Lax-Friedrichs face fluxes with the wave-speed
+ *     bound Eq. (3.4) and slip-wall / periodic boundaries (Section 3.2), the
+ *     warm-rain sources Eq. (2.4) and gravity, times the diagonal inverse mass
+ *     matrix (Section 3.3);
+ *   - the four-stage third-order SSP Runge-Kutta update (Remark 3.1).
+ *
+ * Discretisation conventions (fixed by this interface):
+ *   - Structured Cartesian mesh of n[0] x n[1] (x n[2]) quadrilaterals /
+ *     hexahedra on [0,L0] x [0,L1] (x [0,L2]).  The vertical direction is the
+ *     last one (y in 2-D, z in 3-D); it always has slip walls at the bottom
+ *     and top, the other directions are periodic or walls by periodic_mask.
+ *   - Q^k space, k = order in 1..5, nodal basis at the (k+1) Gauss-Legendre
+ *     points per direction; integrals by the same Gauss rule (collocation),
+ *     so the mass matrix is exactly diagonal.
+ *   - Unknowns U = (rho_d', rho_m', [rho_r'], m_0..m_{d-1}, E'), n_f = 3+d
+ *     fields without rain and 4+d with rain: perturbations of the dry and
+ *     moist (vapour + cloud) densities, rain density, momentum, perturbation
+ *     of the total energy (Section 2.3, Eq. (2.11)).
+ *   - "ABI layout" of a state: U[f][e][a], f the field, e = i0 + n0 (i1 + n1 i2)
+ *     the element, a = a0 + (k+1)(a1 + (k+1) a2) the node (first index
+ *     fastest).  Element storage type: double for DG_FP64, float for
+ *     DG_FP32_BULK.
+ *   - Base (hydrostatic) state tables, Section 2.3: rho_d, rho_m, E, p at the
+ *     node z-levels (index i_vert (k+1) + a_vert, n_vert (k+1) levels) and at
+ *     the face z-levels (index i_vert, n_vert + 1 levels), as float64.
+ *
+ * Memory and ownership:
+ *   - A context owns its device state, scratch buffers and stream binding.
+ *     Pointers passed in are never freed or kept after the call returns.
+ *   - "Device" pointers must point to memory on the context's current CUDA
+ *     device; "host" pointers are ordinary host memory (pinned or pageable).
+ *   - Work is enqueued on the CUDA stream given to dg_init_mesh (NULL = the
+ *     legacy default stream).  Calls documented as synchronising wait for that
+ *     stream before returning.
+ *
+ * Errors: every int-returning call returns DG_OK (0) or a negative code;
+ * dg_strerror() describes it.  No call aborts or traps the device: the
+ * kernels count Newton failures and non-physical states in device counters
+ * that the synchronising calls turn into DG_ENOCONV / DG_ENONPHYS.
+ */
+#ifndef DGMOIST_H
+#define DGMOIST_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_EINVAL (-1)   /* bad argument or size */
+#define DG_ENOMEM (-2)   /* device allocation failed */
+#define DG_ECUDA (-3)    /* a CUDA call failed */
+#define DG_ENOCONV (-4)  /* Newton split hit its iteration cap somewhere */
+#define DG_ENONPHYS (-5) /* non-physical or non-finite state (T, rho <= 0, NaN) */
+#define DG_ESTATE (-6)   /* call order: base state or state not set yet */
+#define DG_ENOTIMPL (-7) /* not available in this build */
+
+#define DG_FP64 0
+#define DG_FP32_BULK 1
+
+#define DG_HOST 0
+#define DG_DEVICE 1
+
+/* Number of values written by dg_reduce. */
+#define DG_NREDUCE 8
+
+typedef struct dg_ctx dg_ctx;
+
+typedef struct dg_config {
+    int dim;            /* 2 or 3 */
+    int n[3];           /* elements per direction (n[2] unused for dim 2), each >= 1 */
+    int order;          /* polynomial degree k, 1..5 */
+    double L[3];        /* domain lengths in m (L[2] unused for dim 2) */
+    int periodic_mask;  /* bit j set: direction j periodic; the vertical is always walls */
+    int rain;           /* 0: no rain (3+d fields); 1: warm rain (4+d fields) */
+    int precision;      /* DG_FP64, or DG_FP32_BULK: float state and flux arithmetic,
+                           float64 split / temperature recovery / reductions */
+    double g;           /* gravity in m/s^2 (the paper does not print it; 9.81 usual) */
+    double rho_w;       /* water density in the rain speed: <= 0 takes the paper's
+                           rho_w = rho_v + rho_c + rho_r; > 0 a constant (kg/m^3) */
+} dg_config;
+
+typedef struct dg_info {
+    int n_fields;               /* n_f */
+    int nodes_per_elem;         /* (k+1)^d */
+    int face_points_per_face;   /* (k+1)^(d-1) */
+    int n_zlev_node;            /* n_vert (k+1) */
+    int n_zlev_face;            /* n_vert + 1 */
+    int elems_per_block;        /* elements handled by one CTA of the stage kernel */
+    long long n_elem;
+    long long n_nodes;          /* n_elem * nodes_per_elem */
+    long long n_dofs;           /* n_nodes * n_fields (the paper's DOF count) */
+    size_t state_bytes;         /* bytes of one state in ABI layout */
+    size_t device_bytes;        /* device memory held by the context */
+} dg_info;
+
+/* Warm-bubble workload: hydrostatic column of constant dry potential
+ * temperature theta, surface pressure p_s, total-water mixing ratio
+ * qt0 (1 - z/H), and a cos^2 potential-temperature bubble of the given
+ * amplitude, centre and radii applied at fixed pressure and mixing ratio. */
+typedef struct dg_bubble {
+    double theta, p_s, qt0, H;
+    double amplitude;
+    double centre[3];
+    double radius[3];
+} dg_bubble;
+
+/* Create a context for the mesh of cfg on the current CUDA device; work goes
+ * to cuda_stream (a cudaStream_t, NULL for the default stream).  Allocates the
+ * device state (two copies), derived fields and face-trace buffers.
+ * Errors: DG_EINVAL for out-of-range fields or a mesh whose
+ * n_nodes * n_fields exceeds 2^31 - 1; DG_ENOMEM; DG_ECUDA. */
+int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream);
+
+/* Release everything owned by ctx (NULL is ignored). */
+void dg_free(dg_ctx *ctx);
+
+/* Sizes of the context's mesh and buffers. */
+int dg_get_info(const dg_ctx *ctx, dg_info *info);
+
+/* The library's Gauss-Legendre rule: n points in (-1, 1), ascending, and
+ * weights, written to host arrays x[n], w[n]; n in 1..6.  Host only. */
+int dg_gauss_legendre(int n, double *x, double *w);
+
+/* Node and face z-levels of ctx's mesh in m, host arrays of
+ * n_zlev_node and n_zlev_face entries. */
+int dg_zlevels(const dg_ctx *ctx, double *z_node, double *z_face);
+
+/* Set the hydrostatic base state (Section 2.3, Eq. (2.9)-(2.10)) from host
+ * tables node_tab[4][n_zlev_node] and face_tab[4][n_zlev_face], rows
+ * rho_d, rho_m, E, p (float64).  Copied; marks the derived fields stale. */
+int dg_set_base_state(dg_ctx *ctx, const double *node_tab, const double *face_tab);
+
+/* Build the warm-bubble workload in the context: base state tables
+ * (hydrostatic column integrated with classical RK4, steps <= 1 m, on the
+ * host) and the initial unknowns on the device (u = 0, rho_r' = 0).
+ * noise: optional per-node temperature change in K, ABI node order
+ * [e][a], float64, on host (where = DG_HOST) or device (DG_DEVICE); NULL for
+ * none.  Errors: DG_EINVAL. */
+int dg_init_bubble(dg_ctx *ctx, const dg_bubble *spec, const double *noise, int where);
+
+/* Copy a state (ABI layout, the context's storage type) into / out of the
+ * context.  where = DG_HOST or DG_DEVICE.  dg_set_state makes the derived
+ * fields stale; dg_get_state with DG_HOST synchronises. */
+int dg_set_state(dg_ctx *ctx, const void *U, int where);
+int dg_get_state(dg_ctx *ctx, void *U, int where);
+
+/* Implicit-condensation split, Eq. (2.8), at every node of the state U
+ * (device, ABI layout, storage type): writes float64 device arrays of
+ * n_nodes values in [e][a] order -- T (K), rho_v, rho_c (kg/m^3) and
+ * p_prime = (rho_d R_d + rho_v R_v) T - p_bar (Pa); any output may be NULL.
+ * If n_unconverged is not NULL the call synchronises and stores the number
+ * of nodes whose Newton iteration hit its cap.  Errors: DG_ESTATE without a
+ * base state; DG_ENONPHYS if a non-physical node was found (synchronising
+ * form only). */
+int dg_saturation_split(dg_ctx *ctx, const void *U, double *T, double *rho_v,
+                        double *rho_c, double *p_prime, long long *n_unconverged);
+
+/* Semi-discrete right-hand side dU/dt = M^{-1}(-F(U) + G(U)), Eq. (3.5)-(3.6),
+ * of the state U (device, ABI layout) into dUdt (device, ABI layout, the
+ * storage type).  U and dUdt must not overlap.  Asynchronous. */
+int dg_rhs(dg_ctx *ctx, const void *U, void *dUdt);
+
+/* Advance the context's state by nsteps SSPRK(4,3) steps of size dt (s).
+ * Synchronises at the end and returns DG_ENOCONV / DG_ENONPHYS if any node
+ * failed during the call (the state is still advanced). */
+int dg_step(dg_ctx *ctx, double dt, int nsteps);
+
+/* Same as dg_step but enqueues only: no synchronisation and no status
+ * check (read it later with dg_check_status). */
+int dg_step_async(dg_ctx *ctx, double dt, int nsteps);
+
+/* Synchronise the stream and report (and clear) the failure counters
+ * accumulated since the last check: DG_OK, DG_ENOCONV or DG_ENONPHYS.
+ * counts (may be NULL) receives {n_unconverged, n_nonphysical}. */
+int dg_check_status(dg_ctx *ctx, long long counts[2]);
+
+/* Diagnostics of the context's state (synchronising), float64:
+ *   out[0] integral of rho_d'            (dry-air mass perturbation)
+ *   out[1] integral of rho_m' + rho_r'   (water mass perturbation)
+ *   out[2] integral of m_0               (x-momentum)
+ *   out[3] integral of rho_c             (cloud water)
+ *   out[4] integral of rho_r'            (rain water; 0 without rain)
+ *   out[5] max over nodes of |u| + v_r + c_m (for a CFL time step)
+ *   out[6] max over nodes of (rho_v - rho_vs(T)) / rho_vs(T) (supersaturation)
+ *   out[7] integral of E'
+ * Integrals use the Gauss rule of the DG space (the diagonal mass matrix). */
+int dg_reduce(dg_ctx *ctx, double out[DG_NREDUCE]);
+
+/* Adjoint of one dg_step (not in this build: returns DG_ENOTIMPL). */
+int dg_adjoint_step(dg_ctx *ctx, double dt, const void *U_n, const double *lam_np1,
+                    double *lam_n);
+
+/* Text for a status code. */
+const char *dg_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGMOIST_H */

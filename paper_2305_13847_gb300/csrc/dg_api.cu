@@ -1,0 +1,713 @@
+// C interface of the moist DG library (declared in include/dgmoist.h).
+//
+// Host side: validation, reference-element tables, buffers, the stage
+// schedule of SSPRK(4,3) and the hydrostatic column of the warm-bubble
+// workload.  Every step of the right-hand side and of the time step runs in
+// the CUDA kernels of dg_device.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "dg_launch.cuh"
+#include "dgmoist.h"
+
+using namespace dgm;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = (cudaSetDevice(dev) == cudaSuccess);
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// ---- reference element -----------------------------------------------------
+// Gauss-Legendre points: roots of P_n by Newton's method (three-term
+// recurrence for P_n and its derivative), weights 2 / ((1 - x^2) P_n'(x)^2).
+void legendre_pd(int n, double x, double &p, double &dp) {
+    double p0 = 1.0, p1 = x;
+    if (n == 0) {
+        p = 1.0;
+        dp = 0.0;
+        return;
+    }
+    for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    p = p1;
+    dp = n * (p0 - x * p1) / (1.0 - x * x);
+}
+
+void gauss_rule(int n, double *x, double *w) {
+    for (int i = 0; i < n; ++i) {
+        double t = -std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p, dp;
+            legendre_pd(n, t, p, dp);
+            const double dt = p / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        double p, dp;
+        legendre_pd(n, t, p, dp);
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+// Lagrange basis through x[0..n): value at s; derivative matrix by the
+// barycentric formula D[i][a] = l_a'(x_i).
+double lagrange_at(const double *x, int n, int a, double s) {
+    double v = 1.0;
+    for (int m = 0; m < n; ++m)
+        if (m != a) v *= (s - x[m]) / (x[a] - x[m]);
+    return v;
+}
+
+void derivative_matrix(const double *x, int n, double D[6][6]) {
+    double bw[6];
+    for (int a = 0; a < n; ++a) {
+        double prod = 1.0;
+        for (int m = 0; m < n; ++m)
+            if (m != a) prod *= (x[a] - x[m]);
+        bw[a] = 1.0 / prod;
+    }
+    for (int i = 0; i < n; ++i) {
+        double diag = 0.0;
+        for (int a = 0; a < n; ++a) {
+            if (a == i) continue;
+            D[i][a] = (bw[a] / bw[i]) / (x[i] - x[a]);
+            diag -= D[i][a];
+        }
+        D[i][i] = diag;
+    }
+}
+
+template <typename Real>
+RefData<Real> make_ref(int order) {
+    const int n = order + 1;
+    double x[6], w[6], D[6][6];
+    gauss_rule(n, x, w);
+    derivative_matrix(x, n, D);
+    RefData<Real> r;
+    std::memset(&r, 0, sizeof(r));
+    for (int a = 0; a < n; ++a) {
+        const double lm = lagrange_at(x, n, a, -1.0), lp = lagrange_at(x, n, a, 1.0);
+        r.lm[a] = (Real)lm;
+        r.lp[a] = (Real)lp;
+        r.liftm[a] = (Real)(lm / w[a]);
+        r.liftp[a] = (Real)(lp / w[a]);
+        r.xi[a] = (Real)x[a];
+        r.w[a] = (Real)w[a];
+        for (int i = 0; i < n; ++i) r.dhat[a][i] = (Real)(w[i] / w[a] * D[i][a]);
+    }
+    return r;
+}
+
+// ---- hydrostatic column of the warm-bubble workload ------------------------
+struct ColumnState {
+    double rho_d, rho_v, rho_m, T, E, p;
+};
+
+double rho_vs_host(double T) {
+    const double es = kEref * std::pow(T / kTref, kEsA) * std::exp(kEsB * (1.0 / kTref - 1.0 / T));
+    return es / (kRv * T);
+}
+
+// p = (rho_d R_d + rho_v R_v) T, rho_v = min(rho_vs(T), qt rho_d): closed form per branch
+ColumnState moist_at(double p, double T, double qt) {
+    ColumnState c;
+    const double rvs = rho_vs_host(T);
+    double rd = p / (T * (kRd + qt * kRv));
+    double rv = qt * rd;
+    if (qt * rd > rvs) {
+        rd = (p - rvs * kRv * T) / (kRd * T);
+        rv = rvs;
+    }
+    c.rho_d = rd;
+    c.rho_v = rv;
+    c.p = p;
+    c.rho_m = qt * rd;
+    c.T = T;
+    c.E = (kCvd * rd + kCvv * rv + kCl * (c.rho_m - rv)) * (T - kTref) + rv * kLprime;
+    return c;
+}
+
+// Classical RK4 for dp/dz = -(rho_d + rho_m) g, T = theta (p/p_ref)^(R_d/c_pd),
+// qt = qt0 (1 - z/H); steps <= 1 m landing on every requested level.
+void column(const std::vector<double> &z, double theta, double p_s, double qt0, double H, double g,
+            std::vector<ColumnState> &out) {
+    const double kappa = kRd / kCpd;
+    std::vector<size_t> order(z.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return z[a] < z[b]; });
+    auto rhs = [&](double zz, double p) {
+        const double T = theta * std::pow(p / kPref, kappa);
+        const ColumnState c = moist_at(p, T, qt0 * (1.0 - zz / H));
+        return -(c.rho_d + c.rho_m) * g;
+    };
+    out.assign(z.size(), ColumnState());
+    double zc = 0.0, p = p_s;
+    for (size_t idx : order) {
+        const double zt = z[idx];
+        if (zt > zc) {
+            const int n = (int)std::ceil((zt - zc) / 1.0);
+            const double hs = (zt - zc) / n;
+            for (int i = 0; i < n; ++i) {
+                const double k1 = rhs(zc, p);
+                const double k2 = rhs(zc + 0.5 * hs, p + 0.5 * hs * k1);
+                const double k3 = rhs(zc + 0.5 * hs, p + 0.5 * hs * k2);
+                const double k4 = rhs(zc + hs, p + hs * k3);
+                p += hs * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+                zc += hs;
+            }
+            zc = zt;
+        }
+        const double T = theta * std::pow(p / kPref, kappa);
+        out[idx] = moist_at(p, T, qt0 * (1.0 - zt / H));   // at rest: E is internal energy
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct dg_ctx {
+    dg_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int fp32 = 0;
+    const Launchers<double> *L64 = nullptr;
+    const Launchers<float> *L32 = nullptr;
+    int nf = 0, np = 0, nfp1 = 0, nd = 0, ntr = 0, epb = 0;
+    long long ne = 0, nodes = 0;
+    size_t rsz = 8;
+    MeshData M;
+    RefData<double> ref64;
+    RefData<float> ref32;
+    void *U[2] = {nullptr, nullptr};   // U^n, work state
+    void *derived = nullptr;
+    void *trace[2] = {nullptr, nullptr};
+    double *bnode_d = nullptr, *bface_d = nullptr;
+    void *bnode_r = nullptr, *bface_r = nullptr;
+    unsigned long long *flags = nullptr;
+    double *partials = nullptr;
+    int nred = 0;
+    std::vector<double> z_node, z_face;
+    bool base_set = false, state_set = false, derived_valid = false;
+    int parity = 0;  // trace buffer holding the traces of U^n
+    size_t device_bytes = 0;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? DG_OK : DG_ECUDA; }
+
+template <typename Real>
+KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
+    KArgs<Real> A;
+    std::memset(&A, 0, sizeof(A));
+    A.M = c->M;
+    A.ref = ref;
+    A.derived = (Real *)c->derived;
+    A.bnode = (const Real *)c->bnode_r;
+    A.bface = (const Real *)c->bface_r;
+    A.bnode_d = c->bnode_d;
+    A.flags = c->flags;
+    return A;
+}
+
+template <typename Real>
+int do_prepare(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, const void *U, int tb) {
+    KArgs<Real> A = base_args<Real>(c, ref);
+    A.Uin = (const Real *)U;
+    A.trace_out = (Real *)c->trace[tb];
+    return cuda_status(L->prepare(A, c->stream));
+}
+
+int prepare(dg_ctx *c, const void *U, int tb) {
+    return c->fp32 ? do_prepare<float>(c, c->L32, c->ref32, U, tb)
+                   : do_prepare<double>(c, c->L64, c->ref64, U, tb);
+}
+
+template <typename Real>
+int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int mode, const void *Uin,
+             const void *Un, void *Uout, int tin, double alpha, double beta, double gdt) {
+    KArgs<Real> A = base_args<Real>(c, ref);
+    A.Uin = (const Real *)Uin;
+    A.Un = (const Real *)Un;
+    A.Uout = (Real *)Uout;
+    A.trace_in = (const Real *)c->trace[tin];
+    A.trace_out = (Real *)c->trace[1 - tin];
+    A.alpha = (Real)alpha;
+    A.beta = (Real)beta;
+    A.gdt = (Real)gdt;
+    return cuda_status(L->stage(A, mode, c->stream));
+}
+
+int stage(dg_ctx *c, int mode, const void *Uin, const void *Un, void *Uout, int tin, double alpha,
+          double beta, double gdt) {
+    return c->fp32 ? do_stage<float>(c, c->L32, c->ref32, mode, Uin, Un, Uout, tin, alpha, beta, gdt)
+                   : do_stage<double>(c, c->L64, c->ref64, mode, Uin, Un, Uout, tin, alpha, beta, gdt);
+}
+
+void release(dg_ctx *c) {
+    void *ptrs[] = {c->U[0], c->U[1], c->derived, c->trace[0], c->trace[1], c->bnode_d,
+                    c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int alloc(dg_ctx *c, void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return DG_ENOMEM;
+    }
+    c->device_bytes += bytes;
+    return DG_OK;
+}
+
+int upload_base(dg_ctx *c, const double *node_tab, const double *face_tab) {
+    const int nn = c->M.nzlev_node, nfz = c->M.nzlev_face;
+    cudaError_t e = cudaMemcpyAsync(c->bnode_d, node_tab, sizeof(double) * 4 * nn,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->bface_d, face_tab, sizeof(double) * 4 * nfz, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e != cudaSuccess) return DG_ECUDA;
+    if (c->fp32) {
+        std::vector<float> fn(4 * nn), ff(4 * nfz);
+        for (int i = 0; i < 4 * nn; ++i) fn[i] = (float)node_tab[i];
+        for (int i = 0; i < 4 * nfz; ++i) ff[i] = (float)face_tab[i];
+        e = cudaMemcpyAsync(c->bnode_r, fn.data(), sizeof(float) * fn.size(), cudaMemcpyHostToDevice,
+                            c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->bface_r, ff.data(), sizeof(float) * ff.size(),
+                                cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // host vectors go out of scope
+        if (e != cudaSuccess) return DG_ECUDA;
+    } else {
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    }
+    c->base_set = true;
+    c->derived_valid = false;
+    return DG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *dg_strerror(int code) {
+    switch (code) {
+        case DG_OK: return "ok";
+        case DG_EINVAL: return "invalid argument or size";
+        case DG_ENOMEM: return "device allocation failed";
+        case DG_ECUDA: return "CUDA error";
+        case DG_ENOCONV: return "Newton split did not converge at some node";
+        case DG_ENONPHYS: return "non-physical or non-finite state";
+        case DG_ESTATE: return "base state or state not set";
+        case DG_ENOTIMPL: return "not available in this build";
+        default: return "unknown status";
+    }
+}
+
+int dg_gauss_legendre(int n, double *x, double *w) {
+    if (n < 1 || n > 6 || !x || !w) return DG_EINVAL;
+    gauss_rule(n, x, w);
+    return DG_OK;
+}
+
+int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
+    if (!out || !cfg) return DG_EINVAL;
+    *out = nullptr;
+    const dg_config &g = *cfg;
+    if (g.dim != 2 && g.dim != 3) return DG_EINVAL;
+    if (g.order < 1 || g.order > 5) return DG_EINVAL;
+    if (g.precision != DG_FP64 && g.precision != DG_FP32_BULK) return DG_EINVAL;
+    if (g.rain != 0 && g.rain != 1) return DG_EINVAL;
+    long long ne = 1;
+    for (int j = 0; j < g.dim; ++j) {
+        if (g.n[j] < 1 || !(g.L[j] > 0.0) || !std::isfinite(g.L[j])) return DG_EINVAL;
+        ne *= g.n[j];
+    }
+    if (!std::isfinite(g.g)) return DG_EINVAL;
+    const int p1 = g.order + 1;
+    const int np = g.dim == 2 ? p1 * p1 : p1 * p1 * p1;
+    const int nf = (g.rain ? 4 : 3) + g.dim;
+    if (ne * np * (long long)(nf + 3) * 2 > 2147483647LL) return DG_EINVAL;
+
+    dg_ctx *c = new (std::nothrow) dg_ctx();
+    if (!c) return DG_ENOMEM;
+    c->cfg = g;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return DG_ECUDA;
+    }
+    c->fp32 = (g.precision == DG_FP32_BULK);
+    c->rsz = c->fp32 ? sizeof(float) : sizeof(double);
+    if (c->fp32) {
+        c->L32 = g.dim == 2 ? launchers_d2_f32(g.order, g.rain) : launchers_d3_f32(g.order, g.rain);
+        c->nf = c->L32->nf; c->np = c->L32->np; c->nfp1 = c->L32->nfp1;
+        c->nd = c->L32->nd; c->ntr = c->L32->ntr; c->epb = c->L32->epb;
+    } else {
+        c->L64 = g.dim == 2 ? launchers_d2_f64(g.order, g.rain) : launchers_d3_f64(g.order, g.rain);
+        c->nf = c->L64->nf; c->np = c->L64->np; c->nfp1 = c->L64->nfp1;
+        c->nd = c->L64->nd; c->ntr = c->L64->ntr; c->epb = c->L64->epb;
+    }
+    c->ne = ne;
+    c->nodes = ne * np;
+
+    MeshData &M = c->M;
+    std::memset(&M, 0, sizeof(M));
+    for (int j = 0; j < 3; ++j) {
+        M.n[j] = j < g.dim ? g.n[j] : 1;
+        M.h[j] = j < g.dim ? g.L[j] / g.n[j] : 1.0;
+        M.two_over_h[j] = 2.0 / M.h[j];
+        M.periodic[j] = (j < g.dim - 1) ? ((g.periodic_mask >> j) & 1) : 0;
+    }
+    M.ne = (int)ne;
+    const int nvert = g.n[g.dim - 1];
+    M.nzlev_node = nvert * p1;
+    M.nzlev_face = nvert + 1;
+    M.g = g.g;
+    M.rho_w = g.rho_w;
+    // v0 Gamma(4.5)/6 (pi N0)^(-1/8) with N0 = 8e6 m^-4, v0 = 130 m^(1/2)/s (Section 2.1)
+    M.kvr = 130.0 * std::tgamma(4.5) / 6.0 * std::pow(M_PI * 8.0e6, -0.125);
+    M.jac = 1.0;
+    for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
+    c->ref64 = make_ref<double>(g.order);
+    c->ref32 = make_ref<float>(g.order);
+
+    // z-levels
+    c->z_node.resize(M.nzlev_node);
+    c->z_face.resize(M.nzlev_face);
+    const double hz = M.h[g.dim - 1];
+    for (int iz = 0; iz < nvert; ++iz)
+        for (int a = 0; a < p1; ++a)
+            c->z_node[iz * p1 + a] = iz * hz + (1.0 + (double)c->ref64.xi[a]) * hz * 0.5;
+    for (int iz = 0; iz <= nvert; ++iz) c->z_face[iz] = iz * hz;
+
+    DeviceGuard dg(c->device);
+    const size_t state = (size_t)c->nodes * nf * c->rsz;
+    const size_t trace = (size_t)2 * g.dim * c->ntr * ne * c->nfp1 * c->rsz;
+    c->nred = std::min<long long>(kGridStrideBlocks, (c->nodes + kRedThreads - 1) / kRedThreads);
+    int st = DG_OK;
+    if (st == DG_OK) st = alloc(c, &c->U[0], state);
+    if (st == DG_OK) st = alloc(c, &c->U[1], state);
+    if (st == DG_OK) st = alloc(c, &c->derived, (size_t)c->nodes * c->nd * c->rsz);
+    if (st == DG_OK) st = alloc(c, &c->trace[0], trace);
+    if (st == DG_OK) st = alloc(c, &c->trace[1], trace);
+    if (st == DG_OK) st = alloc(c, (void **)&c->bnode_d, sizeof(double) * 4 * M.nzlev_node);
+    if (st == DG_OK) st = alloc(c, (void **)&c->bface_d, sizeof(double) * 4 * M.nzlev_face);
+    if (c->fp32) {
+        if (st == DG_OK) st = alloc(c, &c->bnode_r, sizeof(float) * 4 * M.nzlev_node);
+        if (st == DG_OK) st = alloc(c, &c->bface_r, sizeof(float) * 4 * M.nzlev_face);
+    } else {
+        c->bnode_r = nullptr;
+        c->bface_r = nullptr;
+    }
+    if (st == DG_OK) st = alloc(c, (void **)&c->flags, sizeof(unsigned long long) * 2);
+    if (st == DG_OK) st = alloc(c, (void **)&c->partials, sizeof(double) * kNRed * c->nred);
+    if (st == DG_OK && cudaMemsetAsync(c->flags, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+        st = DG_ECUDA;
+    if (st != DG_OK) {
+        release(c);
+        delete c;
+        return st;
+    }
+    if (!c->fp32) {
+        // the float64 tables serve both the split and the flux arithmetic
+        c->bnode_r = c->bnode_d;
+        c->bface_r = c->bface_d;
+    }
+    *out = c;
+    return DG_OK;
+}
+
+void dg_free(dg_ctx *c) {
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        cudaStreamSynchronize(c->stream);
+        if (c->fp32) {
+            release(c);
+        } else {
+            c->bnode_r = nullptr;
+            c->bface_r = nullptr;
+            release(c);
+        }
+    }
+    delete c;
+}
+
+int dg_get_info(const dg_ctx *c, dg_info *info) {
+    if (!c || !info) return DG_EINVAL;
+    info->n_fields = c->nf;
+    info->nodes_per_elem = c->np;
+    info->face_points_per_face = c->nfp1;
+    info->n_zlev_node = c->M.nzlev_node;
+    info->n_zlev_face = c->M.nzlev_face;
+    info->elems_per_block = c->epb;
+    info->n_elem = c->ne;
+    info->n_nodes = c->nodes;
+    info->n_dofs = c->nodes * c->nf;
+    info->state_bytes = (size_t)c->nodes * c->nf * c->rsz;
+    info->device_bytes = c->device_bytes;
+    return DG_OK;
+}
+
+int dg_zlevels(const dg_ctx *c, double *z_node, double *z_face) {
+    if (!c || !z_node || !z_face) return DG_EINVAL;
+    std::copy(c->z_node.begin(), c->z_node.end(), z_node);
+    std::copy(c->z_face.begin(), c->z_face.end(), z_face);
+    return DG_OK;
+}
+
+int dg_set_base_state(dg_ctx *c, const double *node_tab, const double *face_tab) {
+    if (!c || !node_tab || !face_tab) return DG_EINVAL;
+    DeviceGuard dg(c->device);
+    return upload_base(c, node_tab, face_tab);
+}
+
+int dg_init_bubble(dg_ctx *c, const dg_bubble *b, const double *noise, int where) {
+    if (!c || !b) return DG_EINVAL;
+    if (where != DG_HOST && where != DG_DEVICE) return DG_EINVAL;
+    if (!(b->H > 0.0) || !(b->p_s > 0.0) || !(b->theta > 0.0)) return DG_EINVAL;
+    for (int j = 0; j < c->cfg.dim; ++j)
+        if (!(b->radius[j] > 0.0)) return DG_EINVAL;
+    DeviceGuard dg(c->device);
+    const int nn = c->M.nzlev_node, nfz = c->M.nzlev_face;
+    std::vector<double> z(c->z_node);
+    z.insert(z.end(), c->z_face.begin(), c->z_face.end());
+    std::vector<ColumnState> col;
+    column(z, b->theta, b->p_s, b->qt0, b->H, c->cfg.g, col);
+    std::vector<double> tn(4 * nn), tf(4 * nfz);
+    for (int i = 0; i < nn + nfz; ++i) {
+        const ColumnState &s = col[i];
+        const double p = s.p;
+        double *tab = i < nn ? tn.data() : tf.data();
+        const int k = i < nn ? i : i - nn, n = i < nn ? nn : nfz;
+        tab[k] = s.rho_d;
+        tab[n + k] = s.rho_m;
+        tab[2 * n + k] = s.E;
+        tab[3 * n + k] = p;
+    }
+    int st = upload_base(c, tn.data(), tf.data());
+    if (st != DG_OK) return st;
+    BubbleArgs B;
+    B.theta = b->theta;
+    B.qt0 = b->qt0;
+    B.H = b->H;
+    B.amplitude = b->amplitude;
+    for (int j = 0; j < 3; ++j) {
+        B.centre[j] = b->centre[j];
+        B.radius[j] = j < c->cfg.dim ? b->radius[j] : 1.0;
+    }
+    B.noise = nullptr;
+    if (noise) {
+        if (where == DG_DEVICE) {
+            B.noise = noise;
+        } else {
+            // stage the host noise in the derived-field buffer (stale here, >= 8 B per node)
+            if (cudaMemcpyAsync(c->derived, noise, sizeof(double) * c->nodes, cudaMemcpyHostToDevice,
+                                c->stream) != cudaSuccess)
+                return DG_ECUDA;
+            B.noise = (const double *)c->derived;
+        }
+    }
+    cudaError_t e;
+    if (c->fp32) {
+        KArgs<float> A = base_args<float>(c, c->ref32);
+        A.Uout = (float *)c->U[0];
+        e = c->L32->init_bubble(A, B, c->stream);
+    } else {
+        KArgs<double> A = base_args<double>(c, c->ref64);
+        A.Uout = (double *)c->U[0];
+        e = c->L64->init_bubble(A, B, c->stream);
+    }
+    if (e != cudaSuccess) return DG_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    c->state_set = true;
+    c->derived_valid = false;
+    return DG_OK;
+}
+
+int dg_set_state(dg_ctx *c, const void *U, int where) {
+    if (!c || !U || (where != DG_HOST && where != DG_DEVICE)) return DG_EINVAL;
+    DeviceGuard dg(c->device);
+    const size_t bytes = (size_t)c->nodes * c->nf * c->rsz;
+    cudaError_t e = cudaMemcpyAsync(c->U[0], U, bytes,
+                                    where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return DG_ECUDA;
+    c->state_set = true;
+    c->derived_valid = false;
+    return DG_OK;
+}
+
+int dg_get_state(dg_ctx *c, void *U, int where) {
+    if (!c || !U || (where != DG_HOST && where != DG_DEVICE)) return DG_EINVAL;
+    if (!c->state_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    const size_t bytes = (size_t)c->nodes * c->nf * c->rsz;
+    cudaError_t e = cudaMemcpyAsync(U, c->U[0], bytes,
+                                    where == DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return DG_ECUDA;
+    if (where == DG_HOST && cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    return DG_OK;
+}
+
+int dg_check_status(dg_ctx *c, long long counts[2]) {
+    if (!c) return DG_EINVAL;
+    DeviceGuard dg(c->device);
+    unsigned long long h[2] = {0, 0};
+    if (cudaMemcpyAsync(h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return DG_ECUDA;
+    if (cudaMemsetAsync(c->flags, 0, sizeof(h), c->stream) != cudaSuccess) return DG_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    if (counts) {
+        counts[0] = (long long)h[0];
+        counts[1] = (long long)h[1];
+    }
+    if (h[1]) return DG_ENONPHYS;
+    if (h[0]) return DG_ENOCONV;
+    return DG_OK;
+}
+
+int dg_saturation_split(dg_ctx *c, const void *U, double *T, double *rho_v, double *rho_c,
+                        double *p_prime, long long *n_unconverged) {
+    if (!c || !U) return DG_EINVAL;
+    if (!c->base_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    cudaError_t e;
+    if (n_unconverged) {
+        long long dummy[2];
+        int st = dg_check_status(c, dummy);  // start from clean counters
+        (void)st;
+    }
+    if (c->fp32) {
+        KArgs<float> A = base_args<float>(c, c->ref32);
+        A.Uin = (const float *)U;
+        e = c->L32->split(A, T, rho_v, rho_c, p_prime, c->stream);
+    } else {
+        KArgs<double> A = base_args<double>(c, c->ref64);
+        A.Uin = (const double *)U;
+        e = c->L64->split(A, T, rho_v, rho_c, p_prime, c->stream);
+    }
+    if (e != cudaSuccess) return DG_ECUDA;
+    if (n_unconverged) {
+        long long cnt[2];
+        int st = dg_check_status(c, cnt);
+        *n_unconverged = cnt[0];
+        if (st == DG_ENONPHYS) return st;
+        if (st == DG_ECUDA) return st;
+    }
+    return DG_OK;
+}
+
+int dg_rhs(dg_ctx *c, const void *U, void *dUdt) {
+    if (!c || !U || !dUdt || U == dUdt) return DG_EINVAL;
+    if (!c->base_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    // the scratch derived fields and trace buffer 0 now describe U, not U^n
+    c->derived_valid = false;
+    int st = prepare(c, U, 0);
+    if (st != DG_OK) return st;
+    return stage(c, MODE_RHS, U, U, dUdt, 0, 0.0, 1.0, 1.0);
+}
+
+int dg_step_async(dg_ctx *c, double dt, int nsteps) {
+    if (!c || nsteps < 0 || !std::isfinite(dt)) return DG_EINVAL;
+    if (!c->base_set || !c->state_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    int st = DG_OK;
+    if (!c->derived_valid) {
+        st = prepare(c, c->U[0], 0);
+        if (st != DG_OK) return st;
+        c->parity = 0;
+        c->derived_valid = true;
+    }
+    void *Un = c->U[0], *Uw = c->U[1];
+    // SSPRK(4,3), Shu-Osher form (Remark 3.1):
+    //   u1 = u + dt/2 L(u); u2 = u1 + dt/2 L(u1); u3 = 2/3 u + 1/3 u2 + dt/6 L(u2);
+    //   u^{n+1} = u3 + dt/2 L(u3)
+    for (int n = 0; n < nsteps && st == DG_OK; ++n) {
+        int p = c->parity;
+        st = stage(c, MODE_STAGE, Un, Un, Uw, p, 0.0, 1.0, 0.5 * dt);
+        p ^= 1;
+        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Uw, p, 0.0, 1.0, 0.5 * dt);
+        p ^= 1;
+        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Un, Uw, p, 2.0 / 3.0, 1.0 / 3.0, dt / 6.0);
+        p ^= 1;
+        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Un, p, 0.0, 1.0, 0.5 * dt);
+        p ^= 1;
+        c->parity = p;
+    }
+    return st;
+}
+
+int dg_step(dg_ctx *c, double dt, int nsteps) {
+    int st = dg_step_async(c, dt, nsteps);
+    if (st != DG_OK) return st;
+    return dg_check_status(c, nullptr);
+}
+
+int dg_reduce(dg_ctx *c, double out[DG_NREDUCE]) {
+    if (!c || !out) return DG_EINVAL;
+    if (!c->base_set || !c->state_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    if (!c->derived_valid) {
+        int st = prepare(c, c->U[0], 0);
+        if (st != DG_OK) return st;
+        c->parity = 0;
+        c->derived_valid = true;
+    }
+    cudaError_t e;
+    if (c->fp32) {
+        KArgs<float> A = base_args<float>(c, c->ref32);
+        A.Uin = (const float *)c->U[0];
+        e = c->L32->reduce(A, c->partials, c->nred, c->stream);
+    } else {
+        KArgs<double> A = base_args<double>(c, c->ref64);
+        A.Uin = (const double *)c->U[0];
+        e = c->L64->reduce(A, c->partials, c->nred, c->stream);
+    }
+    if (e != cudaSuccess) return DG_ECUDA;
+    std::vector<double> h((size_t)kNRed * c->nred);
+    if (cudaMemcpyAsync(h.data(), c->partials, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return DG_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    for (int r = 0; r < kNRed; ++r) out[r] = (r == 5 || r == 6) ? -INFINITY : 0.0;
+    for (int b = 0; b < c->nred; ++b)
+        for (int r = 0; r < kNRed; ++r) {
+            const double v = h[(size_t)b * kNRed + r];
+            out[r] = (r == 5 || r == 6) ? std::max(out[r], v) : out[r] + v;
+        }
+    return DG_OK;
+}
+
+int dg_adjoint_step(dg_ctx *c, double dt, const void *U_n, const double *lam_np1, double *lam_n) {
+    (void)c; (void)dt; (void)U_n; (void)lam_np1; (void)lam_n;
+    return DG_ENOTIMPL;
+}
+
+}  // extern "C"

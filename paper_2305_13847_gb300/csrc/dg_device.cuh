@@ -1,0 +1,781 @@
+// Device code of the moist DG right-hand side and SSPRK(4,3) stage update.
+//
+// Method: Hittmeir, Lederer, Schoeberl, von Wahl, "A discontinuous Galerkin
+// approach for atmospheric flows with implicit condensation" (arXiv 2305.13847).
+// Equation numbers below refer to that paper.
+//
+// Kernels (templated on dimension D, order K, rain switch and storage type):
+//   k_prepare  per node: implicit-condensation split Eq. (2.8) -> derived
+//              fields; per face point: traces of U and of (T, rho_v, p') on
+//              all 2D faces of the element, written to a trace buffer.
+//   k_stage    per element: volume term of Eq. (3.2) by sum factorisation,
+//              Lax-Friedrichs face fluxes (Section 3.2, Eq. (3.4)) against the
+//              neighbours' traces, sources (Eq. (2.4) and gravity), diagonal
+//              M^{-1}; then either writes dU/dt, or performs the SSPRK(4,3)
+//              stage combination and, fused, the next stage's split and traces.
+//   k_split    per node split only (dg_saturation_split).
+//   k_init_bubble, k_reduce_*  workload set-up and diagnostics.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace dgm {
+
+// ---------------------------------------------------------------------------
+// Physical constants: Table 1 (Appendix A) and Section 2.1 of the paper.
+// ---------------------------------------------------------------------------
+constexpr double kCl = 4218.0;     // specific heat of liquid water
+constexpr double kCpd = 1005.0;    // dry air, constant pressure
+constexpr double kCpv = 1850.0;    // vapour, constant pressure
+constexpr double kCvd = 718.0;     // dry air, constant volume
+constexpr double kCvv = 1390.0;    // vapour, constant volume
+constexpr double kEref = 610.7;    // e_s(T_ref)
+constexpr double kLref = 2.835e6;  // latent heat at T_ref
+constexpr double kRd = 287.05;
+constexpr double kRv = 461.51;
+constexpr double kTref = 273.15;
+constexpr double kPref = 1.0e5;
+// Eq. (2.6): e_s = e_ref (T/T_ref)^a exp(b (1/T_ref - 1/T))
+constexpr double kEsA = (kCpv - kCl) / kRv;
+constexpr double kEsB = (kLref - (kCpv - kCl) * kTref) / kRv;
+constexpr double kLprime = kLref - kRv * kTref;      // rho_v coefficient of Eq. (2.3)
+constexpr double kInvTref = 1.0 / kTref;
+constexpr double kRvs0 = kEref / (kRv * kTref);      // rho_vs(T_ref)
+// Eq. (2.4), q_au = 0
+constexpr double kSevA = 3.86e-3;
+constexpr double kSevB = 9.41e-5;
+constexpr double kSevC = 9.1;
+constexpr double kSau = 1.0e-3;
+constexpr double kSac = 1.72;
+
+constexpr int kMaxNewton = 50;
+constexpr double kNewtonTol = 1e-12;
+
+constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// ---------------------------------------------------------------------------
+// Parameter blocks (passed by value; they live in the kernel-parameter bank)
+// ---------------------------------------------------------------------------
+struct MeshData {
+    int n[3];
+    int ne;
+    int periodic[3];
+    int nzlev_node, nzlev_face;
+    double two_over_h[3];  // 2 / h_j: d(xi)/dx
+    double h[3];
+    double g;
+    double rho_w;          // <= 0: rho_m + rho_r
+    double kvr;            // v0 Gamma(4.5)/6 (pi N0)^(-1/8)
+    double jac;            // |K| / 2^d
+};
+
+template <typename Real>
+struct RefData {
+    Real dhat[6][6];   // dhat[a][i] = (w_i / w_a) l_a'(xi_i): weak derivative of basis a
+    Real lm[6], lp[6];       // l_a(-1), l_a(+1)
+    Real liftm[6], liftp[6]; // l_a(-1)/w_a, l_a(+1)/w_a
+    Real xi[6], w[6];
+};
+
+template <typename Real>
+struct KArgs {
+    MeshData M;
+    RefData<Real> ref;
+    const Real *Uin;       // state the operator is evaluated on (ABI layout)
+    const Real *Un;        // U^n for the stage combination (may equal Uin)
+    Real *Uout;            // MODE_RHS: dU/dt; MODE_STAGE: new stage state
+    Real *derived;         // [ND][nodes]
+    const Real *trace_in;  // traces of Uin:   [2D][NTR][ne][NFP1]
+    Real *trace_out;       // traces of Uout (MODE_STAGE)
+    const Real *bnode;     // base at node levels [4][nzlev_node]: rho_d, rho_m, E, p
+    const Real *bface;     // base at face levels [4][nzlev_face]
+    const double *bnode_d; // float64 copy for the split
+    Real alpha, beta, gdt; // Uout = alpha Un + beta Uin + gdt dU/dt
+    unsigned long long *flags;  // [0] Newton failures, [1] non-physical nodes
+};
+
+// ---------------------------------------------------------------------------
+// Compile-time layout of one (D, K, RAIN) configuration
+// ---------------------------------------------------------------------------
+template <int D_, int K_, bool RAIN_>
+struct Shape {
+    static constexpr int D = D_;
+    static constexpr int K = K_;
+    static constexpr bool RAIN = RAIN_;
+    static constexpr int P1 = K + 1;
+    static constexpr int NP = ipow(P1, D);        // nodes per element
+    static constexpr int NFP1 = ipow(P1, D - 1);  // points per face
+    static constexpr int NFACE = 2 * D;
+    static constexpr int NF = (RAIN ? 4 : 3) + D; // unknowns
+    static constexpr int IM = RAIN ? 3 : 2;       // first momentum field
+    static constexpr int IE = IM + D;             // energy field
+    static constexpr int ND = RAIN ? 5 : 3;       // derived: T, rho_v, p' [, G_rm, v_r]
+    static constexpr int NTR = NF + 3;            // traced: U, T, rho_v, p'
+    static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;   // elements per CTA
+    static constexpr int NT = ((EPB * NP + 31) / 32) * 32;          // threads per CTA
+    static constexpr int VERT = D - 1;
+};
+
+template <int D, int P1>
+__device__ __forceinline__ int digit(int a, int j) {
+    if (j == 0) return a % P1;
+    if (j == 1) return (D == 2) ? a / P1 : (a / P1) % P1;
+    return a / (P1 * P1);
+}
+
+template <int P1>
+__device__ __forceinline__ int stride_of(int j) { return j == 0 ? 1 : (j == 1 ? P1 : P1 * P1); }
+
+// index of the face point of node a on the faces normal to e_j
+template <int D, int P1>
+__device__ __forceinline__ int face_q(int a, int j) {
+    if (D == 2) return j == 0 ? digit<D, P1>(a, 1) : digit<D, P1>(a, 0);
+    if (j == 0) return digit<D, P1>(a, 1) + P1 * digit<D, P1>(a, 2);
+    if (j == 1) return digit<D, P1>(a, 0) + P1 * digit<D, P1>(a, 2);
+    return digit<D, P1>(a, 0) + P1 * digit<D, P1>(a, 1);
+}
+
+// node at position i along direction j through face point q
+template <int D, int P1>
+__device__ __forceinline__ int line_node(int j, int q, int i) {
+    if (D == 2) return j == 0 ? i + P1 * q : q + P1 * i;
+    const int q0 = q % P1, q1 = q / P1;
+    if (j == 0) return i + P1 * (q0 + P1 * q1);
+    if (j == 1) return q0 + P1 * (i + P1 * q1);
+    return q0 + P1 * (q1 + P1 * i);
+}
+
+// vertical node digit of face point q of a face normal to e_j (j not vertical)
+template <int D, int P1>
+__device__ __forceinline__ int face_q_vert(int j, int q) {
+    if (D == 2) return q;           // j == 0: remaining direction is the vertical
+    return q / P1;                  // j = 0 or 1: remaining (., vertical)
+}
+
+__device__ __forceinline__ void elem_multi(const MeshData &M, int e, int &i0, int &i1, int &i2) {
+    i0 = e % M.n[0];
+    const int r = e / M.n[0];
+    i1 = r % M.n[1];
+    i2 = r / M.n[1];
+}
+
+// neighbour across face (j, s) or -1 at a wall
+template <int D>
+__device__ __forceinline__ int neighbour(const MeshData &M, int e, int j, int s) {
+    int i[3];
+    elem_multi(M, e, i[0], i[1], i[2]);
+    int v = i[j] + s;
+    if (v < 0 || v >= M.n[j]) {
+        if (!M.periodic[j]) return -1;
+        v = (v < 0) ? v + M.n[j] : v - M.n[j];
+    }
+    i[j] = v;
+    return i[0] + M.n[0] * (i[1] + M.n[1] * (D == 3 ? i[2] : 0));
+}
+
+template <int D>
+__device__ __forceinline__ int vert_index(const MeshData &M, int e) {
+    int i0, i1, i2;
+    elem_multi(M, e, i0, i1, i2);
+    return D == 2 ? i1 : i2;
+}
+
+// ---------------------------------------------------------------------------
+// Thermodynamics (float64): Eq. (2.3), (2.6), (2.8)
+// ---------------------------------------------------------------------------
+// rho_vs(T) = e_s(T) / (R_v T) = rho_vs(T_ref) (T/T_ref)^(a-1) exp(b (1/T_ref - 1/T))
+__device__ __forceinline__ double rho_vs(double T, double invT) {
+    return kRvs0 * exp((kEsA - 1.0) * log(T * kInvTref) + kEsB * (kInvTref - invT));
+}
+
+struct SplitResult {
+    double T, rv, deficit;  // deficit = rho_vs(T) - rho_v (0 at saturation)
+    bool converged;
+};
+
+// Eq. (2.8): T, rho_v from totals rho_d, rho_m, rho_r and internal energy re.
+// Unsaturated candidate in closed form; if supersaturated, Newton on
+// H(T) = (c_vd rd + c_vv rvs + c_l (rm - rvs + rr)) (T - T_ref) + rvs L' - re
+// from T_u.  H is increasing and convex, so Newton from T_u overshoots once
+// and then decreases monotonically to the root; a bracket guards against
+// rounding.  Stop when |dT| <= 1e-12 T, after one more step.
+__device__ __forceinline__ SplitResult split_point(double rd, double rm, double rr, double re) {
+    SplitResult r;
+    const double cu = kCvd * rd + kCvv * rm + kCl * rr;
+    const double tu = kTref + (re - rm * kLprime) / cu;
+    const double rvs_u = rho_vs(tu, 1.0 / tu);
+    if (!(rm > rvs_u)) {
+        r.T = tu;
+        r.rv = rm;
+        r.deficit = rvs_u - rm;
+        r.converged = true;
+        return r;
+    }
+    double t = tu, lo = tu, hi = INFINITY;
+    bool extra = false, done = false;
+    const double cdry = kCvd * rd + kCl * (rm + rr);
+    for (int it = 0; it < kMaxNewton; ++it) {
+        const double invt = 1.0 / t;
+        const double rvs = rho_vs(t, invt);
+        const double drvs = rvs * invt * ((kEsA - 1.0) + kEsB * invt);
+        const double heat = cdry + (kCvv - kCl) * rvs;
+        const double h = heat * (t - kTref) + rvs * kLprime - re;
+        const double dh = heat + ((kCvv - kCl) * (t - kTref) + kLprime) * drvs;
+        if (h < 0.0) lo = t;
+        if (h > 0.0) hi = t;
+        double tn = t - h / dh;
+        if (!(tn >= lo && tn <= hi)) tn = isinf(hi) ? t + 10.0 : 0.5 * (lo + hi);
+        const bool done_now = extra || (h == 0.0);
+        if (fabs(tn - t) <= kNewtonTol * fabs(tn)) extra = true;
+        t = tn;
+        if (done_now) { done = true; break; }
+    }
+    r.T = t;
+    r.rv = rho_vs(t, 1.0 / t);
+    r.deficit = 0.0;
+    r.converged = done;
+    return r;
+}
+
+// v_r = v0 Gamma(4.5)/6 (pi rho_w N0)^(-1/8) rho_r^(1/8) (Section 2.1)
+template <typename Real>
+__device__ __forceinline__ Real rain_velocity(Real rr, Real rm, const MeshData &M) {
+    const Real rrp = rr > Real(0) ? rr : Real(0);
+    const Real rw = M.rho_w > 0.0 ? Real(M.rho_w) : rm + rr;
+    if (!(rrp > Real(0)) || !(rw > Real(0))) return Real(0);
+    return Real(M.kvr) * pow(rrp / rw, Real(0.125));
+}
+
+// Per-node split plus the node-local quantities the next operator needs.
+struct NodeDerived {
+    double T, rv, pp, gm, vr;
+    bool conv, phys;
+};
+
+template <bool RAIN>
+__device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double rr, double E,
+                                                    double msq, double pbar, const MeshData &M) {
+    NodeDerived o;
+    const double rho = rd + rm + rr;
+    const double re = E - 0.5 * msq / rho;
+    const SplitResult s = split_point(rd, rm, rr, re);
+    o.T = s.T;
+    o.rv = s.rv;
+    o.conv = s.converged;
+    o.pp = (rd * kRd + s.rv * kRv) * s.T - pbar;
+    o.phys = (rd > 0.0) && (rho > 0.0) && (s.T > 50.0) && (s.T < 1000.0) && isfinite(o.pp);
+    o.gm = 0.0;
+    o.vr = 0.0;
+    if (RAIN) {
+        // Eq. (2.4): all rain powers from x = max(rho_r,0)^(1/16)
+        const double rrp = rr > 0.0 ? rr : 0.0;
+        const double x = rrp > 0.0 ? pow(rrp, 0.0625) : 0.0;
+        const double x2 = x * x, x3 = x2 * x, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
+        const double rc = rm - s.rv;
+        const double s_ev = (kSevA - kSevB * (s.T - kTref)) * (1.0 + kSevC * x3) * s.deficit * x8;
+        const double s_au = kSau * (rc > 0.0 ? rc : 0.0);
+        const double s_ac = kSac * rc * x14;
+        o.gm = s_ev - s_au - s_ac;
+        o.vr = rain_velocity<double>(rr, rm, M);
+    }
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise flux of Eq. (2.11) and the wave-speed bound of Eq. (3.4)
+// ---------------------------------------------------------------------------
+template <int D, bool RAIN, typename Real>
+struct Prim {
+    Real rd, rm, rr, rho, E, p, pp, T, rv, vr;
+    Real m[D], u[D];
+};
+
+template <class S, typename Real>
+__device__ __forceinline__ void make_prim(Prim<S::D, S::RAIN, Real> &P, const Real *U, Real brd,
+                                          Real brm, Real bE, Real bp, Real T, Real rv, Real pp) {
+    P.rd = brd + U[0];
+    P.rm = brm + U[1];
+    P.rr = S::RAIN ? U[2] : Real(0);
+    P.rho = P.rd + P.rm + P.rr;
+    const Real inv = Real(1) / P.rho;
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) {
+        P.m[j] = U[S::IM + j];
+        P.u[j] = P.m[j] * inv;
+    }
+    P.E = bE + U[S::IE];
+    P.pp = pp;
+    P.p = bp + pp;
+    P.T = T;
+    P.rv = rv;
+    P.vr = Real(0);
+}
+
+// F_j(U): rho_d u_j, rho_m u_j, rho_r (u_j - v_r d_jz), m_i u_j - rho_r v_r u_i d_jz + p' d_ij,
+//         (E + p) u_j - (c_l (T - T_ref) + |u|^2/2) rho_r v_r d_jz
+template <class S, typename Real>
+__device__ __forceinline__ void flux_dir(const Prim<S::D, S::RAIN, Real> &P, int j, Real *F) {
+    const bool vert = (j == S::VERT);
+    const Real uj = P.u[j];
+    F[0] = P.rd * uj;
+    F[1] = P.rm * uj;
+    const Real rvr = (S::RAIN && vert) ? P.rr * P.vr : Real(0);
+    if (S::RAIN) F[2] = P.rr * uj - rvr;
+#pragma unroll
+    for (int i = 0; i < S::D; ++i) {
+        Real f = P.m[i] * uj;
+        if (S::RAIN && vert) f -= rvr * P.u[i];
+        if (i == j) f += P.pp;
+        F[S::IM + i] = f;
+    }
+    Real fe = (P.E + P.p) * uj;
+    if (S::RAIN && vert) {
+        Real ke = Real(0);
+#pragma unroll
+        for (int i = 0; i < S::D; ++i) ke += P.u[i] * P.u[i];
+        fe -= (Real(kCl) * (P.T - Real(kTref)) + Real(0.5) * ke) * rvr;
+    }
+    F[S::IE] = fe;
+}
+
+// |u.n| + |v_r e_z.n| + c_m, c_m = sqrt(gamma_m p / rho)
+template <class S, typename Real>
+__device__ __forceinline__ Real wave_speed(const Prim<S::D, S::RAIN, Real> &P, int j) {
+    const Real rc = P.rm - P.rv;
+    const Real cv = Real(kCvd) * P.rd + Real(kCvv) * P.rv + Real(kCl) * (rc + P.rr);
+    const Real gam = (cv + Real(kRd) * P.rd + Real(kRv) * P.rv) / cv;
+    Real lam = fabs(P.u[j]) + sqrt(gam * P.p / P.rho);
+    if (S::RAIN && j == S::VERT) lam += fabs(P.vr);
+    return lam;
+}
+
+// trace of a nodal field on face (j, s) at face point q: sum_i l_i(s) v(line node i)
+template <class S, typename Real>
+__device__ __forceinline__ Real interp_face(const Real *v, const Real *ls, int j, int q) {
+    Real acc = Real(0);
+#pragma unroll
+    for (int i = 0; i < S::P1; ++i) acc = fma(ls[i], v[line_node<S::D, S::P1>(j, q, i)], acc);
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// k_prepare: split at every node and traces of every face
+// ---------------------------------------------------------------------------
+template <class S, typename Real>
+__device__ __forceinline__ void write_traces(const KArgs<Real> &A, const Real *s_tr, Real *trace_out) {
+    const int ne = A.M.ne;
+    for (int item = threadIdx.x; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
+        const int el = item / (S::NFACE * S::NFP1);
+        const int rem = item - el * (S::NFACE * S::NFP1);
+        const int face = rem / S::NFP1;
+        const int q = rem - face * S::NFP1;
+        const int e = blockIdx.x * S::EPB + el;
+        if (e >= ne) continue;
+        const int j = face >> 1;
+        const Real *ls = (face & 1) ? A.ref.lp : A.ref.lm;
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) {
+            const Real *v = s_tr + (size_t)fld * S::EPB * S::NP + el * S::NP;
+            trace_out[(((size_t)face * S::NTR + fld) * ne + e) * S::NFP1 + q] =
+                interp_face<S, Real>(v, ls, j, q);
+        }
+    }
+}
+
+template <class S, typename Real>
+__device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real *u, int e, int a,
+                                                Real *s_tr, int t) {
+    const size_t nodes = (size_t)A.M.ne * S::NP;
+    const size_t gi = (size_t)e * S::NP + a;
+    const int lev = vert_index<S::D>(A.M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+    const double brd = A.bnode_d[lev];
+    const double brm = A.bnode_d[A.M.nzlev_node + lev];
+    const double bE = A.bnode_d[2 * A.M.nzlev_node + lev];
+    const double bp = A.bnode_d[3 * A.M.nzlev_node + lev];
+    double msq = 0.0;
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) msq += (double)u[S::IM + j] * (double)u[S::IM + j];
+    const NodeDerived nd = node_derived<S::RAIN>(brd + (double)u[0], brm + (double)u[1],
+                                                 S::RAIN ? (double)u[2] : 0.0,
+                                                 bE + (double)u[S::IE], msq, bp, A.M);
+    if (!nd.conv) atomicAdd(&A.flags[0], 1ull);
+    if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
+    A.derived[gi] = (Real)nd.T;
+    A.derived[nodes + gi] = (Real)nd.rv;
+    A.derived[2 * nodes + gi] = (Real)nd.pp;
+    if (S::RAIN) {
+        A.derived[3 * nodes + gi] = (Real)nd.gm;
+        A.derived[4 * nodes + gi] = (Real)nd.vr;
+    }
+    const int str = S::EPB * S::NP;
+#pragma unroll
+    for (int f = 0; f < S::NF; ++f) s_tr[f * str + t] = u[f];
+    s_tr[S::NF * str + t] = (Real)nd.T;
+    s_tr[(S::NF + 1) * str + t] = (Real)nd.rv;
+    s_tr[(S::NF + 2) * str + t] = (Real)nd.pp;
+}
+
+template <class S, typename Real>
+__global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *s_tr = reinterpret_cast<Real *>(smem_raw);  // [NTR][EPB*NP]
+    const int t = threadIdx.x;
+    const int el = t / S::NP, a = t - el * S::NP;
+    const int e = blockIdx.x * S::EPB + el;
+    const bool valid = (t < S::EPB * S::NP) && (e < A.M.ne);
+    if (valid) {
+        const size_t nodes = (size_t)A.M.ne * S::NP;
+        const size_t gi = (size_t)e * S::NP + a;
+        Real u[S::NF];
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
+        split_and_store<S, Real>(A, u, e, a, s_tr, t);
+    }
+    __syncthreads();
+    write_traces<S, Real>(A, s_tr, A.trace_out);
+}
+
+// ---------------------------------------------------------------------------
+// k_stage: dU/dt of Eq. (3.2) per element, then MODE_RHS or MODE_STAGE
+// ---------------------------------------------------------------------------
+constexpr int MODE_RHS = 0;
+constexpr int MODE_STAGE = 1;
+
+template <class S, typename Real>
+constexpr size_t stage_smem_bytes() {
+    return sizeof(Real) * ((size_t)S::NTR * S::EPB * S::NP + (size_t)S::D * S::NF * S::EPB * S::NP +
+                           (size_t)S::EPB * S::NFACE * S::NF * S::NFP1);
+}
+
+template <class S, typename Real>
+__device__ __forceinline__ void load_base(const Real *tab, int nlev, int lev, Real &rd, Real &rm,
+                                          Real &E, Real &p) {
+    rd = tab[lev];
+    rm = tab[nlev + lev];
+    E = tab[2 * nlev + lev];
+    p = tab[3 * nlev + lev];
+}
+
+template <class S, typename Real, int MODE>
+__global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int STR = S::EPB * S::NP;
+    Real *s_tr = reinterpret_cast<Real *>(smem_raw);          // [NTR][STR]
+    Real *s_fl = s_tr + S::NTR * STR;                         // [D][NF][STR]
+    Real *s_fh = s_fl + S::D * S::NF * STR;                   // [EPB][NFACE][NF][NFP1]
+    const MeshData &M = A.M;
+    const int ne = M.ne;
+    const size_t nodes = (size_t)ne * S::NP;
+    const int t = threadIdx.x;
+    const int el = t / S::NP, a = t - el * S::NP;
+    const int e = blockIdx.x * S::EPB + el;
+    const bool valid = (t < STR) && (e < ne);
+
+    Real u[S::NF], R[S::NF];
+    // ---- phase 1: nodal fluxes, sources, node values for own traces
+    if (valid) {
+        const size_t gi = (size_t)e * S::NP + a;
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
+        const Real T = A.derived[gi], rv = A.derived[nodes + gi], pp = A.derived[2 * nodes + gi];
+        const int lev = vert_index<S::D>(M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        Real brd, brm, bE, bp;
+        load_base<S, Real>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
+        Prim<S::D, S::RAIN, Real> P;
+        make_prim<S, Real>(P, u, brd, brm, bE, bp, T, rv, pp);
+        if (S::RAIN) P.vr = A.derived[4 * nodes + gi];
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            Real F[S::NF];
+            flux_dir<S, Real>(P, j, F);
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) s_fl[(j * S::NF + f) * STR + t] = F[f];
+        }
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) {
+            s_tr[f * STR + t] = u[f];
+            R[f] = Real(0);
+        }
+        s_tr[S::NF * STR + t] = T;
+        s_tr[(S::NF + 1) * STR + t] = rv;
+        s_tr[(S::NF + 2) * STR + t] = pp;
+        // sources G (Eq. (2.11)): microphysics and gravity
+        if (S::RAIN) {
+            const Real gm = A.derived[3 * nodes + gi];
+            R[1] = gm;
+            R[2] = -gm;
+        }
+        const Real g = Real(M.g);
+        R[S::IM + S::VERT] = -g * (u[0] + u[1] + (S::RAIN ? u[2] : Real(0)));
+        R[S::IE] = -g * u[S::IM + S::VERT];
+    }
+    __syncthreads();
+
+    // ---- phase 2a: volume term, sum factorised: R_a += (2/h_j) sum_i dhat[a_j][i] F_j(i)
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const int aj = digit<S::D, S::P1>(a, j);
+            const int st = stride_of<S::P1>(j);
+            const int b0 = el * S::NP + a - aj * st;
+            const Real sc = Real(M.two_over_h[j]);
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) {
+                const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
+                Real acc = Real(0);
+#pragma unroll
+                for (int i = 0; i < S::P1; ++i) acc = fma(A.ref.dhat[aj][i], fl[i * st], acc);
+                R[f] = fma(sc, acc, R[f]);
+            }
+        }
+    }
+
+    // ---- phase 2b: Lax-Friedrichs flux at every face point of the CTA's elements
+    for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
+        const int el2 = item / (S::NFACE * S::NFP1);
+        const int rem = item - el2 * (S::NFACE * S::NFP1);
+        const int face = rem / S::NFP1;
+        const int q = rem - face * S::NFP1;
+        const int e2 = blockIdx.x * S::EPB + el2;
+        if (e2 >= ne) continue;
+        const int j = face >> 1;
+        const int s = (face & 1) ? 1 : -1;
+        const Real *ls = (face & 1) ? A.ref.lp : A.ref.lm;
+        Real tm[S::NTR], tp[S::NTR];
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld)
+            tm[fld] = interp_face<S, Real>(s_tr + fld * STR + el2 * S::NP, ls, j, q);
+        const int nb = neighbour<S::D>(M, e2, j, s);
+        if (nb >= 0) {
+            const int fo = 2 * j + (s > 0 ? 0 : 1);
+#pragma unroll
+            for (int fld = 0; fld < S::NTR; ++fld)
+                tp[fld] = A.trace_in[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q];
+        } else {
+            // slip wall: m+ = m- - 2 (m-.n) n, everything else copied (Section 3.2)
+#pragma unroll
+            for (int fld = 0; fld < S::NTR; ++fld) tp[fld] = tm[fld];
+            tp[S::IM + j] = -tm[S::IM + j];
+        }
+        Real brd, brm, bE, bp;
+        const int iz = vert_index<S::D>(M, e2);
+        if (j == S::VERT) {
+            load_base<S, Real>(A.bface, M.nzlev_face, iz + (s > 0 ? 1 : 0), brd, brm, bE, bp);
+        } else {
+            load_base<S, Real>(A.bnode, M.nzlev_node, iz * S::P1 + face_q_vert<S::D, S::P1>(j, q),
+                               brd, brm, bE, bp);
+        }
+        Prim<S::D, S::RAIN, Real> Pm, Pp;
+        make_prim<S, Real>(Pm, tm, brd, brm, bE, bp, tm[S::NF], tm[S::NF + 1], tm[S::NF + 2]);
+        make_prim<S, Real>(Pp, tp, brd, brm, bE, bp, tp[S::NF], tp[S::NF + 1], tp[S::NF + 2]);
+        if (S::RAIN) {
+            Pm.vr = rain_velocity<Real>(Pm.rr, Pm.rm, M);
+            Pp.vr = rain_velocity<Real>(Pp.rr, Pp.rm, M);
+        }
+        Real Fm[S::NF], Fp[S::NF];
+        flux_dir<S, Real>(Pm, j, Fm);
+        flux_dir<S, Real>(Pp, j, Fp);
+        const Real lm = wave_speed<S, Real>(Pm, j), lpp = wave_speed<S, Real>(Pp, j);
+        const Real lam = lm > lpp ? lm : lpp;
+        const Real hs = Real(0.5) * Real(s);
+        Real *out = s_fh + ((el2 * S::NFACE + face) * S::NF) * S::NFP1 + q;
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f)
+            out[f * S::NFP1] = hs * (Fm[f] + Fp[f]) + Real(0.5) * lam * (tm[f] - tp[f]);
+    }
+    __syncthreads();
+
+    // ---- phase 3: lift the face fluxes, R_a -= (2/h_j) l_a(s)/w_a Fhat(j, s)
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const int aj = digit<S::D, S::P1>(a, j);
+            const int q = face_q<S::D, S::P1>(a, j);
+            const Real sc = Real(M.two_over_h[j]);
+            const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * S::NF) * S::NFP1 + q;
+            const Real *fp = s_fh + ((el * S::NFACE + 2 * j + 1) * S::NF) * S::NFP1 + q;
+            const Real cm = sc * A.ref.liftm[aj], cp = sc * A.ref.liftp[aj];
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f)
+                R[f] -= cp * fp[f * S::NFP1] + cm * fm[f * S::NFP1];
+        }
+        const size_t gi = (size_t)e * S::NP + a;
+        if (MODE == MODE_RHS) {
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) A.Uout[f * nodes + gi] = R[f];
+        } else {
+            Real un[S::NF];
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) {
+                Real v = A.beta * u[f] + A.gdt * R[f];
+                if (A.alpha != Real(0)) v += A.alpha * A.Un[f * nodes + gi];
+                un[f] = v;
+                A.Uout[f * nodes + gi] = v;
+            }
+            split_and_store<S, Real>(A, un, e, a, s_tr, t);
+        }
+    }
+    if (MODE == MODE_STAGE) {
+        __syncthreads();
+        write_traces<S, Real>(A, s_tr, A.trace_out);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_split: derived fields only (float64 outputs)
+// ---------------------------------------------------------------------------
+template <class S, typename Real>
+__global__ void k_split(KArgs<Real> A, double *oT, double *orv, double *orc, double *opp) {
+    const size_t nodes = (size_t)A.M.ne * S::NP;
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < nodes;
+         gi += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(gi / S::NP), a = (int)(gi - (size_t)e * S::NP);
+        const int lev = vert_index<S::D>(A.M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        const int nl = A.M.nzlev_node;
+        double msq = 0.0;
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const double m = (double)A.Uin[(S::IM + j) * nodes + gi];
+            msq += m * m;
+        }
+        const double rd = A.bnode_d[lev] + (double)A.Uin[gi];
+        const double rm = A.bnode_d[nl + lev] + (double)A.Uin[nodes + gi];
+        const double rr = S::RAIN ? (double)A.Uin[2 * nodes + gi] : 0.0;
+        const double E = A.bnode_d[2 * nl + lev] + (double)A.Uin[S::IE * nodes + gi];
+        const NodeDerived nd = node_derived<false>(rd, rm, rr, E, msq, A.bnode_d[3 * nl + lev], A.M);
+        if (!nd.conv) atomicAdd(&A.flags[0], 1ull);
+        if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
+        if (oT) oT[gi] = nd.T;
+        if (orv) orv[gi] = nd.rv;
+        if (orc) orc[gi] = rm - nd.rv;
+        if (opp) opp[gi] = nd.pp;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_init_bubble: warm bubble at fixed pressure and mixing ratio
+// ---------------------------------------------------------------------------
+struct BubbleArgs {
+    double theta, qt0, H, amplitude;
+    double centre[3], radius[3];
+    const double *noise;  // device, [e][a] or NULL
+};
+
+template <class S, typename Real>
+__global__ void k_init_bubble(KArgs<Real> A, BubbleArgs B) {
+    const size_t nodes = (size_t)A.M.ne * S::NP;
+    const double kappa = kRd / kCpd;
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < nodes;
+         gi += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(gi / S::NP), a = (int)(gi - (size_t)e * S::NP);
+        int im[3];
+        elem_multi(A.M, e, im[0], im[1], im[2]);
+        double x[3] = {0.0, 0.0, 0.0};
+        double r2 = 0.0;
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const int aj = digit<S::D, S::P1>(a, j);
+            x[j] = im[j] * A.M.h[j] + (1.0 + (double)A.ref.xi[aj]) * A.M.h[j] * 0.5;
+            const double d = (x[j] - B.centre[j]) / B.radius[j];
+            r2 += d * d;
+        }
+        const double Lb = fmin(sqrt(r2), 1.0);
+        const double cb = cos(0.5 * M_PI * Lb);
+        const double thp = B.amplitude * cb * cb;
+        const int nl = A.M.nzlev_node;
+        const int lev = im[S::VERT] * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        const double pbar = A.bnode_d[3 * nl + lev];
+        const double ex = pow(pbar / kPref, kappa);
+        double T = (B.theta + thp) * ex;
+        if (B.noise) T += B.noise[gi];
+        const double qt = B.qt0 * (1.0 - x[S::VERT] / B.H);
+        // p = (rho_d R_d + rho_v R_v) T with rho_v = min(rho_vs(T), qt rho_d)
+        const double rvs = rho_vs(T, 1.0 / T);
+        double rd = pbar / (T * (kRd + qt * kRv));
+        double rv = qt * rd;
+        if (qt * rd > rvs) {
+            rd = (pbar - rvs * kRv * T) / (kRd * T);
+            rv = rvs;
+        }
+        const double rm = qt * rd;
+        const double E = (kCvd * rd + kCvv * rv + kCl * (rm - rv)) * (T - kTref) + rv * kLprime;
+        A.Uout[gi] = (Real)(rd - A.bnode_d[lev]);
+        A.Uout[nodes + gi] = (Real)(rm - A.bnode_d[nl + lev]);
+        for (int f = 2; f < S::NF; ++f) A.Uout[f * nodes + gi] = Real(0);
+        A.Uout[S::IE * nodes + gi] = (Real)(E - A.bnode_d[2 * nl + lev]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions (deterministic: fixed per-block tree, then one block in order)
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+constexpr int kNRed = 8;
+
+template <class S, typename Real>
+__global__ void __launch_bounds__(kRedThreads) k_reduce_partial(KArgs<Real> A, double *partials) {
+    __shared__ double sh[kNRed][kRedThreads];
+    const size_t nodes = (size_t)A.M.ne * S::NP;
+    double acc[kNRed];
+#pragma unroll
+    for (int r = 0; r < kNRed; ++r) acc[r] = 0.0;
+    acc[5] = 0.0;
+    acc[6] = -INFINITY;
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < nodes;
+         gi += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(gi / S::NP), a = (int)(gi - (size_t)e * S::NP);
+        double W = A.M.jac;
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) W *= (double)A.ref.w[digit<S::D, S::P1>(a, j)];
+        const int nl = A.M.nzlev_node;
+        const int lev = vert_index<S::D>(A.M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        const double urd = (double)A.Uin[gi], urm = (double)A.Uin[nodes + gi];
+        const double urr = S::RAIN ? (double)A.Uin[2 * nodes + gi] : 0.0;
+        const double rd = A.bnode_d[lev] + urd, rm = A.bnode_d[nl + lev] + urm, rr = urr;
+        const double T = (double)A.derived[gi], rv = (double)A.derived[nodes + gi];
+        const double pp = (double)A.derived[2 * nodes + gi];
+        const double rho = rd + rm + rr;
+        double msq = 0.0;
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const double m = (double)A.Uin[(S::IM + j) * nodes + gi];
+            msq += m * m;
+        }
+        acc[0] += W * urd;
+        acc[1] += W * (urm + urr);
+        acc[2] += W * (double)A.Uin[S::IM * nodes + gi];
+        acc[3] += W * (rm - rv);
+        acc[4] += W * urr;
+        const double p = A.bnode_d[3 * nl + lev] + pp;
+        const double rc = rm - rv;
+        const double cv = kCvd * rd + kCvv * rv + kCl * (rc + rr);
+        const double cm = sqrt((cv + kRd * rd + kRv * rv) / cv * p / rho);
+        const double vr = S::RAIN ? rain_velocity<double>(rr, rm, A.M) : 0.0;
+        acc[5] = fmax(acc[5], sqrt(msq) / rho + fabs(vr) + cm);
+        const double rvs = rho_vs(T, 1.0 / T);
+        acc[6] = fmax(acc[6], (rv - rvs) / rvs);
+        acc[7] += W * (double)A.Uin[S::IE * nodes + gi];
+    }
+#pragma unroll
+    for (int r = 0; r < kNRed; ++r) sh[r][threadIdx.x] = acc[r];
+    __syncthreads();
+    for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+#pragma unroll
+            for (int r = 0; r < kNRed; ++r) {
+                const double o = sh[r][threadIdx.x + off];
+                sh[r][threadIdx.x] = (r == 5 || r == 6) ? fmax(sh[r][threadIdx.x], o)
+                                                        : sh[r][threadIdx.x] + o;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int r = 0; r < kNRed; ++r) partials[(size_t)blockIdx.x * kNRed + r] = sh[r][0];
+    }
+}
+
+}  // namespace dgm

@@ -1,0 +1,131 @@
+// Host-side launchers of the device kernels, one table per (D, K, rain,
+// storage type).  Instantiated in dg_inst_*.cu so that the configurations
+// compile in parallel.
+#pragma once
+
+#include "dg_device.cuh"
+
+namespace dgm {
+
+template <typename Real>
+struct Launchers {
+    int nf, np, nfp1, nd, ntr, epb, nt;
+    size_t prep_smem, stage_smem;
+    cudaError_t (*prepare)(const KArgs<Real> &, cudaStream_t);
+    cudaError_t (*stage)(const KArgs<Real> &, int mode, cudaStream_t);
+    cudaError_t (*split)(const KArgs<Real> &, double *, double *, double *, double *, cudaStream_t);
+    cudaError_t (*init_bubble)(const KArgs<Real> &, const BubbleArgs &, cudaStream_t);
+    cudaError_t (*reduce)(const KArgs<Real> &, double *partials, int nblocks, cudaStream_t);
+};
+
+constexpr int kGridStrideBlocks = 152 * 8;
+
+inline int grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    if (b > (size_t)kGridStrideBlocks) b = kGridStrideBlocks;
+    return (int)(b > 0 ? b : 1);
+}
+
+template <class S, typename Real>
+struct Impl {
+    static constexpr size_t prep_smem = sizeof(Real) * (size_t)S::NTR * S::EPB * S::NP;
+    static constexpr size_t stage_smem = stage_smem_bytes<S, Real>();
+
+    static int blocks(const KArgs<Real> &A) { return (A.M.ne + S::EPB - 1) / S::EPB; }
+
+    static cudaError_t prepare(const KArgs<Real> &A, cudaStream_t st) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t err = cudaFuncSetAttribute(k_prepare<S, Real>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)prep_smem);
+            if (err != cudaSuccess) return err;
+            attr = true;
+        }
+        k_prepare<S, Real><<<blocks(A), S::NT, prep_smem, st>>>(A);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t stage(const KArgs<Real> &A, int mode, cudaStream_t st) {
+        static bool attr[2] = {false, false};
+        cudaError_t err = cudaSuccess;
+        if (mode == MODE_RHS) {
+            if (!attr[0]) {
+                err = cudaFuncSetAttribute(k_stage<S, Real, MODE_RHS>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem);
+                if (err != cudaSuccess) return err;
+                attr[0] = true;
+            }
+            k_stage<S, Real, MODE_RHS><<<blocks(A), S::NT, stage_smem, st>>>(A);
+        } else {
+            if (!attr[1]) {
+                err = cudaFuncSetAttribute(k_stage<S, Real, MODE_STAGE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem);
+                if (err != cudaSuccess) return err;
+                attr[1] = true;
+            }
+            k_stage<S, Real, MODE_STAGE><<<blocks(A), S::NT, stage_smem, st>>>(A);
+        }
+        return cudaGetLastError();
+    }
+
+    static cudaError_t split(const KArgs<Real> &A, double *T, double *rv, double *rc, double *pp,
+                             cudaStream_t st) {
+        const size_t nodes = (size_t)A.M.ne * S::NP;
+        k_split<S, Real><<<grid_for(nodes, 256), 256, 0, st>>>(A, T, rv, rc, pp);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t init_bubble(const KArgs<Real> &A, const BubbleArgs &B, cudaStream_t st) {
+        const size_t nodes = (size_t)A.M.ne * S::NP;
+        k_init_bubble<S, Real><<<grid_for(nodes, 256), 256, 0, st>>>(A, B);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t reduce(const KArgs<Real> &A, double *partials, int nblocks, cudaStream_t st) {
+        k_reduce_partial<S, Real><<<nblocks, kRedThreads, 0, st>>>(A, partials);
+        return cudaGetLastError();
+    }
+
+    static Launchers<Real> table() {
+        Launchers<Real> L;
+        L.nf = S::NF;
+        L.np = S::NP;
+        L.nfp1 = S::NFP1;
+        L.nd = S::ND;
+        L.ntr = S::NTR;
+        L.epb = S::EPB;
+        L.nt = S::NT;
+        L.prep_smem = prep_smem;
+        L.stage_smem = stage_smem;
+        L.prepare = &prepare;
+        L.stage = &stage;
+        L.split = &split;
+        L.init_bubble = &init_bubble;
+        L.reduce = &reduce;
+        return L;
+    }
+};
+
+// Tables defined in the instantiation units; NULL for an unsupported order.
+const Launchers<double> *launchers_d2_f64(int K, int rain);
+const Launchers<double> *launchers_d3_f64(int K, int rain);
+const Launchers<float> *launchers_d2_f32(int K, int rain);
+const Launchers<float> *launchers_d3_f32(int K, int rain);
+
+}  // namespace dgm
+
+#define DGM_DEFINE_LAUNCHERS(NAME, DIM, REAL)                                          \
+    namespace dgm {                                                                    \
+    const Launchers<REAL> *NAME(int K, int rain) {                                     \
+        static const Launchers<REAL> t[5][2] = {                                       \
+            {Impl<Shape<DIM, 1, false>, REAL>::table(), Impl<Shape<DIM, 1, true>, REAL>::table()}, \
+            {Impl<Shape<DIM, 2, false>, REAL>::table(), Impl<Shape<DIM, 2, true>, REAL>::table()}, \
+            {Impl<Shape<DIM, 3, false>, REAL>::table(), Impl<Shape<DIM, 3, true>, REAL>::table()}, \
+            {Impl<Shape<DIM, 4, false>, REAL>::table(), Impl<Shape<DIM, 4, true>, REAL>::table()}, \
+            {Impl<Shape<DIM, 5, false>, REAL>::table(), Impl<Shape<DIM, 5, true>, REAL>::table()}, \
+        };                                                                             \
+        if (K < 1 || K > 5) return nullptr;                                            \
+        return &t[K - 1][rain ? 1 : 0];                                                \
+    }                                                                                  \
+    }

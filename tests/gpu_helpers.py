@@ -1,0 +1,77 @@
+"""Shared helpers of the GPU tests: oracle problems and library contexts on the same inputs.
+
+Inputs reach both sides from the oracle's set-up functions and the seeded
+generator; nothing computed by the CUDA library is fed back to the oracle.
+"""
+import numpy as np
+
+from oracle import dg, initial
+from oracle.mesh import Mesh
+from paper_2305_13847_gb300 import dgmoist as dm
+from paper_2305_13847_gb300 import inputs
+
+BASE_KEYS = ("rho_d", "rho_m", "E", "p")
+
+
+def oracle_problem(dim, n, L, order, periodic, rain, qt0=0.015, g=9.81):
+    mesh = Mesh(dim, n, L, order, periodic)
+    node, face, extra = initial.base_tables(mesh, H=L[-1], qt0=qt0, g=g)
+    return dg.Problem(mesh, node, face, rain=rain, g=g), extra
+
+
+def library_context(prob, precision=dm.DG_FP64, stream=None):
+    mesh = prob.mesh
+    mask = sum(1 << j for j, p in enumerate(mesh.periodic[:-1]) if p)
+    cfg = dm.make_config(mesh.dim, mesh.n, mesh.L, mesh.k, mask, prob.rain, precision, prob.g,
+                         prob.rho_w or 0.0)
+    ctx = dm.dg_init_mesh(cfg, stream)
+    node = np.stack([prob.base_node[k] for k in BASE_KEYS])
+    face = np.stack([prob.base_face[k] for k in BASE_KEYS])
+    dm.dg_set_base_state(ctx, node, face)
+    return ctx
+
+
+def perturbed_state(prob, seed, amplitude=2.0, rain_amp=1e-4):
+    """Bubble state plus smooth seeded momentum, energy and rain perturbations.
+
+    The rain field dips slightly below zero in places (DG undershoot) so the
+    clipping of fractional powers is exercised.
+    """
+    mesh = prob.mesh
+    w = {"centre": [0.5 * Lj for Lj in mesh.L[:-1]] + [0.2 * mesh.L[-1]],
+         "radius": [0.2 * Lj for Lj in mesh.L]}
+    U = initial.bubble_state(prob, amplitude, w["centre"], w["radius"], H=mesh.L[-1])
+    xs = mesh.node_coords()
+    u01 = inputs.uniform(seed, np.arange(16))
+    def wave(i):
+        ph = 2 * np.pi * u01[(3 * i) % 16]
+        return np.prod([np.sin(2 * np.pi * (1 + (i + j) % 2) * xs[j] / mesh.L[j] + ph + j)
+                        for j in range(mesh.dim)], axis=0)
+    for j, fi in enumerate(prob.i_m):
+        U[fi] += 2.0 * wave(j)
+    U[prob.i_E] += 50.0 * wave(5)
+    U[prob.i_rd] += 1e-4 * wave(6)
+    if prob.rain:
+        U[prob.i_rr] = rain_amp * (0.45 + 0.55 * wave(7))
+    return U
+
+
+def to_device(U, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(U)).to(device="cuda", dtype=dtype)
+
+
+def flux_scale(prob, U):
+    """Per-field round-off scale of the right-hand side: the largest flux
+    component times the largest derivative-matrix factor (k+1)^2 (2/h).
+
+    dU/dt is a difference of such terms; float64 rounding on them is of
+    order 1e-16 of this scale per operation."""
+    mesh = prob.mesh
+    el = np.arange(mesh.Ne)
+    T, rv, pp, _ = dg.nodal_derived(prob, U, el)
+    P = dg.primitives(prob, [U[f] for f in range(prob.nf)], dg.node_base(prob, el), T, rv, pp)
+    fl = [dg.physical_flux(prob, j, P) for j in range(mesh.dim)]
+    fac = (mesh.k + 1) ** 2 * max(2.0 / h for h in mesh.h)
+    return np.array([max(np.abs(fl[j][f]).max() for j in range(mesh.dim)) * fac
+                     for f in range(prob.nf)])

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA library through its C interface against the FP64 oracle.
+
+Tolerances (float64 path):
+  * split: T and p' to 1e-12 relative / 1e-7 Pa, rho_v, rho_c to 1e-12 of rho_m
+    (both sides solve Eq. (2.8) to |dT| <= 1e-12 T plus one Newton step);
+  * right-hand side: |dU/dt_gpu - dU/dt_oracle| <= 1e-12 x the per-field flux
+    scale (largest flux component x (k+1)^2 x 2/h): the two sides sum the same
+    terms in different orders, each rounding at 1e-16 of that scale;
+  * 100 SSPRK(4,3) steps: relative L2 difference per field <= 1e-11.
+"""
+import numpy as np
+import pytest
+
+from oracle import dg, initial
+from paper_2305_13847_gb300 import dgmoist as dm
+from paper_2305_13847_gb300 import inputs
+from paper_2305_13847_gb300 import workloads
+from tests.gpu_helpers import (flux_scale, library_context, oracle_problem, perturbed_state,
+                               to_device)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = {
+    # name: (dim, n, L, order, periodic, rain)
+    "bubble2d_q3": (2, (20, 10), (20e3, 10e3), 3, (True, False), False),
+    "rain3d_q4_ragged": (3, (7, 5, 3), (14e3, 10e3, 6e3), 4, (True, True, False), True),
+    "rain2d_q2_walls": (2, (6, 5), (6e3, 5e3), 2, (False, False), True),
+    "rain3d_q3_xwall": (3, (3, 4, 2), (3e3, 4e3, 2e3), 3, (False, True, False), True),
+    "single_elem_3d_q3": (3, (1, 1, 1), (2e3, 2e3, 2e3), 3, (True, True, False), True),
+    "rain2d_q1": (2, (9, 4), (9e3, 4e3), 1, (True, False), True),
+    "rain2d_q5": (2, (4, 3), (8e3, 6e3), 5, (True, False), True),
+    "dry3d_q5": (3, (2, 2, 2), (4e3, 4e3, 4e3), 5, (True, True, False), False),
+}
+
+
+def _setup(name, seed=11):
+    dim, n, L, k, per, rain = CASES[name]
+    prob, extra = oracle_problem(dim, n, L, k, per, rain)
+    U = perturbed_state(prob, seed)
+    return prob, U
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dm.lib()
+
+
+def test_zlevels_match_oracle():
+    prob, _ = _setup("rain3d_q4_ragged")
+    ctx = library_context(prob)
+    try:
+        zn, zf = dm.dg_zlevels(ctx)
+        assert np.allclose(zn, prob.mesh.z_node_levels(), rtol=0, atol=1e-9)
+        assert np.allclose(zf, prob.mesh.z_face_levels(), rtol=0, atol=1e-9)
+    finally:
+        dm.dg_free(ctx)
+
+
+@pytest.mark.parametrize("name", ["bubble2d_q3", "rain3d_q4_ragged"])
+def test_saturation_split_parity(name):
+    prob, U = _setup(name)
+    ctx = library_context(prob)
+    try:
+        info = dm.dg_get_info(ctx)
+        Ud = to_device(U, torch.float64)
+        outs = [torch.empty(info.n_nodes, dtype=torch.float64, device="cuda") for _ in range(4)]
+        bad = dm.dg_saturation_split(ctx, Ud, *outs)
+        assert bad == 0
+        T, rv, rc, pp = (o.cpu().numpy().reshape(prob.mesh.Ne, -1) for o in outs)
+        To, rvo, ppo, bado = dg.nodal_derived(prob, U, np.arange(prob.mesh.Ne))
+        assert bado == 0
+        rm = prob.base_node["rho_m"][prob.mesh.node_level_index()] + U[prob.i_rm]
+        assert np.abs(T - To).max() <= 1e-12 * To.max()
+        assert np.abs(rv - rvo).max() <= 1e-12 * rm.max()
+        assert np.abs(rc - (rm - rvo)).max() <= 1e-12 * rm.max()
+        assert np.abs(pp - ppo).max() <= 1e-7
+        sat = (rm - rvo) > 0
+        assert sat.any() and (~sat).any()      # both branches exercised
+    finally:
+        dm.dg_free(ctx)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_parity(name):
+    prob, U = _setup(name)
+    ctx = library_context(prob)
+    try:
+        Ud = to_device(U, torch.float64)
+        out = torch.empty_like(Ud)
+        dm.dg_rhs(ctx, Ud, out)
+        torch.cuda.synchronize()
+        R = out.cpu().numpy()
+        Ro = dg.rhs(prob, U)
+        scale = flux_scale(prob, U)
+        err = np.abs(R - Ro).reshape(prob.nf, -1).max(axis=1)
+        ratio = err / scale
+        assert np.all(ratio <= 1e-12), (name, ratio, err, scale)
+        # and the tendencies are not trivially zero
+        assert np.all(np.abs(Ro).reshape(prob.nf, -1).max(axis=1) > 0)
+    finally:
+        dm.dg_free(ctx)
+
+
+def test_step_parity_bubble2d_100_steps():
+    w = inputs.workload("bubble2d_q3")
+    prob, extra = oracle_problem(w["dim"], w["n"], w["L"], w["order"], w["periodic"], w["rain"])
+    U0 = initial.bubble_state(prob, w["A"], w["centre"], w["radius"], H=w["H"])
+    dt = dg.cfl_dt(prob, U0, w["cfl"])
+    Uo = dg.run(prob, U0, dt, w["steps"])
+    ctx = library_context(prob)
+    try:
+        dm.dg_set_state(ctx, np.ascontiguousarray(U0), dm.DG_HOST)
+        dm.dg_step(ctx, dt, w["steps"])
+        Ug = np.empty_like(U0)
+        dm.dg_get_state(ctx, Ug, dm.DG_HOST)
+        for f in range(prob.nf):
+            rel = np.linalg.norm(Ug[f] - Uo[f]) / np.linalg.norm(Uo[f])
+            assert rel <= 1e-11, (dg.field_names(prob.mesh.dim, prob.rain)[f], rel)
+    finally:
+        dm.dg_free(ctx)
+
+
+def test_step_parity_rain3d_small():
+    prob, U0 = _setup("rain3d_q4_ragged")
+    dt = dg.cfl_dt(prob, U0, 0.05)
+    Uo = dg.run(prob, U0, dt, 5)
+    ctx = library_context(prob)
+    try:
+        dm.dg_set_state(ctx, np.ascontiguousarray(U0), dm.DG_HOST)
+        dm.dg_step(ctx, dt, 5)
+        Ug = np.empty_like(U0)
+        dm.dg_get_state(ctx, Ug, dm.DG_HOST)
+        for f in range(prob.nf):
+            rel = np.linalg.norm(Ug[f] - Uo[f]) / np.linalg.norm(Uo[f])
+            assert rel <= 1e-11, (f, rel)
+    finally:
+        dm.dg_free(ctx)
+
+
+@pytest.mark.parametrize("name,n", [("bubble2d_q3", None), ("rain3d_q4", (6, 5, 4))])
+def test_init_bubble_parity(name, n):
+    over = {"n": n} if n else {}
+    w = inputs.workload(name, **over)
+    prob, extra = oracle_problem(w["dim"], w["n"], w["L"], w["order"], w["periodic"], w["rain"])
+    noise = inputs.node_noise(w, prob.mesh.Ne, prob.mesh.Np)
+    Uo = initial.bubble_state(prob, w["A"], w["centre"], w["radius"], noise=noise, H=w["H"])
+    ctx = workloads.open_workload(w)
+    try:
+        Ug = np.empty_like(Uo)
+        dm.dg_get_state(ctx, Ug, dm.DG_HOST)
+        lev = prob.mesh.node_level_index()
+        for f in range(prob.nf):
+            base = {prob.i_rd: "rho_d", prob.i_rm: "rho_m", prob.i_E: "E"}.get(f)
+            scale = np.abs(prob.base_node[base]).max() if base else 1.0
+            assert np.abs(Ug[f] - Uo[f]).max() <= 1e-12 * scale, f
+    finally:
+        dm.dg_free(ctx)
+
+
+def test_reduce_matches_oracle_integrals():
+    prob, U = _setup("rain3d_q4_ragged")
+    ctx = library_context(prob)
+    try:
+        dm.dg_set_state(ctx, np.ascontiguousarray(U), dm.DG_HOST)
+        out = dm.dg_reduce(ctx)
+        T, rv, pp, _ = dg.nodal_derived(prob, U, np.arange(prob.mesh.Ne))
+        rm = prob.base_node["rho_m"][prob.mesh.node_level_index()] + U[prob.i_rm]
+        fields = [U[prob.i_rd], U[prob.i_rm] + U[prob.i_rr], U[prob.i_m[0]], rm - rv, U[prob.i_rr]]
+        for r, fld in enumerate(fields):
+            # summation-order round-off: 1e-13 of the integral of |field|
+            ref = dg.mass_integral(prob, fld)
+            assert abs(out[r] - ref) <= 1e-13 * dg.mass_integral(prob, np.abs(fld)), r
+        assert out[5] == pytest.approx(dg.max_wave_speed(prob, U), rel=1e-12)
+        assert out[6] <= 1e-12
+        assert abs(out[7] - dg.mass_integral(prob, U[prob.i_E])) <= 1e-13 * dg.mass_integral(
+            prob, np.abs(U[prob.i_E]))
+    finally:
+        dm.dg_free(ctx)
+
+
+def test_dry_mass_conserved_over_steps():
+    prob, U = _setup("rain3d_q4_ragged")
+    ctx = library_context(prob)
+    try:
+        dm.dg_set_state(ctx, np.ascontiguousarray(U), dm.DG_HOST)
+        m0 = dm.dg_reduce(ctx)
+        dm.dg_step(ctx, 0.05, 10)
+        m1 = dm.dg_reduce(ctx)
+        scale = dg.mass_integral(prob, prob.base_node["rho_d"][prob.mesh.node_level_index()])
+        assert abs(m1[0] - m0[0]) <= 1e-13 * scale
+    finally:
+        dm.dg_free(ctx)
+
+
+def test_status_and_error_paths():
+    prob, U = _setup("rain2d_q1")
+    mesh = prob.mesh
+    cfg = dm.make_config(mesh.dim, mesh.n, mesh.L, mesh.k, 1, 1)
+    ctx = dm.dg_init_mesh(cfg)
+    try:
+        Ud = to_device(U, torch.float64)
+        out = torch.empty_like(Ud)
+        with pytest.raises(dm.DGError) as ei:
+            dm.dg_rhs(ctx, Ud, out)               # no base state yet
+        assert ei.value.code == dm.DG_ESTATE
+        assert dm.dg_adjoint_step(ctx, 0.1, None, None, None) == dm.DG_ENOTIMPL
+    finally:
+        dm.dg_free(ctx)
+    # a non-finite state is reported as DG_ENONPHYS, the context stays usable
+    ctx = library_context(prob)
+    try:
+        bad = U.copy()
+        bad[prob.i_E, 0, 0] = np.nan
+        dm.dg_set_state(ctx, bad, dm.DG_HOST)
+        with pytest.raises(dm.DGError) as ei:
+            dm.dg_step(ctx, 0.01, 1)
+        assert ei.value.code == dm.DG_ENONPHYS
+        dm.dg_set_state(ctx, np.ascontiguousarray(U), dm.DG_HOST)
+        dm.dg_step(ctx, 0.01, 1)
+        st, counts = dm.dg_check_status(ctx)
+        assert st == dm.DG_OK and counts.sum() == 0
+    finally:
+        dm.dg_free(ctx)
