@@ -197,6 +197,36 @@ int dg_check_status(dg_ctx *ctx, long long counts[2]);
  * Integrals use the Gauss rule of the DG space (the diagonal mass matrix). */
 int dg_reduce(dg_ctx *ctx, double out[DG_NREDUCE]);
 
+/* Size of the fixed device scratch array used by dg_rhs_noalloc (32 MiB). */
+#define DG_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* dg_rhs without any device allocation.  No counterpart in the paper: the
+ * arithmetic is exactly dg_rhs's; only where its scratch lives differs.
+ *
+ * For callers that cannot call cudaMalloc -- a host program whose memory
+ * pool owns all device memory (a stray allocation would fragment it or
+ * escape its accounting), a latency-critical loop that cannot pay for the
+ * device synchronisation an allocation may imply, a process with a
+ * device-memory budget fixed at start-up.  No context is needed: cfg
+ * describes the mesh (precision must be DG_FP64), base_node[4][n_zlev_node]
+ * and base_face[4][n_zlev_face] are the base-state tables (device, float64,
+ * rows rho_d, rho_m, E, p, levels as in dg_zlevels), U the state and dUdt the
+ * output (device, ABI layout, float64, not overlapping).  Work goes to
+ * cuda_stream (a cudaStream_t, NULL = default stream); the call is
+ * asynchronous and allocates nothing: its scratch (derived fields, face
+ * traces, failure counters) is one file-scope device array of
+ * DG_STATIC_SCRATCH_BYTES that each GPU loading the library holds until the
+ * process exits.  The first call on a device looks up that array's address
+ * (with the device current) -- make that first call before any stream
+ * capture.  Every call shares the one array, so calls whose work overlaps on
+ * the GPU (different streams, different host threads) race; serialise them.
+ * Errors: DG_EINVAL for a bad argument, a non-float64 precision, or a mesh
+ * whose scratch (derived fields + face traces) exceeds
+ * DG_STATIC_SCRATCH_BYTES (e.g. about 1,900 elements of 3-D Q4 with rain);
+ * DG_ECUDA. */
+int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, const double *base_face,
+                   const void *U, void *dUdt, void *cuda_stream);
+
 /* Adjoint of one dg_step (not in this build: returns DG_ENOTIMPL). */
 int dg_adjoint_step(dg_ctx *ctx, double dt, const void *U_n, const double *lam_np1,
                     double *lam_n);

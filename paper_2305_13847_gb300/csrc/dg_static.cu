@@ -1,0 +1,172 @@
+// dg_rhs_noalloc: the right-hand side of dg_rhs without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a host program whose memory pool owns
+// every byte of the device (a stray allocation would fragment the pool or
+// escape its accounting), a latency-critical loop that cannot pay for the
+// implicit device synchronisation an allocation may cause, or a process that
+// fixes its device-memory budget at start-up.  This entry point serves them:
+// the caller passes the inputs and the output, and the scratch the kernels
+// need (derived fields, face traces, failure counters) lives in one
+// file-scope __device__ array of fixed size, DG_STATIC_SCRATCH_BYTES, that
+// every GPU which loads the library holds until the process exits.
+//
+// The paper has no counterpart: this is packaging, the arithmetic is the
+// same kernels dg_rhs launches (k_prepare, then k_stage in MODE_RHS).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "dg_launch.cuh"
+#include "dgmoist.h"
+
+using namespace dgm;
+
+namespace {
+
+// The scratch array.  In host code its name is only a stand-in for the
+// device symbol, never a device address: its address on each device is
+// looked up once with cudaGetSymbolAddress (below) and passed to the kernels.
+static __device__ __align__(256) unsigned char g_static_scratch[DG_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Address of the scratch array on the current device; the first call on a
+// device looks it up (with that device current) and caches it.
+int scratch_on_current_device(unsigned char **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DG_ECUDA;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return DG_ECUDA;
+        }
+        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return DG_OK;
+}
+
+size_t round_up(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Reference-element tables of the Q^k nodal basis at the Gauss points, from
+// the library's own Gauss rule (dg_gauss_legendre).
+int reference_tables(int order, RefData<double> &r) {
+    const int n = order + 1;
+    double x[6], w[6];
+    if (dg_gauss_legendre(n, x, w) != DG_OK) return DG_EINVAL;
+    std::memset(&r, 0, sizeof(r));
+    double bw[6];
+    for (int a = 0; a < n; ++a) {
+        double prod = 1.0;
+        for (int m = 0; m < n; ++m)
+            if (m != a) prod *= x[a] - x[m];
+        bw[a] = 1.0 / prod;
+    }
+    for (int a = 0; a < n; ++a) {
+        double lm = 1.0, lp = 1.0;
+        for (int m = 0; m < n; ++m) {
+            if (m == a) continue;
+            lm *= (-1.0 - x[m]) / (x[a] - x[m]);
+            lp *= (1.0 - x[m]) / (x[a] - x[m]);
+        }
+        r.lm[a] = lm;
+        r.lp[a] = lp;
+        r.liftm[a] = lm / w[a];
+        r.liftp[a] = lp / w[a];
+        r.xi[a] = x[a];
+        r.w[a] = w[a];
+    }
+    // dhat[a][i] = (w_i / w_a) l_a'(x_i); l_a'(x_i) by the barycentric formula
+    for (int i = 0; i < n; ++i) {
+        double diag = 0.0;
+        for (int a = 0; a < n; ++a) {
+            if (a == i) continue;
+            const double d = (bw[a] / bw[i]) / (x[i] - x[a]);
+            r.dhat[a][i] = w[i] / w[a] * d;
+            diag -= d;
+        }
+        r.dhat[i][i] = diag;
+    }
+    return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, const double *base_face,
+                              const void *U, void *dUdt, void *cuda_stream) {
+    if (!cfg || !base_node || !base_face || !U || !dUdt || U == dUdt) return DG_EINVAL;
+    const dg_config &g = *cfg;
+    if (g.dim != 2 && g.dim != 3) return DG_EINVAL;
+    if (g.order < 1 || g.order > 5 || (g.rain != 0 && g.rain != 1)) return DG_EINVAL;
+    if (g.precision != DG_FP64) return DG_EINVAL;
+    long long ne = 1;
+    for (int j = 0; j < g.dim; ++j) {
+        if (g.n[j] < 1 || !(g.L[j] > 0.0) || !std::isfinite(g.L[j])) return DG_EINVAL;
+        ne *= g.n[j];
+    }
+    if (!std::isfinite(g.g)) return DG_EINVAL;
+    const Launchers<double> *L =
+        g.dim == 2 ? launchers_d2_f64(g.order, g.rain) : launchers_d3_f64(g.order, g.rain);
+    if (!L) return DG_EINVAL;
+
+    // scratch: derived fields, one trace buffer, two failure counters
+    const size_t nodes = (size_t)ne * L->np;
+    const size_t derived_bytes = round_up(sizeof(double) * L->nd * nodes);
+    const size_t trace_bytes = round_up(sizeof(double) * 2 * g.dim * L->ntr * (size_t)ne * L->nfp1);
+    const size_t flag_bytes = 2 * sizeof(unsigned long long);
+    if (derived_bytes + trace_bytes + flag_bytes > (size_t)DG_STATIC_SCRATCH_BYTES) return DG_EINVAL;
+
+    unsigned char *scratch = nullptr;
+    int st = scratch_on_current_device(&scratch);
+    if (st != DG_OK) return st;
+
+    KArgs<double> A;
+    std::memset(&A, 0, sizeof(A));
+    MeshData &M = A.M;
+    const int p1 = g.order + 1;
+    for (int j = 0; j < 3; ++j) {
+        M.n[j] = j < g.dim ? g.n[j] : 1;
+        M.h[j] = j < g.dim ? g.L[j] / g.n[j] : 1.0;
+        M.two_over_h[j] = 2.0 / M.h[j];
+        M.periodic[j] = (j < g.dim - 1) ? ((g.periodic_mask >> j) & 1) : 0;
+    }
+    M.ne = (int)ne;
+    M.nzlev_node = g.n[g.dim - 1] * p1;
+    M.nzlev_face = g.n[g.dim - 1] + 1;
+    M.g = g.g;
+    M.rho_w = g.rho_w;
+    M.kvr = 130.0 * std::tgamma(4.5) / 6.0 * std::pow(M_PI * 8.0e6, -0.125);
+    M.jac = 1.0;
+    for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
+    if (reference_tables(g.order, A.ref) != DG_OK) return DG_EINVAL;
+
+    A.derived = reinterpret_cast<double *>(scratch);
+    double *trace = reinterpret_cast<double *>(scratch + derived_bytes);
+    A.flags = reinterpret_cast<unsigned long long *>(scratch + derived_bytes + trace_bytes);
+    A.bnode = base_node;
+    A.bface = base_face;
+    A.bnode_d = base_node;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    // the failure counters must start at zero; derived fields and traces are
+    // written in full by k_prepare before anything reads them
+    if (cudaMemsetAsync(A.flags, 0, flag_bytes, stream) != cudaSuccess) return DG_ECUDA;
+    A.Uin = static_cast<const double *>(U);
+    A.trace_out = trace;
+    if (L->prepare(A, stream) != cudaSuccess) return DG_ECUDA;
+    A.Un = A.Uin;
+    A.Uout = static_cast<double *>(dUdt);
+    A.trace_in = trace;
+    A.trace_out = nullptr;
+    A.alpha = 0.0;
+    A.beta = 1.0;
+    A.gdt = 1.0;
+    if (L->stage(A, MODE_RHS, stream) != cudaSuccess) return DG_ECUDA;
+    return DG_OK;
+}

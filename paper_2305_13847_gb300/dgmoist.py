@@ -80,6 +80,7 @@ SIGNATURES = [
     ("dg_reduce", _I, [_VP, _VP]),
     ("dg_adjoint_step", _I, [_VP, ctypes.c_double, _VP, _VP, _VP]),
     ("dg_strerror", ctypes.c_char_p, [_I]),
+    ("dg_rhs_noalloc", _I, [ctypes.POINTER(dg_config), _VP, _VP, _VP, _VP, _VP]),
 ]
 
 
@@ -239,6 +240,18 @@ def dg_reduce(ctx):
 
 def dg_adjoint_step(ctx, dt, U_n, lam_np1, lam_n):
     return lib().dg_adjoint_step(ctx, float(dt), _addr(U_n), _addr(lam_np1), _addr(lam_n))
+
+
+def dg_rhs_noalloc(cfg, base_node, base_face, U, dUdt, stream=None):
+    """dg_rhs without device allocation (its scratch is a fixed device array)."""
+    _check(lib().dg_rhs_noalloc(ctypes.byref(cfg), _addr(base_node), _addr(base_face), _addr(U),
+                                _addr(dUdt), _stream_handle(stream)), "dg_rhs_noalloc")
+
+
+def dg_rhs_noalloc_status(cfg, base_node, base_face, U, dUdt, stream=None):
+    """Raw status of dg_rhs_noalloc (for the size-limit check)."""
+    return lib().dg_rhs_noalloc(ctypes.byref(cfg), _addr(base_node), _addr(base_face), _addr(U),
+                                _addr(dUdt), _stream_handle(stream))
 
 
 def dg_strerror(code):
