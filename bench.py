@@ -193,6 +193,50 @@ def cpu_baseline_subprocess(timeout=600):
 # ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
+def _measure(torch, dm, ctx, info, dt, steps, warmup, stream, barrier, dist):
+    """Time `steps` SSPRK(4,3) steps (after `warmup`) with CUDA events on `stream`."""
+    dm.dg_step(ctx, dt, warmup)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    barrier()
+    evs[0].record(stream)
+    for i in range(steps):
+        dm.dg_step_async(ctx, dt, 1)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    st, counts = dm.dg_check_status(ctx)
+    if st != dm.DG_OK:
+        raise RuntimeError("step failed: %s %s" % (dm.dg_strerror(st), counts.tolist()))
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item()) / 1000.0, step_ms
+
+
+def _open(dm, workloads, inputs, name, precision, stream, mesh=None):
+    over = {"n": tuple(int(v) for v in mesh.split(","))} if mesh else {}
+    w = inputs.workload(name, **over)
+    ctx = workloads.open_workload(w, stream=stream, precision=precision)
+    info = dm.dg_get_info(ctx)
+    red = dm.dg_reduce(ctx)
+    dt = w["cfl"] * min(L / n for L, n in zip(w["L"], w["n"])) / red[5]
+    return w, ctx, info, dt
+
+
+def _roofline(info, word, t_total, steps, peak, peak_kind):
+    launch_s = t_total / (STAGES * steps)
+    bytes_per_launch = algorithmic_bytes_per_node(info.n_fields, word) * info.n_nodes
+    achieved = bytes_per_launch / launch_s / 1e9
+    return {"bound": "hbm", "kernel": "k_stage (fused RHS + SSPRK stage + next split)",
+            "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": 1000.0 * launch_s}
+
+
 def run_gb300(args):
     import torch
     from paper_2305_13847_gb300 import dgmoist as dm
@@ -212,39 +256,15 @@ def run_gb300(args):
             dist.barrier()
 
     stream = torch.cuda.current_stream()
-    w = inputs.workload(WORKLOAD)
-    ctx = workloads.open_workload(w, stream=stream, precision=args.precision)
-    info = dm.dg_get_info(ctx)
-    red = dm.dg_reduce(ctx)
-    dt = w["cfl"] * min(L / n for L, n in zip(w["L"], w["n"])) / red[5]
+    peak, peak_kind = measured_peaks()
     word = 4 if args.precision == "fp32_bulk" else 8
-
-    # warm-up (also the first split + traces of the initial state)
-    dm.dg_step(ctx, dt, args.warmup)
+    w, ctx, info, dt = _open(dm, workloads, inputs, WORKLOAD, args.precision, stream, args.mesh)
 
     sampler = ClockSampler(local)
     sampler.start()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    torch.cuda.synchronize()
-    barrier()
-    evs[0].record(stream)
-    for i in range(args.steps):
-        dm.dg_step_async(ctx, dt, 1)
-        evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    t_max, step_ms = _measure(torch, dm, ctx, info, dt, args.steps, args.warmup, stream, barrier, dist)
     clocks = sampler.stop()
-    st, counts = dm.dg_check_status(ctx)
-    if st != dm.DG_OK:
-        raise RuntimeError("step failed: %s %s" % (dm.dg_strerror(st), counts.tolist()))
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    t_local = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max = float(t_local.item()) / 1000.0
-    units = world * info.n_dofs * STAGES * args.steps
-    value = units / t_max
+    value = world * info.n_dofs * STAGES * args.steps / t_max
 
     # end to end through the C interface with host buffers: upload the state
     # from pinned memory, one step, download the state, every step
@@ -264,13 +284,25 @@ def run_gb300(args):
     if dist is not None:
         dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
     e2e_value = world * info.n_dofs * STAGES * e2e_steps / float(e2e_local.item())
-
-    # roofline of the dominant kernel (the fused stage kernel: four launches per step)
-    peak, peak_kind = measured_peaks()
-    launch_s = (total_ms / 1000.0) / (STAGES * args.steps)
-    bytes_per_launch = algorithmic_bytes_per_node(info.n_fields, word) * info.n_nodes
-    achieved = bytes_per_launch / launch_s / 1e9
+    roof = _roofline(info, word, t_max, args.steps, peak, peak_kind)
     dm.dg_free(ctx)
+    del host
+
+    # the FP32-bulk form: its own workload (128x128x64, Q3) and the same mesh
+    extra = {}
+    if args.precision == "fp64" and not args.no_fp32:
+        for key, name, mesh in (("fp32_bulk", "rain3d_q3_fp32", None),
+                                ("fp32_bulk_same_mesh", WORKLOAD, args.mesh)):
+            w2, ctx2, info2, dt2 = _open(dm, workloads, inputs, name, "fp32_bulk", stream, mesh)
+            t2, sm2 = _measure(torch, dm, ctx2, info2, dt2, args.steps, args.warmup, stream, barrier,
+                               dist)
+            extra[key] = {
+                "workload": "%s: %s hex, Q%d, 7 fields, %d DOFs, float32 state and flux, float64 split"
+                            % (name, "x".join(map(str, w2["n"])), w2["order"], info2.n_dofs),
+                "value": world * info2.n_dofs * STAGES * args.steps / t2, "unit": UNIT,
+                "ms_per_step": 1000.0 * t2 / args.steps,
+                "roofline": _roofline(info2, 4, t2, args.steps, peak, peak_kind)}
+            dm.dg_free(ctx2)
 
     if rank == 0:
         line = {
@@ -279,21 +311,20 @@ def run_gb300(args):
             "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if word == 4 else "f64", "data": "synthetic",
-            "config": {"workload": "rain3d_q4: 3-D warm-rain bubble, 64x64x32 hex, Q4 (125 nodes/elem), "
-                                   "7 fields, %d DOFs, dt %.4g s" % (info.n_dofs, dt),
+            "config": {"workload": "rain3d_q4: 3-D warm-rain bubble, %s hex, Q4 (125 nodes/elem), "
+                                   "7 fields, %d DOFs, dt %.4g s" % ("x".join(map(str, w["n"])),
+                                                                    info.n_dofs, dt),
                        "precision": args.precision, "l2": "inputs larger than L2 (state %.0f MB)"
                        % (info.state_bytes / 1e6), "parallelism": "replicas" if world > 1 else "1 GPU"},
             "step_ms": {"median": float(np.median(step_ms)), "min": float(np.min(step_ms)),
                         "max": float(np.max(step_ms))},
-            "roofline": {"bound": "hbm", "kernel": "k_stage (fused RHS + SSPRK stage + next split)",
-                         "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "algorithmic_bytes_per_launch": bytes_per_launch},
+            "roofline": roof,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(info.state_bytes),
                     "d2h_bytes_per_step": int(info.state_bytes), "steps": e2e_steps},
             "gpu_launches": STAGES * args.steps,
         }
+        line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_subprocess()
         print(json.dumps(line))
@@ -309,6 +340,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurements")
+    ap.add_argument("--mesh", default=None,
+                    help="override the element counts, e.g. 40,40,20 (profiling runs only)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -205,6 +205,7 @@ struct dg_ctx {
     void *bnode_r = nullptr, *bface_r = nullptr;
     unsigned long long *flags = nullptr;
     double *partials = nullptr;
+    double *rvs_tab = nullptr;
     int nred = 0;
     std::vector<double> z_node, z_face;
     bool base_set = false, state_set = false, derived_valid = false;
@@ -226,6 +227,7 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     A.bnode = (const Real *)c->bnode_r;
     A.bface = (const Real *)c->bface_r;
     A.bnode_d = c->bnode_d;
+    A.rvs_tab = c->rvs_tab;
     A.flags = c->flags;
     return A;
 }
@@ -266,7 +268,7 @@ int stage(dg_ctx *c, int mode, const void *Uin, const void *Un, void *Uout, int 
 
 void release(dg_ctx *c) {
     void *ptrs[] = {c->U[0], c->U[1], c->derived, c->trace[0], c->trace[1], c->bnode_d,
-                    c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials};
+                    c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -425,8 +427,13 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     }
     if (st == DG_OK) st = alloc(c, (void **)&c->flags, sizeof(unsigned long long) * 2);
     if (st == DG_OK) st = alloc(c, (void **)&c->partials, sizeof(double) * kNRed * c->nred);
+    if (st == DG_OK) st = alloc(c, (void **)&c->rvs_tab, sizeof(double) * 2 * kTabN);
     if (st == DG_OK && cudaMemsetAsync(c->flags, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = DG_ECUDA;
+    if (st == DG_OK) {
+        k_fill_rvs_table<<<(kTabN + 255) / 256, 256, 0, c->stream>>>(c->rvs_tab);
+        if (cudaGetLastError() != cudaSuccess) st = DG_ECUDA;
+    }
     if (st != DG_OK) {
         release(c);
         delete c;

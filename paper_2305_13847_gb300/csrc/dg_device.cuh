@@ -21,6 +21,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "dg_math.cuh"
+
 namespace dgm {
 
 // ---------------------------------------------------------------------------
@@ -92,6 +94,7 @@ struct KArgs {
     const Real *bnode;     // base at node levels [4][nzlev_node]: rho_d, rho_m, E, p
     const Real *bface;     // base at face levels [4][nzlev_face]
     const double *bnode_d; // float64 copy for the split
+    const double *rvs_tab; // rho_vs table: [kTabN][2] = (rho_vs(T_i), 1/T_i)
     Real alpha, beta, gdt; // Uout = alpha Un + beta Uin + gdt dU/dt
     unsigned long long *flags;  // [0] Newton failures, [1] non-physical nodes
 };
@@ -190,62 +193,138 @@ __device__ __forceinline__ double rho_vs(double T, double invT) {
     return kRvs0 * exp((kEsA - 1.0) * log(T * kInvTref) + kEsB * (kInvTref - invT));
 }
 
+// float32 rho_vs for the pre-solve: rho_vs(T_ref) 2^((a-1) log2(T/T_ref) + b log2(e) (1/T_ref - 1/T))
+__device__ __forceinline__ float rho_vs_f32(float T) {
+    const float l2e = 1.4426950408889634f;
+    return (float)kRvs0 * exp2f((float)(kEsA - 1.0) * __log2f(T * (float)kInvTref) +
+                                (float)kEsB * l2e * ((float)kInvTref - __frcp_rn(T)));
+}
+
+// float64 rho_vs(T) from the table (see dg_math.cuh); also returns 1/T.
+// Outside the table range the closed form is evaluated directly.
+__device__ __forceinline__ double rho_vs_tab(double T, const double *__restrict__ tab, double &invT) {
+    if (!(T >= kTabT0 && T <= kTabT1 - 1.0)) {
+        invT = 1.0 / T;
+        return rho_vs(T, invT);
+    }
+    const int i = __double2int_rn((T - kTabT0) * kTabInvStep);
+    const double2 ent = __ldg(reinterpret_cast<const double2 *>(tab) + i);
+    const double Ti = kTabT0 + (double)i * (1.0 / kTabInvStep);
+    const double s = (T - Ti) * ent.y;
+    // ln(1+s) and s/(1+s) to s^5 (truncation < 1e-20 for |s| <= 4.2e-4)
+    const double l1 = s * fma(s, fma(s, fma(s, fma(s, 0.2, -0.25), 1.0 / 3.0), -0.5), 1.0);
+    const double q = s * fma(s, fma(s, fma(s, fma(s, 1.0, -1.0), 1.0), -1.0), 1.0);
+    invT = fma(-ent.y, q, ent.y);                       // 1/T = (1/T_i)(1 - s/(1+s))
+    const double z = fma(kEsA - 1.0, l1, kEsB * ent.y * q);
+    // exp(z) for |z| <= 0.024 to z^7 (truncation < 3e-18)
+    const double ez = fma(z, fma(z, fma(z, fma(z, fma(z, fma(z, fma(z, 1.0 / 5040.0, 1.0 / 720.0),
+        1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0), 1.0);
+    return ent.x * ez;
+}
+
 struct SplitResult {
     double T, rv, deficit;  // deficit = rho_vs(T) - rho_v (0 at saturation)
     bool converged;
 };
 
 // Eq. (2.8): T, rho_v from totals rho_d, rho_m, rho_r and internal energy re.
-// Unsaturated candidate in closed form; if supersaturated, Newton on
-// H(T) = (c_vd rd + c_vv rvs + c_l (rm - rvs + rr)) (T - T_ref) + rvs L' - re
-// from T_u.  H is increasing and convex, so Newton from T_u overshoots once
-// and then decreases monotonically to the root; a bracket guards against
-// rounding.  Stop when |dT| <= 1e-12 T, after one more step.
-__device__ __forceinline__ SplitResult split_point(double rd, double rm, double rr, double re) {
+// Unsaturated candidate T_u in closed form; if rho_m > rho_vs(T_u) the vapour
+// is saturated and T solves
+//   H(T) = (c_vd rd + c_vv rvs + c_l (rm - rvs + rr)) (T - T_ref) + rvs L' - re = 0,
+// H increasing and convex.  Newton's method runs first in float32 from T_u
+// (to ~1e-7), then two float64 Newton steps reach float64 rounding; if the
+// last float64 step is not below 1e-10 T the float64 iteration continues
+// (bracketed, cap kMaxNewton).  The saturation test is decided in float32
+// unless rho_m is within 1e-5 of rho_vs; the float64 value is always formed
+// when the caller needs the evaporation deficit.
+template <bool NEED_DEFICIT>
+__device__ __forceinline__ SplitResult split_point(double rd, double rm, double rr, double re,
+                                                   const double *__restrict__ tab) {
     SplitResult r;
     const double cu = kCvd * rd + kCvv * rm + kCl * rr;
-    const double tu = kTref + (re - rm * kLprime) / cu;
-    const double rvs_u = rho_vs(tu, 1.0 / tu);
-    if (!(rm > rvs_u)) {
+    const double tu = kTref + (re - rm * kLprime) * recip(cu);
+    const float rvs32 = rho_vs_f32((float)tu);
+    bool sat;
+    double rvs_u = 0.0, invt;
+    if (NEED_DEFICIT || fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tu > 0.0)) {
+        rvs_u = rho_vs_tab(tu, tab, invt);
+        sat = rm > rvs_u;
+    } else {
+        sat = rm > (double)rvs32;
+    }
+    if (!sat) {
         r.T = tu;
         r.rv = rm;
-        r.deficit = rvs_u - rm;
+        r.deficit = NEED_DEFICIT ? rvs_u - rm : 0.0;
         r.converged = true;
         return r;
     }
-    double t = tu, lo = tu, hi = INFINITY;
-    bool extra = false, done = false;
     const double cdry = kCvd * rd + kCl * (rm + rr);
+    // float32 pre-solve
+    {
+        const float cdf = (float)cdry, ref = (float)re, tref = (float)kTref;
+        const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
+        const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
+        float t = (float)tu;
+        for (int it = 0; it < 30; ++it) {
+            const float rvs = rho_vs_f32(t);
+            const float it_ = __frcp_rn(t);
+            const float drvs = rvs * it_ * (am1 + bb * it_);
+            const float heat = cdf + clv * rvs;
+            const float h = heat * (t - tref) + rvs * lp - ref;
+            const float dh = heat + (clv * (t - tref) + lp) * drvs;
+            const float dt = h / dh;
+            t -= dt;
+            if (fabsf(dt) <= 2e-6f * t) break;
+        }
+        r.T = (double)t;
+    }
+    // float64 Newton steps
+    double t = (r.T > tu) ? r.T : tu;
+    double lo = tu, hi = INFINITY, rvs = 0.0, drvs = 0.0, step = INFINITY;
+    bool done = false;
     for (int it = 0; it < kMaxNewton; ++it) {
-        const double invt = 1.0 / t;
-        const double rvs = rho_vs(t, invt);
-        const double drvs = rvs * invt * ((kEsA - 1.0) + kEsB * invt);
-        const double heat = cdry + (kCvv - kCl) * rvs;
-        const double h = heat * (t - kTref) + rvs * kLprime - re;
-        const double dh = heat + ((kCvv - kCl) * (t - kTref) + kLprime) * drvs;
+        rvs = rho_vs_tab(t, tab, invt);
+        drvs = rvs * invt * fma(kEsB, invt, kEsA - 1.0);
+        const double heat = fma(kCvv - kCl, rvs, cdry);
+        const double h = fma(heat, t - kTref, fma(rvs, kLprime, -re));
+        const double dh = fma(fma(kCvv - kCl, t - kTref, kLprime), drvs, heat);
         if (h < 0.0) lo = t;
         if (h > 0.0) hi = t;
-        double tn = t - h / dh;
+        double tn = t - h * recip(dh);
         if (!(tn >= lo && tn <= hi)) tn = isinf(hi) ? t + 10.0 : 0.5 * (lo + hi);
-        const bool done_now = extra || (h == 0.0);
-        if (fabs(tn - t) <= kNewtonTol * fabs(tn)) extra = true;
+        step = tn - t;
         t = tn;
-        if (done_now) { done = true; break; }
+        if (it >= 1 && fabs(step) <= 1e-10 * t) {
+            done = true;
+            break;
+        }
     }
     r.T = t;
-    r.rv = rho_vs(t, 1.0 / t);
+    // rho_vs at the final T from the last evaluation: the step is below
+    // 1e-10 T, so the neglected second-order term is below 1e-20 relative
+    r.rv = fma(drvs, step, rvs);
     r.deficit = 0.0;
     r.converged = done;
     return r;
 }
 
-// v_r = v0 Gamma(4.5)/6 (pi rho_w N0)^(-1/8) rho_r^(1/8) (Section 2.1)
-template <typename Real>
-__device__ __forceinline__ Real rain_velocity(Real rr, Real rm, const MeshData &M) {
-    const Real rrp = rr > Real(0) ? rr : Real(0);
-    const Real rw = M.rho_w > 0.0 ? Real(M.rho_w) : rm + rr;
-    if (!(rrp > Real(0)) || !(rw > Real(0))) return Real(0);
-    return Real(M.kvr) * pow(rrp / rw, Real(0.125));
+// v_r = v0 Gamma(4.5)/6 (pi rho_w N0)^(-1/8) rho_r^(1/8) = kvr (rho_r / rho_w)^(1/8) (Section 2.1)
+__device__ __forceinline__ double rain_velocity(double rr, double rm, const MeshData &M) {
+    const double rrp = rr > 0.0 ? rr : 0.0;
+    const double rw = M.rho_w > 0.0 ? M.rho_w : rm + rr;
+    if (!(rrp > 0.0) || !(rw > 0.0)) return 0.0;
+    const double t = rrp * recip(rw);
+    const double y = inv_root8(t);                          // t^(-1/8)
+    const double y2 = y * y, y4 = y2 * y2;
+    return M.kvr * t * (y4 * y2 * y);                       // t^(1/8) = t y^7
+}
+
+__device__ __forceinline__ float rain_velocity(float rr, float rm, const MeshData &M) {
+    const float rrp = rr > 0.0f ? rr : 0.0f;
+    const float rw = M.rho_w > 0.0 ? (float)M.rho_w : rm + rr;
+    if (!(rrp > 0.0f) || !(rw > 0.0f)) return 0.0f;
+    return (float)M.kvr * exp2f(0.125f * __log2f(rrp * __frcp_rn(rw)));
 }
 
 // Per-node split plus the node-local quantities the next operator needs.
@@ -256,11 +335,12 @@ struct NodeDerived {
 
 template <bool RAIN>
 __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double rr, double E,
-                                                    double msq, double pbar, const MeshData &M) {
+                                                    double msq, double pbar, const MeshData &M,
+                                                    const double *__restrict__ tab) {
     NodeDerived o;
     const double rho = rd + rm + rr;
-    const double re = E - 0.5 * msq / rho;
-    const SplitResult s = split_point(rd, rm, rr, re);
+    const double re = E - 0.5 * msq * recip(rho);
+    const SplitResult s = split_point<RAIN>(rd, rm, rr, re, tab);
     o.T = s.T;
     o.rv = s.rv;
     o.conv = s.converged;
@@ -269,16 +349,116 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
     o.gm = 0.0;
     o.vr = 0.0;
     if (RAIN) {
-        // Eq. (2.4): all rain powers from x = max(rho_r,0)^(1/16)
+        // Eq. (2.4): the rain powers from x = max(rho_r, 0)^(1/16) = r y^15, y = r^(-1/16)
         const double rrp = rr > 0.0 ? rr : 0.0;
-        const double x = rrp > 0.0 ? pow(rrp, 0.0625) : 0.0;
+        double x = 0.0;
+        if (rrp > 0.0) {
+            const double y = inv_root16(rrp);
+            const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+            x = rrp * (y8 * y4 * y2 * y);
+        }
         const double x2 = x * x, x3 = x2 * x, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
         const double rc = rm - s.rv;
         const double s_ev = (kSevA - kSevB * (s.T - kTref)) * (1.0 + kSevC * x3) * s.deficit * x8;
         const double s_au = kSau * (rc > 0.0 ? rc : 0.0);
         const double s_ac = kSac * rc * x14;
         o.gm = s_ev - s_au - s_ac;
-        o.vr = rain_velocity<double>(rr, rm, M);
+        o.vr = rain_velocity(rr, rm, M);
+    }
+    return o;
+}
+
+// Split of the FP32-bulk form: the state is float32; the temperature recovery
+// from the total energy (the cancellation-prone balance E - |m|^2/(2 rho) -
+// rho_m L') and the Newton solve for the saturated vapour density run in
+// float64.  Newton iterates in float32 from T_u to ~1e-7, then one float64
+// Newton correction with the float64 rho_vs (table) gives T to ~1e-13 and
+// rho_v = rho_vs(T) to the same order, so vapour is never supersaturated by
+// more than ~1e-12 relative.  Rain sources and v_r are bulk (float32)
+// arithmetic.
+template <bool RAIN>
+__device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im, int ie, int d,
+                                                         double brd, double brm, double bE,
+                                                         double pbar, const MeshData &M,
+                                                         const double *__restrict__ tab) {
+    NodeDerived o;
+    const double rd = brd + (double)u[0];
+    const double rm = brm + (double)u[1];
+    const double rr = RAIN ? (double)u[2] : 0.0;
+    const double E = bE + (double)u[ie];
+    float msq = 0.0f;
+    for (int j = 0; j < d; ++j) msq = fmaf(u[im + j], u[im + j], msq);
+    const float rhof = (float)(rd + rm + rr);
+    const double re = E - (double)(0.5f * msq * __frcp_rn(rhof));
+    const double cu = kCvd * rd + kCvv * rm + kCl * rr;
+    const double tu = kTref + fma(-rm, kLprime, re) * recip(cu);
+    const float tuf = (float)tu;
+    const float rvs32 = rho_vs_f32(tuf);
+    bool sat;
+    if (fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tu > 0.0)) {
+        double it_;
+        sat = rm > rho_vs_tab(tu, tab, it_);
+    } else {
+        sat = rm > (double)rvs32;
+    }
+    float deficit = 0.0f;
+    o.conv = true;
+    if (!sat) {
+        o.T = tu;
+        o.rv = rm;
+        deficit = rvs32 - (float)rm;
+    } else {
+        const double cdry = kCvd * rd + kCl * (rm + rr);
+        const float cdf = (float)cdry, ref = (float)re, tref = (float)kTref;
+        const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
+        const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
+        float t = tuf;
+        bool conv = false;
+        for (int it = 0; it < 40; ++it) {
+            const float rvs = rho_vs_f32(t);
+            const float it_ = __frcp_rn(t);
+            const float drvs = rvs * it_ * (am1 + bb * it_);
+            const float heat = cdf + clv * rvs;
+            const float h = heat * (t - tref) + rvs * lp - ref;
+            const float dh = heat + (clv * (t - tref) + lp) * drvs;
+            const float dt = h / dh;
+            t -= dt;
+            if (fabsf(dt) <= 1e-6f * t) {
+                conv = true;
+                break;
+            }
+        }
+        // one float64 Newton correction
+        double invt;
+        const double T32 = (double)t;
+        const double rvs = rho_vs_tab(T32, tab, invt);
+        const double heat = fma(kCvv - kCl, rvs, cdry);
+        const double h = fma(heat, T32 - kTref, fma(rvs, kLprime, -re));
+        const float rvsf = (float)rvs, itf = (float)invt;
+        const float drvs = rvsf * itf * (am1 + bb * itf);
+        const float dh = (float)heat + (clv * (t - tref) + lp) * drvs;
+        const float dT = (float)h / dh;
+        o.T = T32 - (double)dT;
+        o.rv = fma(-(double)drvs, (double)dT, rvs);
+        o.conv = conv && fabsf(dT) <= 1e-4f * t;
+    }
+    o.pp = (rd * kRd + o.rv * kRv) * o.T - pbar;
+    const double rho = rd + rm + rr;
+    o.phys = (rd > 0.0) && (rho > 0.0) && (o.T > 50.0) && (o.T < 1000.0) && isfinite(o.pp);
+    o.gm = 0.0;
+    o.vr = 0.0;
+    if (RAIN) {
+        const float rrf = u[2] > 0.0f ? u[2] : 0.0f;
+        const float x = rrf > 0.0f ? exp2f(0.0625f * __log2f(rrf)) : 0.0f;
+        const float x2 = x * x, x3 = x2 * x, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
+        const float rc = (float)(rm - o.rv);
+        const float Tf = (float)o.T;
+        const float s_ev = ((float)kSevA - (float)kSevB * (Tf - (float)kTref)) *
+                           (1.0f + (float)kSevC * x3) * deficit * x8;
+        const float s_au = (float)kSau * (rc > 0.0f ? rc : 0.0f);
+        const float s_ac = (float)kSac * rc * x14;
+        o.gm = (double)(s_ev - s_au - s_ac);
+        o.vr = (double)rain_velocity(u[2], (float)rm, M);
     }
     return o;
 }
@@ -288,7 +468,7 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
 // ---------------------------------------------------------------------------
 template <int D, bool RAIN, typename Real>
 struct Prim {
-    Real rd, rm, rr, rho, E, p, pp, T, rv, vr;
+    Real rd, rm, rr, rho, irho, E, p, pp, T, rv, vr;
     Real m[D], u[D];
 };
 
@@ -299,7 +479,8 @@ __device__ __forceinline__ void make_prim(Prim<S::D, S::RAIN, Real> &P, const Re
     P.rm = brm + U[1];
     P.rr = S::RAIN ? U[2] : Real(0);
     P.rho = P.rd + P.rm + P.rr;
-    const Real inv = Real(1) / P.rho;
+    const Real inv = recip(P.rho);
+    P.irho = inv;
 #pragma unroll
     for (int j = 0; j < S::D; ++j) {
         P.m[j] = U[S::IM + j];
@@ -340,14 +521,15 @@ __device__ __forceinline__ void flux_dir(const Prim<S::D, S::RAIN, Real> &P, int
     F[S::IE] = fe;
 }
 
-// |u.n| + |v_r e_z.n| + c_m, c_m = sqrt(gamma_m p / rho)
-template <class S, typename Real>
-__device__ __forceinline__ Real wave_speed(const Prim<S::D, S::RAIN, Real> &P, int j) {
+// |u.n| + |v_r e_z.n| + c_m, c_m = sqrt(gamma_m p / rho), gamma_m = (c_v + R)/c_v
+// (c_v, R per unit volume: c_vd rho_d + c_vv rho_v + c_l (rho_c + rho_r), R_d rho_d + R_v rho_v)
+template <class S, int J, typename Real>
+__device__ __forceinline__ Real wave_speed(const Prim<S::D, S::RAIN, Real> &P) {
     const Real rc = P.rm - P.rv;
     const Real cv = Real(kCvd) * P.rd + Real(kCvv) * P.rv + Real(kCl) * (rc + P.rr);
-    const Real gam = (cv + Real(kRd) * P.rd + Real(kRv) * P.rv) / cv;
-    Real lam = fabs(P.u[j]) + sqrt(gam * P.p / P.rho);
-    if (S::RAIN && j == S::VERT) lam += fabs(P.vr);
+    const Real cm2 = (cv + Real(kRd) * P.rd + Real(kRv) * P.rv) * P.p * P.irho * recip(cv);
+    Real lam = fabs(P.u[J]) + sqrt_nr(cm2);
+    if (S::RAIN && J == S::VERT) lam += fabs(P.vr);
     return lam;
 }
 
@@ -384,22 +566,32 @@ __device__ __forceinline__ void write_traces(const KArgs<Real> &A, const Real *s
     }
 }
 
+template <class S>
+__device__ __forceinline__ NodeDerived derive_node(const double *u, const KArgs<double> &A, int lev) {
+    const int nl = A.M.nzlev_node;
+    double msq = 0.0;
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) msq += u[S::IM + j] * u[S::IM + j];
+    return node_derived<S::RAIN>(A.bnode_d[lev] + u[0], A.bnode_d[nl + lev] + u[1],
+                                 S::RAIN ? u[2] : 0.0, A.bnode_d[2 * nl + lev] + u[S::IE], msq,
+                                 A.bnode_d[3 * nl + lev], A.M, A.rvs_tab);
+}
+
+template <class S>
+__device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<float> &A, int lev) {
+    const int nl = A.M.nzlev_node;
+    return node_derived_bulk<S::RAIN>(u, S::IM, S::IE, S::D, A.bnode_d[lev], A.bnode_d[nl + lev],
+                                      A.bnode_d[2 * nl + lev], A.bnode_d[3 * nl + lev], A.M,
+                                      A.rvs_tab);
+}
+
 template <class S, typename Real>
 __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real *u, int e, int a,
                                                 Real *s_tr, int t) {
     const size_t nodes = (size_t)A.M.ne * S::NP;
     const size_t gi = (size_t)e * S::NP + a;
     const int lev = vert_index<S::D>(A.M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
-    const double brd = A.bnode_d[lev];
-    const double brm = A.bnode_d[A.M.nzlev_node + lev];
-    const double bE = A.bnode_d[2 * A.M.nzlev_node + lev];
-    const double bp = A.bnode_d[3 * A.M.nzlev_node + lev];
-    double msq = 0.0;
-#pragma unroll
-    for (int j = 0; j < S::D; ++j) msq += (double)u[S::IM + j] * (double)u[S::IM + j];
-    const NodeDerived nd = node_derived<S::RAIN>(brd + (double)u[0], brm + (double)u[1],
-                                                 S::RAIN ? (double)u[2] : 0.0,
-                                                 bE + (double)u[S::IE], msq, bp, A.M);
+    const NodeDerived nd = derive_node<S>(u, A, lev);
     if (!nd.conv) atomicAdd(&A.flags[0], 1ull);
     if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
     A.derived[gi] = (Real)nd.T;
@@ -456,6 +648,60 @@ __device__ __forceinline__ void load_base(const Real *tab, int nlev, int lev, Re
     rm = tab[nlev + lev];
     E = tab[2 * nlev + lev];
     p = tab[3 * nlev + lev];
+}
+
+// Lax-Friedrichs flux F_n = {{F}}.n + Lambda/2 [[U]] (Section 3.2) at face point q of
+// face (J, s) of element e2, in the outward direction s e_J; own trace from
+// shared memory, neighbour trace from the trace buffer, slip-wall ghost state
+// m+ = m- - 2 (m-.n) n with everything else copied.
+template <class S, typename Real, int J>
+__device__ __forceinline__ void face_point(const KArgs<Real> &A, const Real *s_tr, Real *s_fh, int el2,
+                                           int face, int q, int e2) {
+    constexpr int STR = S::EPB * S::NP;
+    const MeshData &M = A.M;
+    const int ne = M.ne;
+    const int s = (face & 1) ? 1 : -1;
+    const Real *ls = (face & 1) ? A.ref.lp : A.ref.lm;
+    Real tm[S::NTR], tp[S::NTR];
+#pragma unroll
+    for (int fld = 0; fld < S::NTR; ++fld)
+        tm[fld] = interp_face<S, Real>(s_tr + fld * STR + el2 * S::NP, ls, J, q);
+    const int nb = neighbour<S::D>(M, e2, J, s);
+    if (nb >= 0) {
+        const int fo = 2 * J + (s > 0 ? 0 : 1);
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld)
+            tp[fld] = A.trace_in[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q];
+    } else {
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) tp[fld] = tm[fld];
+        tp[S::IM + J] = -tm[S::IM + J];
+    }
+    Real brd, brm, bE, bp;
+    const int iz = vert_index<S::D>(M, e2);
+    if (J == S::VERT) {
+        load_base<S, Real>(A.bface, M.nzlev_face, iz + (s > 0 ? 1 : 0), brd, brm, bE, bp);
+    } else {
+        load_base<S, Real>(A.bnode, M.nzlev_node, iz * S::P1 + face_q_vert<S::D, S::P1>(J, q), brd,
+                           brm, bE, bp);
+    }
+    Prim<S::D, S::RAIN, Real> Pm, Pp;
+    make_prim<S, Real>(Pm, tm, brd, brm, bE, bp, tm[S::NF], tm[S::NF + 1], tm[S::NF + 2]);
+    make_prim<S, Real>(Pp, tp, brd, brm, bE, bp, tp[S::NF], tp[S::NF + 1], tp[S::NF + 2]);
+    if (S::RAIN) {
+        Pm.vr = rain_velocity(Pm.rr, Pm.rm, M);
+        Pp.vr = rain_velocity(Pp.rr, Pp.rm, M);
+    }
+    Real Fm[S::NF], Fp[S::NF];
+    flux_dir<S, Real>(Pm, J, Fm);
+    flux_dir<S, Real>(Pp, J, Fp);
+    const Real lm = wave_speed<S, J, Real>(Pm), lpp = wave_speed<S, J, Real>(Pp);
+    const Real lam = lm > lpp ? lm : lpp;
+    const Real hs = Real(0.5) * Real(s);
+    Real *out = s_fh + ((el2 * S::NFACE + face) * S::NF) * S::NFP1 + q;
+#pragma unroll
+    for (int f = 0; f < S::NF; ++f)
+        out[f * S::NFP1] = hs * (Fm[f] + Fp[f]) + Real(0.5) * lam * (tm[f] - tp[f]);
 }
 
 template <class S, typename Real, int MODE>
@@ -540,50 +786,11 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
         const int q = rem - face * S::NFP1;
         const int e2 = blockIdx.x * S::EPB + el2;
         if (e2 >= ne) continue;
-        const int j = face >> 1;
-        const int s = (face & 1) ? 1 : -1;
-        const Real *ls = (face & 1) ? A.ref.lp : A.ref.lm;
-        Real tm[S::NTR], tp[S::NTR];
-#pragma unroll
-        for (int fld = 0; fld < S::NTR; ++fld)
-            tm[fld] = interp_face<S, Real>(s_tr + fld * STR + el2 * S::NP, ls, j, q);
-        const int nb = neighbour<S::D>(M, e2, j, s);
-        if (nb >= 0) {
-            const int fo = 2 * j + (s > 0 ? 0 : 1);
-#pragma unroll
-            for (int fld = 0; fld < S::NTR; ++fld)
-                tp[fld] = A.trace_in[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q];
-        } else {
-            // slip wall: m+ = m- - 2 (m-.n) n, everything else copied (Section 3.2)
-#pragma unroll
-            for (int fld = 0; fld < S::NTR; ++fld) tp[fld] = tm[fld];
-            tp[S::IM + j] = -tm[S::IM + j];
+        switch (face >> 1) {
+            case 0: face_point<S, Real, 0>(A, s_tr, s_fh, el2, face, q, e2); break;
+            case 1: face_point<S, Real, 1>(A, s_tr, s_fh, el2, face, q, e2); break;
+            default: face_point<S, Real, (S::D == 3 ? 2 : 1)>(A, s_tr, s_fh, el2, face, q, e2); break;
         }
-        Real brd, brm, bE, bp;
-        const int iz = vert_index<S::D>(M, e2);
-        if (j == S::VERT) {
-            load_base<S, Real>(A.bface, M.nzlev_face, iz + (s > 0 ? 1 : 0), brd, brm, bE, bp);
-        } else {
-            load_base<S, Real>(A.bnode, M.nzlev_node, iz * S::P1 + face_q_vert<S::D, S::P1>(j, q),
-                               brd, brm, bE, bp);
-        }
-        Prim<S::D, S::RAIN, Real> Pm, Pp;
-        make_prim<S, Real>(Pm, tm, brd, brm, bE, bp, tm[S::NF], tm[S::NF + 1], tm[S::NF + 2]);
-        make_prim<S, Real>(Pp, tp, brd, brm, bE, bp, tp[S::NF], tp[S::NF + 1], tp[S::NF + 2]);
-        if (S::RAIN) {
-            Pm.vr = rain_velocity<Real>(Pm.rr, Pm.rm, M);
-            Pp.vr = rain_velocity<Real>(Pp.rr, Pp.rm, M);
-        }
-        Real Fm[S::NF], Fp[S::NF];
-        flux_dir<S, Real>(Pm, j, Fm);
-        flux_dir<S, Real>(Pp, j, Fp);
-        const Real lm = wave_speed<S, Real>(Pm, j), lpp = wave_speed<S, Real>(Pp, j);
-        const Real lam = lm > lpp ? lm : lpp;
-        const Real hs = Real(0.5) * Real(s);
-        Real *out = s_fh + ((el2 * S::NFACE + face) * S::NF) * S::NFP1 + q;
-#pragma unroll
-        for (int f = 0; f < S::NF; ++f)
-            out[f * S::NFP1] = hs * (Fm[f] + Fp[f]) + Real(0.5) * lam * (tm[f] - tp[f]);
     }
     __syncthreads();
 
@@ -634,17 +841,11 @@ __global__ void k_split(KArgs<Real> A, double *oT, double *orv, double *orc, dou
         const int e = (int)(gi / S::NP), a = (int)(gi - (size_t)e * S::NP);
         const int lev = vert_index<S::D>(A.M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
         const int nl = A.M.nzlev_node;
-        double msq = 0.0;
+        Real u[S::NF];
 #pragma unroll
-        for (int j = 0; j < S::D; ++j) {
-            const double m = (double)A.Uin[(S::IM + j) * nodes + gi];
-            msq += m * m;
-        }
-        const double rd = A.bnode_d[lev] + (double)A.Uin[gi];
-        const double rm = A.bnode_d[nl + lev] + (double)A.Uin[nodes + gi];
-        const double rr = S::RAIN ? (double)A.Uin[2 * nodes + gi] : 0.0;
-        const double E = A.bnode_d[2 * nl + lev] + (double)A.Uin[S::IE * nodes + gi];
-        const NodeDerived nd = node_derived<false>(rd, rm, rr, E, msq, A.bnode_d[3 * nl + lev], A.M);
+        for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
+        const NodeDerived nd = derive_node<S>(u, A, lev);
+        const double rm = A.bnode_d[nl + lev] + (double)u[1];
         if (!nd.conv) atomicAdd(&A.flags[0], 1ull);
         if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
         if (oT) oT[gi] = nd.T;
@@ -752,7 +953,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(KArgs<Real> A, d
         const double rc = rm - rv;
         const double cv = kCvd * rd + kCvv * rv + kCl * (rc + rr);
         const double cm = sqrt((cv + kRd * rd + kRv * rv) / cv * p / rho);
-        const double vr = S::RAIN ? rain_velocity<double>(rr, rm, A.M) : 0.0;
+        const double vr = S::RAIN ? rain_velocity(rr, rm, A.M) : 0.0;
         acc[5] = fmax(acc[5], sqrt(msq) / rho + fabs(vr) + cm);
         const double rvs = rho_vs(T, 1.0 / T);
         acc[6] = fmax(acc[6], (rv - rvs) / rvs);
@@ -775,6 +976,16 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(KArgs<Real> A, d
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int r = 0; r < kNRed; ++r) partials[(size_t)blockIdx.x * kNRed + r] = sh[r][0];
+    }
+}
+
+// rho_vs table entries (rho_vs(T_i), 1/T_i), T_i = 150 K + i/8 K, float64 closed form
+static __global__ void k_fill_rvs_table(double *tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kTabN) {
+        const double T = kTabT0 + (double)i / kTabInvStep;
+        tab[2 * i] = rho_vs(T, 1.0 / T);
+        tab[2 * i + 1] = 1.0 / T;
     }
 }
 

@@ -1,0 +1,77 @@
+// Float64 elementary functions of the split and the rain terms, built to use
+// few float64 instructions (GB300 runs float64 at ~1/70 of the float32 rate).
+//
+// * rho_vs(T): table-driven evaluation in the manner of Tang's table-driven
+//   exponential (Tang 1989): rho_vs is tabulated in float64 on a 1/8 K grid
+//   (host, libm), and between grid points
+//       rho_vs(T) = rho_vs(T_i) exp((a-1) ln(1+s) + b s / (T_i (1+s))),
+//   s = (T - T_i)/T_i, |s| <= 4.2e-4, with the two logarithmic terms and the
+//   exponential evaluated by truncated Taylor series (truncation < 1e-17).
+// * r^(-1/n) by the Newton iteration y <- y + y (1 - r y^n) / n, which needs no
+//   division, seeded from a float32 estimate (error ~1e-7, so two iterations
+//   reach float64 rounding).
+// * Reciprocal and reciprocal square root by Newton-Raphson refinement of a
+//   float32 seed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace dgm {
+
+// rho_vs table: T_i = kTabT0 + i / kTabInvStep, i = 0 .. kTabN - 1
+constexpr double kTabT0 = 150.0;
+constexpr double kTabInvStep = 8.0;
+constexpr int kTabN = 2001;          // 150 K .. 400 K
+constexpr double kTabT1 = kTabT0 + (kTabN - 1) / kTabInvStep;
+
+// 1/x: float32 seed, two Newton-Raphson steps r <- r + r (1 - x r)
+__device__ __forceinline__ double recip(double x) {
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+// 1/sqrt(x): float32 seed, two Newton steps y <- y (3 - x y^2) / 2
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    double y = (double)rsqrtf((float)x);
+    double h = 0.5 * x;
+    y = y * fma(-h * y, y, 1.5);
+    return y * fma(-h * y, y, 1.5);
+}
+
+__device__ __forceinline__ double sqrt_nr(double x) { return x > 0.0 ? x * rsqrt_nr(x) : 0.0; }
+
+// r^(-1/16) for r > 0 (two iterations from a float32 seed; tiny r, outside the
+// float32 range of the seed, takes the library power function)
+__device__ __forceinline__ double inv_root16(double r) {
+    if (r < 1e-30) return pow(r, -0.0625);
+    double y = (double)exp2f(-0.0625f * __log2f((float)r));
+    for (int it = 0; it < 2; ++it) {
+        const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4, y16 = y8 * y8;
+        const double e = fma(-r, y16, 1.0);
+        y = fma(0.0625 * y, e, y);
+    }
+    return y;
+}
+
+// r^(-1/8) for r > 0
+__device__ __forceinline__ double inv_root8(double r) {
+    if (r < 1e-30) return pow(r, -0.125);
+    double y = (double)exp2f(-0.125f * __log2f((float)r));
+    for (int it = 0; it < 2; ++it) {
+        const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+        const double e = fma(-r, y8, 1.0);
+        y = fma(0.125 * y, e, y);
+    }
+    return y;
+}
+
+// float32 versions for the FP32-bulk arithmetic
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float sqrt_nr(float x) { return x > 0.0f ? sqrtf(x) : 0.0f; }
+__device__ __forceinline__ float inv_root8(float r) { return exp2f(-0.125f * __log2f(r)); }
+
+}  // namespace dgm

@@ -6,9 +6,10 @@
 // implicit device synchronisation an allocation may cause, or a process that
 // fixes its device-memory budget at start-up.  This entry point serves them:
 // the caller passes the inputs and the output, and the scratch the kernels
-// need (derived fields, face traces, failure counters) lives in one
-// file-scope __device__ array of fixed size, DG_STATIC_SCRATCH_BYTES, that
-// every GPU which loads the library holds until the process exits.
+// need (a saturation-density table, derived fields, face traces, failure
+// counters) lives in one file-scope __device__ array of fixed size,
+// DG_STATIC_SCRATCH_BYTES, that every GPU which loads the library holds until
+// the process exits.
 //
 // The paper has no counterpart: this is packaging, the arithmetic is the
 // same kernels dg_rhs launches (k_prepare, then k_stage in MODE_RHS).
@@ -115,12 +116,14 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
         g.dim == 2 ? launchers_d2_f64(g.order, g.rain) : launchers_d3_f64(g.order, g.rain);
     if (!L) return DG_EINVAL;
 
-    // scratch: derived fields, one trace buffer, two failure counters
+    // scratch: saturation-density table, derived fields, one trace buffer, two failure counters
     const size_t nodes = (size_t)ne * L->np;
     const size_t derived_bytes = round_up(sizeof(double) * L->nd * nodes);
     const size_t trace_bytes = round_up(sizeof(double) * 2 * g.dim * L->ntr * (size_t)ne * L->nfp1);
+    const size_t table_bytes = round_up(sizeof(double) * 2 * kTabN);
     const size_t flag_bytes = 2 * sizeof(unsigned long long);
-    if (derived_bytes + trace_bytes + flag_bytes > (size_t)DG_STATIC_SCRATCH_BYTES) return DG_EINVAL;
+    if (table_bytes + derived_bytes + trace_bytes + flag_bytes > (size_t)DG_STATIC_SCRATCH_BYTES)
+        return DG_EINVAL;
 
     unsigned char *scratch = nullptr;
     int st = scratch_on_current_device(&scratch);
@@ -146,9 +149,11 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
     if (reference_tables(g.order, A.ref) != DG_OK) return DG_EINVAL;
 
-    A.derived = reinterpret_cast<double *>(scratch);
-    double *trace = reinterpret_cast<double *>(scratch + derived_bytes);
-    A.flags = reinterpret_cast<unsigned long long *>(scratch + derived_bytes + trace_bytes);
+    double *table = reinterpret_cast<double *>(scratch);
+    A.rvs_tab = table;
+    A.derived = reinterpret_cast<double *>(scratch + table_bytes);
+    double *trace = reinterpret_cast<double *>(scratch + table_bytes + derived_bytes);
+    A.flags = reinterpret_cast<unsigned long long *>(scratch + table_bytes + derived_bytes + trace_bytes);
     A.bnode = base_node;
     A.bface = base_face;
     A.bnode_d = base_node;
@@ -157,6 +162,8 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     // the failure counters must start at zero; derived fields and traces are
     // written in full by k_prepare before anything reads them
     if (cudaMemsetAsync(A.flags, 0, flag_bytes, stream) != cudaSuccess) return DG_ECUDA;
+    k_fill_rvs_table<<<(kTabN + 255) / 256, 256, 0, stream>>>(table);
+    if (cudaGetLastError() != cudaSuccess) return DG_ECUDA;
     A.Uin = static_cast<const double *>(U);
     A.trace_out = trace;
     if (L->prepare(A, stream) != cudaSuccess) return DG_ECUDA;

@@ -62,8 +62,10 @@ def to_device(U, dtype):
 
 
 def flux_scale(prob, U):
-    """Per-field round-off scale of the right-hand side: the largest flux
-    component times the largest derivative-matrix factor (k+1)^2 (2/h).
+    """Per-field round-off scale of the right-hand side: the largest term of
+    the face flux -- physical flux component, Lambda |U_f|, and for the
+    momenta the full pressure p (p' = p - p_bar carries the rounding of p) --
+    times the largest derivative-matrix factor (k+1)^2 (2/h).
 
     dU/dt is a difference of such terms; float64 rounding on them is of
     order 1e-16 of this scale per operation."""
@@ -73,5 +75,8 @@ def flux_scale(prob, U):
     P = dg.primitives(prob, [U[f] for f in range(prob.nf)], dg.node_base(prob, el), T, rv, pp)
     fl = [dg.physical_flux(prob, j, P) for j in range(mesh.dim)]
     fac = (mesh.k + 1) ** 2 * max(2.0 / h for h in mesh.h)
-    return np.array([max(np.abs(fl[j][f]).max() for j in range(mesh.dim)) * fac
+    lam = dg.max_wave_speed(prob, U)
+    pmax = np.abs(prob.base_node["p"]).max()
+    return np.array([max(max(np.abs(fl[j][f]).max() for j in range(mesh.dim)),
+                         lam * np.abs(U[f]).max(), pmax if f in prob.i_m else 0.0) * fac
                      for f in range(prob.nf)])

@@ -84,6 +84,47 @@ def test_saturation_split_parity(name):
         dm.dg_free(ctx)
 
 
+def test_saturation_split_random_states():
+    # wide temperature range (inside and outside the library's 150-399 K table),
+    # saturated and unsaturated, with rain and motion; zero base state
+    from oracle import thermo
+    from oracle.mesh import Mesh
+    n = 3000
+    mesh = Mesh(2, (n, 1), (1.0e3 * n, 1.0e3), 1, (True, False))
+    zn = np.zeros(mesh.z_node_levels().size)
+    zf = np.zeros(mesh.z_face_levels().size)
+    prob = dg.Problem(mesh, dict(rho_d=zn, rho_m=zn, E=zn, p=zn), dict(rho_d=zf, rho_m=zf, E=zf, p=zf),
+                      rain=True)
+    u = inputs.uniform(77, np.arange(6 * n * 4)).reshape(6, n, 4)
+    rho_d = 0.2 + 1.2 * u[0]
+    T = 145.0 + 270.0 * u[3]
+    # below 200 K only little water, so that the all-vapour temperature T_u of
+    # the split stays positive (colder, wetter states are non-physical)
+    rho_m = rho_d * np.where(T < 200.0, 0.001, 0.05) * u[1]
+    rho_r = np.where(u[2] < 0.3, 0.0, 3e-3 * u[2])
+    m0 = 40.0 * (u[4] - 0.5)
+    m1 = 40.0 * (u[5] - 0.5)
+    rho_v = np.minimum(thermo.saturation_vapour_density(T), rho_m)
+    E = thermo.total_energy(rho_d, rho_v, rho_m - rho_v, rho_r, T, [m0, m1])
+    U = np.stack([rho_d, rho_m, rho_r, m0, m1, E])
+    ctx = library_context(prob)
+    try:
+        Ud = to_device(U, torch.float64)
+        outs = [torch.empty(n * 4, dtype=torch.float64, device="cuda") for _ in range(4)]
+        assert dm.dg_saturation_split(ctx, Ud, *outs) == 0
+        Tg, rvg, rcg, ppg = (o.cpu().numpy().reshape(n, 4) for o in outs)
+        To, rvo, rco, _, conv = thermo.split(rho_d, rho_m, rho_r, E - (m0 ** 2 + m1 ** 2) / (
+            2 * (rho_d + rho_m + rho_r)))
+        assert conv.all()
+        assert np.abs(Tg / To - 1).max() <= 1e-13
+        assert np.abs(rvg - rvo).max() <= 1e-13 * rho_m.max()
+        assert np.abs(Tg / T - 1).max() <= 1e-11
+        sat = rco > 0
+        assert sat.mean() > 0.2 and (~sat).mean() > 0.2
+    finally:
+        dm.dg_free(ctx)
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_rhs_parity(name):
     prob, U = _setup(name)
