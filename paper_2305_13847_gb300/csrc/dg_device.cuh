@@ -330,6 +330,7 @@ __device__ __forceinline__ float rain_velocity(float rr, float rm, const MeshDat
 // Per-node split plus the node-local quantities the next operator needs.
 struct NodeDerived {
     double T, rv, pp, gm, vr;
+    float Tf, rvf, ppf, gmf, vrf;   // float32 copies (FP32-bulk form)
     bool conv, phys;
 };
 
@@ -379,37 +380,41 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
 template <bool RAIN>
 __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im, int ie, int d,
                                                          double brd, double brm, double bE,
-                                                         double pbar, const MeshData &M,
+                                                         double pbar, float brdf, float brmf,
+                                                         const MeshData &M,
                                                          const double *__restrict__ tab) {
     NodeDerived o;
+    // float32 totals for the saturation test, the pre-solve and the checks
+    const float rdf = brdf + u[0], rmf = brmf + u[1], rrf = RAIN ? u[2] : 0.0f;
+    const float rhof = rdf + rmf + rrf;
+    float msq = 0.0f;
+    for (int j = 0; j < d; ++j) msq = fmaf(u[im + j], u[im + j], msq);
+    // float64 temperature recovery: T_u = T_ref + (E - |m|^2/(2 rho) - rho_m L') / C_u
     const double rd = brd + (double)u[0];
     const double rm = brm + (double)u[1];
     const double rr = RAIN ? (double)u[2] : 0.0;
-    const double E = bE + (double)u[ie];
-    float msq = 0.0f;
-    for (int j = 0; j < d; ++j) msq = fmaf(u[im + j], u[im + j], msq);
-    const float rhof = (float)(rd + rm + rr);
-    const double re = E - (double)(0.5f * msq * __frcp_rn(rhof));
-    const double cu = kCvd * rd + kCvv * rm + kCl * rr;
-    const double tu = kTref + fma(-rm, kLprime, re) * recip(cu);
+    const double re = (bE + (double)u[ie]) - (double)(0.5f * msq * __frcp_rn(rhof));
+    const double cu = fma(kCvd, rd, fma(kCvv, rm, kCl * rr));
+    const double tu = fma(fma(-rm, kLprime, re), recip(cu), kTref);
     const float tuf = (float)tu;
     const float rvs32 = rho_vs_f32(tuf);
     bool sat;
-    if (fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tu > 0.0)) {
+    if (fabsf(rmf - rvs32) <= 1e-5f * rmf || !(tuf > 0.0f)) {
         double it_;
-        sat = rm > rho_vs_tab(tu, tab, it_);
+        sat = rm > rho_vs_tab(tu, tab, it_);      // close call: decide in float64
     } else {
-        sat = rm > (double)rvs32;
+        sat = rmf > rvs32;
     }
-    float deficit = 0.0f;
+    float deficit = 0.0f, rvf, Tf;
     o.conv = true;
     if (!sat) {
         o.T = tu;
         o.rv = rm;
-        deficit = rvs32 - (float)rm;
+        Tf = tuf;
+        rvf = rmf;
+        deficit = rvs32 - rmf;
     } else {
-        const double cdry = kCvd * rd + kCl * (rm + rr);
-        const float cdf = (float)cdry, ref = (float)re, tref = (float)kTref;
+        const float cdf = kCvd * rdf + kCl * (rmf + rrf), ref = (float)re, tref = (float)kTref;
         const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
         const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
         float t = tuf;
@@ -428,37 +433,42 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
                 break;
             }
         }
-        // one float64 Newton correction
+        // one float64 Newton correction of T with the float64 rho_vs
         double invt;
         const double T32 = (double)t;
         const double rvs = rho_vs_tab(T32, tab, invt);
-        const double heat = fma(kCvv - kCl, rvs, cdry);
-        const double h = fma(heat, T32 - kTref, fma(rvs, kLprime, -re));
-        const float rvsf = (float)rvs, itf = (float)invt;
+        const double cdry = fma(kCvd, rd, kCl * (rm + rr));
+        const double h = fma(fma(kCvv - kCl, rvs, cdry), T32 - kTref, fma(rvs, kLprime, -re));
+        const float rvsf = (float)rvs, itf = __frcp_rn(t);
         const float drvs = rvsf * itf * (am1 + bb * itf);
-        const float dh = (float)heat + (clv * (t - tref) + lp) * drvs;
+        const float dh = cdf + clv * rvsf + (clv * (t - tref) + lp) * drvs;
         const float dT = (float)h / dh;
         o.T = T32 - (double)dT;
         o.rv = fma(-(double)drvs, (double)dT, rvs);
+        Tf = (float)o.T;
+        rvf = (float)o.rv;
         o.conv = conv && fabsf(dT) <= 1e-4f * t;
     }
-    o.pp = (rd * kRd + o.rv * kRv) * o.T - pbar;
-    const double rho = rd + rm + rr;
-    o.phys = (rd > 0.0) && (rho > 0.0) && (o.T > 50.0) && (o.T < 1000.0) && isfinite(o.pp);
+    // p' = (rho_d R_d + rho_v R_v) T - p_bar in float64 (cancellation against p_bar)
+    o.pp = fma(fma(rd, kRd, o.rv * kRv), o.T, -pbar);
+    const float ppf = (float)o.pp;
+    o.phys = (rdf > 0.0f) && (rhof > 0.0f) && (Tf > 50.0f) && (Tf < 1000.0f) && isfinite(ppf);
     o.gm = 0.0;
     o.vr = 0.0;
+    o.Tf = Tf;
+    o.rvf = rvf;
+    o.ppf = ppf;
     if (RAIN) {
-        const float rrf = u[2] > 0.0f ? u[2] : 0.0f;
-        const float x = rrf > 0.0f ? exp2f(0.0625f * __log2f(rrf)) : 0.0f;
+        const float rrp = rrf > 0.0f ? rrf : 0.0f;
+        const float x = rrp > 0.0f ? exp2f(0.0625f * __log2f(rrp)) : 0.0f;
         const float x2 = x * x, x3 = x2 * x, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
-        const float rc = (float)(rm - o.rv);
-        const float Tf = (float)o.T;
+        const float rc = rmf - rvf;
         const float s_ev = ((float)kSevA - (float)kSevB * (Tf - (float)kTref)) *
                            (1.0f + (float)kSevC * x3) * deficit * x8;
         const float s_au = (float)kSau * (rc > 0.0f ? rc : 0.0f);
         const float s_ac = (float)kSac * rc * x14;
-        o.gm = (double)(s_ev - s_au - s_ac);
-        o.vr = (double)rain_velocity(u[2], (float)rm, M);
+        o.gmf = s_ev - s_au - s_ac;
+        o.vrf = rain_velocity(rrf, rmf, M);
     }
     return o;
 }
@@ -581,8 +591,8 @@ template <class S>
 __device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<float> &A, int lev) {
     const int nl = A.M.nzlev_node;
     return node_derived_bulk<S::RAIN>(u, S::IM, S::IE, S::D, A.bnode_d[lev], A.bnode_d[nl + lev],
-                                      A.bnode_d[2 * nl + lev], A.bnode_d[3 * nl + lev], A.M,
-                                      A.rvs_tab);
+                                      A.bnode_d[2 * nl + lev], A.bnode_d[3 * nl + lev],
+                                      A.bnode[lev], A.bnode[nl + lev], A.M, A.rvs_tab);
 }
 
 template <class S, typename Real>
@@ -594,19 +604,33 @@ __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real
     const NodeDerived nd = derive_node<S>(u, A, lev);
     if (!nd.conv) atomicAdd(&A.flags[0], 1ull);
     if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
-    A.derived[gi] = (Real)nd.T;
-    A.derived[nodes + gi] = (Real)nd.rv;
-    A.derived[2 * nodes + gi] = (Real)nd.pp;
+    Real T, rv, pp, gm, vr;
+    if (sizeof(Real) == sizeof(float)) {
+        T = (Real)nd.Tf;
+        rv = (Real)nd.rvf;
+        pp = (Real)nd.ppf;
+        gm = (Real)nd.gmf;
+        vr = (Real)nd.vrf;
+    } else {
+        T = (Real)nd.T;
+        rv = (Real)nd.rv;
+        pp = (Real)nd.pp;
+        gm = (Real)nd.gm;
+        vr = (Real)nd.vr;
+    }
+    A.derived[gi] = T;
+    A.derived[nodes + gi] = rv;
+    A.derived[2 * nodes + gi] = pp;
     if (S::RAIN) {
-        A.derived[3 * nodes + gi] = (Real)nd.gm;
-        A.derived[4 * nodes + gi] = (Real)nd.vr;
+        A.derived[3 * nodes + gi] = gm;
+        A.derived[4 * nodes + gi] = vr;
     }
     const int str = S::EPB * S::NP;
 #pragma unroll
     for (int f = 0; f < S::NF; ++f) s_tr[f * str + t] = u[f];
-    s_tr[S::NF * str + t] = (Real)nd.T;
-    s_tr[(S::NF + 1) * str + t] = (Real)nd.rv;
-    s_tr[(S::NF + 2) * str + t] = (Real)nd.pp;
+    s_tr[S::NF * str + t] = T;
+    s_tr[(S::NF + 1) * str + t] = rv;
+    s_tr[(S::NF + 2) * str + t] = pp;
 }
 
 template <class S, typename Real>
@@ -663,9 +687,17 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const Real *s_t
     const int s = (face & 1) ? 1 : -1;
     const Real *ls = (face & 1) ? A.ref.lp : A.ref.lm;
     Real tm[S::NTR], tp[S::NTR];
+    if (sizeof(Real) == sizeof(double)) {
+        // float64 form: the own trace was written with the same interpolation
+        // when this state was produced; reading it back saves float64 work
 #pragma unroll
-    for (int fld = 0; fld < S::NTR; ++fld)
-        tm[fld] = interp_face<S, Real>(s_tr + fld * STR + el2 * S::NP, ls, J, q);
+        for (int fld = 0; fld < S::NTR; ++fld)
+            tm[fld] = A.trace_in[(((size_t)face * S::NTR + fld) * ne + e2) * S::NFP1 + q];
+    } else {
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld)
+            tm[fld] = interp_face<S, Real>(s_tr + fld * STR + el2 * S::NP, ls, J, q);
+    }
     const int nb = neighbour<S::D>(M, e2, J, s);
     if (nb >= 0) {
         const int fo = 2 * J + (s > 0 ? 0 : 1);
