@@ -227,9 +227,36 @@ int dg_reduce(dg_ctx *ctx, double out[DG_NREDUCE]);
 int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, const double *base_face,
                    const void *U, void *dUdt, void *cuda_stream);
 
-/* Adjoint of one dg_step (not in this build: returns DG_ENOTIMPL). */
+/* Adjoint of the right-hand side: ubar = (dR/dU)^T w for R = dg_rhs at the
+ * state U (device, ABI layout, float64), w and ubar device float64 arrays in
+ * the ABI layout (ubar must not overlap U or w).  This is the linearisation
+ * of the computed operator of Eq. (3.2)/(3.3): transposed volume
+ * contraction and lift, Lax-Friedrichs flux with the active side of the max
+ * in Eq. (3.4), and the split Eq. (2.8) differentiated by the implicit
+ * function theorem on its active branch (saturated or not).  The fractional
+ * powers of rain in v_r and in the warm-rain sources (Eq. (2.4)) have
+ * unbounded derivatives as rho_r -> 0+; they are differentiated at
+ * max(rho_r, 1e-12 kg/m^3), which keeps the linearisation of long runs
+ * bounded and leaves it exact wherever rho_r >= 1e-12.  Uses the context's
+ * derived-field and trace buffers (the next dg_step re-derives them).
+ * DG_ENOTIMPL for DG_FP32_BULK contexts; asynchronous. */
+int dg_rhs_adjoint(dg_ctx *ctx, const void *U, const double *w, double *ubar);
+
+/* Adjoint of one SSPRK(4,3) step of size dt from the state U_n (device,
+ * ABI layout, float64): lam_n = (dU^{n+1}/dU^n)^T lam_np1.  The three
+ * intermediate stage states are recomputed from U_n inside the call; the
+ * stages are then reversed (Remark 3.1, Shu-Osher form) with dg_rhs_adjoint.
+ * lam_np1, lam_n: device float64, ABI layout, distinct.  Allocates six
+ * state-sized and one trace-sized scratch buffers in the context on first
+ * use.  DG_ENOTIMPL for DG_FP32_BULK contexts; asynchronous. */
 int dg_adjoint_step(dg_ctx *ctx, double dt, const void *U_n, const double *lam_np1,
                     double *lam_n);
+
+/* Cloud-water functional J(U) = integral of rho_c = rho_m - rho_v over the
+ * domain (Gauss rule of the DG space; rho_v from the split Eq. (2.8)) and
+ * its gradient dJ/dU (device float64, ABI layout).  J is written to a host
+ * double; the call synchronises.  DG_ENOTIMPL for DG_FP32_BULK contexts. */
+int dg_cloud_functional(dg_ctx *ctx, const void *U, double *J, double *dJdU);
 
 /* Text for a status code. */
 const char *dg_strerror(int code);

@@ -122,12 +122,18 @@ def physical_flux(prob, j, P):
     return F
 
 
+def _abs(x):
+    """|x| by the sign of the real part (the same as np.abs for real x; keeps
+    the complex-step derivative for complex x)."""
+    return np.where(np.real(x) < 0, -x, x)
+
+
 def wave_speed(prob, j, P):
     """|u.n| + |v_r e_z.n| + c_m for n = +-e_j (one argument of the max in Eq. (3.4))."""
     cm = thermo.sound_speed(P["rho_d"], P["rho_v"], P["rho_c"], P["rho_r"], P["p"])
-    lam = np.abs(P["u"][j]) + cm
+    lam = _abs(P["u"][j]) + cm
     if j == prob.mesh.vert:
-        lam = lam + np.abs(P["v_r"])
+        lam = lam + _abs(P["v_r"])
     return lam
 
 

@@ -6,6 +6,17 @@ import numpy as np
 
 from . import constants as C
 
+def _arr(x):
+    """float64 array, or complex128 when given complex values.
+
+    Complex inputs let the oracle be differentiated by the complex step
+    (f(x + i h v) has imaginary part h f'(x) v + O(h^3)); for real inputs
+    nothing changes.
+    """
+    a = np.asarray(x)
+    return a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+
+
 # Exponents of the Clausius-Clapeyron solution, Eq. (2.6)
 ES_A = (C.c_pv - C.c_l) / C.R_v                              # power of T/T_ref
 ES_B = (C.L_ref - (C.c_pv - C.c_l) * C.T_ref) / C.R_v        # factor in the exponential
@@ -14,19 +25,19 @@ L_PRIME = C.L_ref - C.R_v * C.T_ref                          # rho_v coefficient
 
 def saturation_vapour_pressure(T):
     """e_s(T), Eq. (2.6): Clausius-Clapeyron with a latent heat linear in T."""
-    T = np.asarray(T, dtype=np.float64)
+    T = _arr(T)
     return C.e_ref * (T / C.T_ref) ** ES_A * np.exp(ES_B * (1.0 / C.T_ref - 1.0 / T))
 
 
 def saturation_vapour_density(T):
     """rho_vs(T) = e_s(T) / (R_v T): the first argument of the min in Eq. (2.8b)."""
-    T = np.asarray(T, dtype=np.float64)
+    T = _arr(T)
     return saturation_vapour_pressure(T) / (C.R_v * T)
 
 
 def saturation_vapour_density_dT(T):
     """d rho_vs / dT, differentiating the closed form of Eq. (2.6) / (R_v T)."""
-    T = np.asarray(T, dtype=np.float64)
+    T = _arr(T)
     return saturation_vapour_density(T) * ((ES_A - 1.0) / T + ES_B / T ** 2)
 
 
@@ -77,8 +88,9 @@ def split(rho_d, rho_m, rho_r, rho_e, rel_tol=1e-12, max_iter=60):
 
     Returns (T, rho_v, rho_c, iters, converged) as arrays.
     """
-    rho_d, rho_m, rho_r, rho_e = np.broadcast_arrays(
-        *(np.asarray(a, dtype=np.float64) for a in (rho_d, rho_m, rho_r, rho_e)))
+    args = [_arr(a) for a in (rho_d, rho_m, rho_r, rho_e)]
+    dt = np.result_type(*args)
+    rho_d, rho_m, rho_r, rho_e = np.broadcast_arrays(*(a.astype(dt) for a in args))
     shape = rho_d.shape
     rho_d, rho_m, rho_r, rho_e = (a.ravel() for a in (rho_d, rho_m, rho_r, rho_e))
 
@@ -89,7 +101,7 @@ def split(rho_d, rho_m, rho_r, rho_e, rel_tol=1e-12, max_iter=60):
     iters = np.zeros(T.shape, dtype=np.int64)
     converged = np.ones(T.shape, dtype=bool)
 
-    sat = rho_m > saturation_vapour_density(T_u)
+    sat = np.real(rho_m) > np.real(saturation_vapour_density(T_u))
     idx = np.nonzero(sat)[0]
     if idx.size:
         d, m, r, e = rho_d[idx], rho_m[idx], rho_r[idx], rho_e[idx]
@@ -108,7 +120,7 @@ def split(rho_d, rho_m, rho_r, rho_e, rel_tol=1e-12, max_iter=60):
         lo = T_u[idx].copy()
         hi = lo + 10.0
         for _ in range(200):                      # expand the upper end of the bracket
-            grow = H(hi, everything) < 0.0
+            grow = np.real(H(hi, everything)) < 0.0
             if not grow.any():
                 break
             hi = np.where(grow, hi + 10.0, hi)
@@ -122,15 +134,19 @@ def split(rho_d, rho_m, rho_r, rho_e, rel_tol=1e-12, max_iter=60):
             a = np.nonzero(active)[0]
             ta = t[a]
             h = H(ta, a)
-            lo[a] = np.where(h < 0.0, ta, lo[a])
-            hi[a] = np.where(h > 0.0, ta, hi[a])
+            # bracket tests on real parts (complex inputs carry a derivative
+            # in the imaginary part; see _arr)
+            hr, tr = np.real(h), np.real(ta)
+            lo[a] = np.where(hr < 0.0, ta, lo[a])
+            hi[a] = np.where(hr > 0.0, ta, hi[a])
             tn = ta - h / dH(ta, a)
-            outside = ~((tn >= lo[a]) & (tn <= hi[a]))
+            tnr = np.real(tn)
+            outside = ~((tnr >= np.real(lo[a])) & (tnr <= np.real(hi[a])))
             tn = np.where(outside, 0.5 * (lo[a] + hi[a]), tn)
             step = np.abs(tn - ta)
             t[a] = tn
             it[a] += 1
-            done_now = extra[a] | (h == 0.0)
+            done_now = extra[a] | (hr == 0.0)
             small = step <= rel_tol * np.abs(tn)
             extra[a] = extra[a] | small
             active[a] = ~done_now
@@ -170,7 +186,7 @@ def rain_velocity(rho_r, rho_m, rho_w=None):
     Negative or zero rain gives v_r = 0 (the fractional power of a negative
     DG undershoot is not defined; the paper is silent).
     """
-    rho_r = np.asarray(rho_r, dtype=np.float64)
+    rho_r = _arr(rho_r)
     rr = np.maximum(rho_r, 0.0)
     if rho_w is None or rho_w <= 0.0:
         rw = rho_m + rho_r
@@ -188,7 +204,7 @@ def sources(T, rho_v, rho_c, rho_r):
     Fractional powers use max(rho_r, 0) (negative rain from DG undershoot has
     no real power; the paper is silent).
     """
-    rr = np.maximum(np.asarray(rho_r, dtype=np.float64), 0.0)
+    rr = np.maximum(_arr(rho_r), 0.0)
     rvs = saturation_vapour_density(T)
     s_ev = ((C.S_EV_A - C.S_EV_B * (T - C.T_ref)) * (1.0 + C.S_EV_C * rr ** (3.0 / 16.0))
             * (rvs - rho_v) * rr ** 0.5)

@@ -1,0 +1,502 @@
+// Adjoint (vector-Jacobian product) of the DG right-hand side, float64.
+//
+// For a state U and an adjoint vector w (both in the ABI layout) the kernels
+// compute ubar = (dR/dU)^T w, R the right-hand side of Eq. (3.2)/(3.3):
+//   k_adj_local   per element: transposed volume contraction, the nodal
+//                 flux and source Jacobians, the Lax-Friedrichs face-flux
+//                 Jacobians on both sides of every face point, and the
+//                 transposed interpolation of the own-side trace adjoints;
+//                 the neighbour-side trace adjoints go to a buffer;
+//   k_adj_gather  per node: gathers the neighbours' contributions to its
+//                 traces, then the split Eq. (2.8) is differentiated by the
+//                 implicit-function theorem on the active branch, giving
+//                 the adjoint of U; out = alpha out + beta w + gamma ubar.
+// The pointwise Jacobians (flux, wave-speed bound, sources, v_r) are taken
+// in forward mode with dual numbers through the same templated code the
+// forward kernels run, so the adjoint linearises exactly the computed
+// operator.  Non-smooth points take the active branch: max in Lambda, the
+// saturation min in the split, max(rho_c, 0) and max(rho_r, 0); fractional
+// powers of rain below kRainFloorLin are differentiated at the floor.
+#pragma once
+
+#include "dg_device.cuh"
+
+namespace dgm {
+
+// ---------------------------------------------------------------------------
+// Dual numbers (value, derivative) for forward-mode differentiation
+// ---------------------------------------------------------------------------
+struct Dual {
+    double v, d;
+    __device__ __forceinline__ Dual() : v(0.0), d(0.0) {}
+    __device__ __forceinline__ Dual(double x) : v(x), d(0.0) {}
+    __device__ __forceinline__ Dual(double x, double y) : v(x), d(y) {}
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+    const double q = a.v / b.v;
+    return Dual(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ Dual &operator+=(Dual &a, Dual b) { return a = a + b; }
+__device__ __forceinline__ Dual &operator-=(Dual &a, Dual b) { return a = a - b; }
+__device__ __forceinline__ bool operator>(Dual a, Dual b) { return a.v > b.v; }
+__device__ __forceinline__ bool operator<(Dual a, Dual b) { return a.v < b.v; }
+__device__ __forceinline__ bool operator!=(Dual a, Dual b) { return a.v != b.v; }
+__device__ __forceinline__ Dual fma(Dual a, Dual b, Dual c) {
+    return Dual(::fma(a.v, b.v, c.v), a.d * b.v + a.v * b.d + c.d);
+}
+__device__ __forceinline__ Dual recip(Dual a) {
+    const double r = 1.0 / a.v;
+    return Dual(r, -a.d * r * r);
+}
+__device__ __forceinline__ Dual sqrt_nr(Dual a) {
+    if (!(a.v > 0.0)) return Dual(0.0, 0.0);
+    const double s = sqrt(a.v);
+    return Dual(s, 0.5 * a.d / s);
+}
+// |x| with the symmetric derivative 0 at x = 0 (the velocity is exactly 0 in
+// a resting initial state; central differences see 0 there)
+__device__ __forceinline__ Dual fabs(Dual a) {
+    return a.v < 0.0 ? -a : (a.v > 0.0 ? a : Dual(0.0, 0.0));
+}
+__device__ __forceinline__ Dual pow(Dual a, double p) {
+    const double y = ::pow(a.v, p);
+    return Dual(y, p * y / a.v * a.d);
+}
+
+// r^p for rain r > 0 with its derivative taken at max(r, floor) (kRainFloorLin):
+// the powers p < 1 of the warm-rain closure have unbounded derivatives as
+// r -> 0+, and the rain that the DG discretisation leaks into cloud-free
+// elements would otherwise dominate the linearisation.
+__device__ __forceinline__ Dual rain_pow(Dual r, double p, double floor) {
+    const double y = ::pow(r.v, p);
+    const double re = r.v > floor ? r.v : floor;
+    return Dual(y, p * ::pow(re, p - 1.0) * r.d);
+}
+
+__device__ __forceinline__ Dual rain_velocity(Dual rr, Dual rm, const MeshData &M) {
+    const Dual rrp = rr.v > 0.0 ? rr : Dual(0.0);
+    const Dual rw = M.rho_w > 0.0 ? Dual(M.rho_w) : rm + rr;
+    if (!(rrp.v > 0.0) || !(rw.v > 0.0)) return Dual(0.0);
+    // kvr (r / rho_w)^(1/8) = kvr r^(1/8) rho_w^(-1/8)
+    return Dual(M.kvr) * rain_pow(rrp, 0.125, M.rain_floor) * pow(rw, -0.125);
+}
+
+// rho_vs(T) with derivative (closed form of Eq. (2.6) / (R_v T))
+__device__ __forceinline__ Dual rho_vs_dual(Dual T) {
+    const double r = rho_vs(T.v, 1.0 / T.v);
+    return Dual(r, r * ((kEsA - 1.0) / T.v + kEsB / (T.v * T.v)) * T.d);
+}
+
+// ---------------------------------------------------------------------------
+struct AdjArgs {
+    MeshData M;
+    RefData<double> ref;
+    const double *U;        // state (ABI layout)
+    const double *derived;  // T, rho_v, p' (, G, v_r) of U
+    const double *trace;    // traces of U, [2D][NTR][ne][NFP1]
+    const double *bnode, *bface;  // base tables
+    const double *w;        // adjoint input (ABI layout)
+    double *ubar_part;      // [NTR][nodes]: adjoints of U (NF) and of T, rho_v, p'
+    double *tadj;           // [2D][NTR][ne][NFP1]: neighbour trace adjoints
+    double *out;            // [NF][nodes]
+    double alpha, beta, gamma;
+};
+
+// Column-by-column Jacobian-vector products of the nodal flux: for the
+// inputs x = (U, T, rho_v, p') at one node, xbar_k += sum_j sum_f
+// Fbar[j][f] dF_jf / dx_k.
+template <class S>
+__device__ __forceinline__ void flux_vjp(const double *x, double brd, double brm, double bE,
+                                         double bp, const double (*Fbar)[S::NF], const MeshData &M,
+                                         double *xbar) {
+    for (int k = 0; k < S::NTR; ++k) {
+        Dual xd[S::NTR];
+#pragma unroll
+        for (int i = 0; i < S::NTR; ++i) xd[i] = Dual(x[i], i == k ? 1.0 : 0.0);
+        Prim<S::D, S::RAIN, Dual> P;
+        make_prim<S, Dual>(P, xd, Dual(brd), Dual(brm), Dual(bE), Dual(bp), xd[S::NF],
+                           xd[S::NF + 1], xd[S::NF + 2]);
+        if (S::RAIN) P.vr = rain_velocity(P.rr, P.rm, M);
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            Dual F[S::NF];
+            flux_dir<S, Dual>(P, j, F);
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) acc = ::fma(Fbar[j][f], F[f].d, acc);
+        }
+        xbar[k] += acc;
+    }
+}
+
+// Sources G (Eq. (2.4), gravity) as functions of x = (U, T, rho_v, p'):
+// forward-mode Jacobian-vector products dotted with the adjoint wv.
+template <class S>
+__device__ __forceinline__ void source_vjp(const double *x, double brd, double brm,
+                                           const double *wv, const MeshData &M, double *xbar) {
+    const double g = M.g;
+    // gravity: G_{m_vert} = -g (rho_d' + rho_m' + rho_r'), G_E = -g m_vert
+    const double wm = wv[S::IM + S::VERT];
+    xbar[0] -= g * wm;
+    xbar[1] -= g * wm;
+    if (S::RAIN) xbar[2] -= g * wm;
+    xbar[S::IM + S::VERT] -= g * wv[S::IE];
+    if (!S::RAIN) return;
+    // microphysics: G_rm = S_ev - S_au - S_ac, G_rr = -G_rm; inputs rho_m', rho_r', T, rho_v
+    const double wg = wv[1] - wv[2];
+    const int ins[4] = {1, 2, S::NF, S::NF + 1};
+    const double rm0 = brm + x[1];
+    const bool sat = rm0 - x[S::NF + 1] > 0.0;
+    for (int c = 0; c < 4; ++c) {
+        const int k = ins[c];
+        const Dual rm = Dual(brm) + Dual(x[1], k == 1 ? 1.0 : 0.0);
+        const Dual rr = Dual(x[2], k == 2 ? 1.0 : 0.0);
+        const Dual T = Dual(x[S::NF], k == S::NF ? 1.0 : 0.0);
+        const Dual rv = Dual(x[S::NF + 1], k == S::NF + 1 ? 1.0 : 0.0);
+        const Dual rc = rm - rv;
+        Dual deficit = rho_vs_dual(T) - rv;
+        if (sat) deficit.v = 0.0;            // the forward value is exactly 0 at saturation
+        const Dual rrp = rr.v > 0.0 ? rr : Dual(0.0);
+        const Dual xr = rrp.v > 0.0 ? rain_pow(rrp, 0.0625, M.rain_floor) : Dual(0.0);
+        const Dual x2 = xr * xr, x3 = x2 * xr, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
+        const Dual s_ev = (Dual(kSevA) - Dual(kSevB) * (T - Dual(kTref))) *
+                          (Dual(1.0) + Dual(kSevC) * x3) * deficit * x8;
+        const Dual s_au = rc.v > 0.0 ? Dual(kSau) * rc : Dual(0.0);
+        const Dual s_ac = Dual(kSac) * rc * x14;
+        xbar[k] += wg * (s_ev - s_au - s_ac).d;
+    }
+    (void)brd;
+}
+
+// Lax-Friedrichs face flux: adjoints of both traces at one face point.
+template <class S, int J>
+__device__ __forceinline__ void face_vjp(const AdjArgs &A, const double *s_w, double *s_ta, int el2,
+                                         int face, int q, int e2) {
+    constexpr int STR = S::EPB * S::NP;
+    const MeshData &M = A.M;
+    const int ne = M.ne;
+    const int s = (face & 1) ? 1 : -1;
+    double tm[S::NTR], tp[S::NTR];
+#pragma unroll
+    for (int fld = 0; fld < S::NTR; ++fld)
+        tm[fld] = A.trace[(((size_t)face * S::NTR + fld) * ne + e2) * S::NFP1 + q];
+    const int nb = neighbour<S::D>(M, e2, J, s);
+    if (nb >= 0) {
+        const int fo = 2 * J + (s > 0 ? 0 : 1);
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld)
+            tp[fld] = A.trace[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q];
+    } else {
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) tp[fld] = tm[fld];
+        tp[S::IM + J] = -tm[S::IM + J];
+    }
+    double brd, brm, bE, bp;
+    const int iz = vert_index<S::D>(M, e2);
+    if (J == S::VERT) {
+        load_base<S, double>(A.bface, M.nzlev_face, iz + (s > 0 ? 1 : 0), brd, brm, bE, bp);
+    } else {
+        load_base<S, double>(A.bnode, M.nzlev_node, iz * S::P1 + face_q_vert<S::D, S::P1>(J, q), brd,
+                             brm, bE, bp);
+    }
+    // adjoint of Fhat: R_a -= (2/h_J) l_a(s)/w_a Fhat(q) along the line through q
+    const double *lift = (face & 1) ? A.ref.liftp : A.ref.liftm;
+    double fhb[S::NF];
+#pragma unroll
+    for (int f = 0; f < S::NF; ++f) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < S::P1; ++i)
+            acc = ::fma(lift[i], s_w[f * STR + el2 * S::NP + line_node<S::D, S::P1>(J, q, i)], acc);
+        fhb[f] = -M.two_over_h[J] * acc;
+    }
+    // values: which side's wave speed is the max (forward: lam = lm > lp ? lm : lp)
+    Prim<S::D, S::RAIN, double> Pm, Pp;
+    make_prim<S, double>(Pm, tm, brd, brm, bE, bp, tm[S::NF], tm[S::NF + 1], tm[S::NF + 2]);
+    make_prim<S, double>(Pp, tp, brd, brm, bE, bp, tp[S::NF], tp[S::NF + 1], tp[S::NF + 2]);
+    if (S::RAIN) {
+        Pm.vr = rain_velocity(Pm.rr, Pm.rm, M);
+        Pp.vr = rain_velocity(Pp.rr, Pp.rm, M);
+    }
+    const double lmv = wave_speed<S, J, double>(Pm), lpv = wave_speed<S, J, double>(Pp);
+    const bool m_active = lmv > lpv;
+    const double lam = m_active ? lmv : lpv;
+    const double hs = 0.5 * s;
+    double tmb[S::NTR], tpb[S::NTR];
+    for (int side = 0; side < 2; ++side) {
+        const double *tt = side == 0 ? tm : tp;
+        const bool active = side == 0 ? m_active : !m_active;
+        const double jsign = side == 0 ? 1.0 : -1.0;   // d[[U]]/dU^- = 1, d[[U]]/dU^+ = -1
+        for (int k = 0; k < S::NTR; ++k) {
+            Dual td[S::NTR];
+#pragma unroll
+            for (int i = 0; i < S::NTR; ++i) td[i] = Dual(tt[i], i == k ? 1.0 : 0.0);
+            Prim<S::D, S::RAIN, Dual> P;
+            make_prim<S, Dual>(P, td, Dual(brd), Dual(brm), Dual(bE), Dual(bp), td[S::NF],
+                               td[S::NF + 1], td[S::NF + 2]);
+            if (S::RAIN) P.vr = rain_velocity(P.rr, P.rm, M);
+            Dual F[S::NF];
+            flux_dir<S, Dual>(P, J, F);
+            const double dlam = active ? wave_speed<S, J, Dual>(P).d : 0.0;
+            double acc = 0.0;
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) {
+                double df = hs * F[f].d + 0.5 * dlam * (tm[f] - tp[f]);
+                if (f == k) df += 0.5 * lam * jsign;
+                acc = ::fma(fhb[f], df, acc);
+            }
+            (side == 0 ? tmb : tpb)[k] = acc;
+        }
+    }
+    if (nb >= 0) {
+        // the + side is the neighbour's trace on its face (J, -s)
+        const int fo = 2 * J + (s > 0 ? 0 : 1);
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld)
+            A.tadj[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q] = tpb[fld];
+    } else {
+        // wall ghost: tp = tm with m_J negated
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) tmb[fld] += (fld == S::IM + J) ? -tpb[fld] : tpb[fld];
+    }
+    double *o = s_ta + ((size_t)(el2 * S::NFACE + face) * S::NTR) * S::NFP1 + q;
+#pragma unroll
+    for (int fld = 0; fld < S::NTR; ++fld) o[fld * S::NFP1] = tmb[fld];
+}
+
+template <class S>
+constexpr size_t adj_smem_bytes() {
+    return sizeof(double) * ((size_t)S::NF * S::EPB * S::NP + (size_t)S::EPB * S::NFACE * S::NTR * S::NFP1);
+}
+
+template <class S>
+__global__ void __launch_bounds__(S::NT) k_adj_local(AdjArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int STR = S::EPB * S::NP;
+    double *s_w = reinterpret_cast<double *>(smem_raw);        // [NF][STR]
+    double *s_ta = s_w + S::NF * STR;                          // [EPB][NFACE][NTR][NFP1]
+    const MeshData &M = A.M;
+    const int ne = M.ne;
+    const size_t nodes = (size_t)ne * S::NP;
+    const int t = threadIdx.x;
+    const int el = t / S::NP, a = t - el * S::NP;
+    const int e = blockIdx.x * S::EPB + el;
+    const bool valid = (t < STR) && (e < ne);
+    double x[S::NTR], xbar[S::NTR];
+    double brd = 0.0, brm = 0.0, bE = 0.0, bp = 0.0;
+    if (valid) {
+        const size_t gi = (size_t)e * S::NP + a;
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) {
+            x[f] = A.U[f * nodes + gi];
+            s_w[f * STR + t] = A.w[f * nodes + gi];
+        }
+        x[S::NF] = A.derived[gi];
+        x[S::NF + 1] = A.derived[nodes + gi];
+        x[S::NF + 2] = A.derived[2 * nodes + gi];
+        const int lev = vert_index<S::D>(M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        load_base<S, double>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
+#pragma unroll
+        for (int k = 0; k < S::NTR; ++k) xbar[k] = 0.0;
+    }
+    __syncthreads();
+    if (valid) {
+        // volume: R_a += (2/h_j) sum_i dhat[a_j][i] F_j(i)  =>  Fbar_j(i) = (2/h_j) sum_a dhat[a_j][i] w(a)
+        double Fbar[S::D][S::NF];
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const int aj = digit<S::D, S::P1>(a, j);
+            const int st = stride_of<S::P1>(j);
+            const int b0 = el * S::NP + a - aj * st;
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) {
+                double acc = 0.0;
+#pragma unroll
+                for (int i = 0; i < S::P1; ++i)
+                    acc = ::fma(A.ref.dhat[i][aj], s_w[f * STR + b0 + i * st], acc);
+                Fbar[j][f] = M.two_over_h[j] * acc;
+            }
+        }
+        flux_vjp<S>(x, brd, brm, bE, bp, Fbar, M, xbar);
+        double wv[S::NF];
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) wv[f] = s_w[f * STR + t];
+        source_vjp<S>(x, brd, brm, wv, M, xbar);
+    }
+    for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
+        const int el2 = item / (S::NFACE * S::NFP1);
+        const int rem = item - el2 * (S::NFACE * S::NFP1);
+        const int face = rem / S::NFP1;
+        const int q = rem - face * S::NFP1;
+        const int e2 = blockIdx.x * S::EPB + el2;
+        if (e2 >= ne) continue;
+        switch (face >> 1) {
+            case 0: face_vjp<S, 0>(A, s_w, s_ta, el2, face, q, e2); break;
+            case 1: face_vjp<S, 1>(A, s_w, s_ta, el2, face, q, e2); break;
+            default: face_vjp<S, (S::D == 3 ? 2 : 1)>(A, s_w, s_ta, el2, face, q, e2); break;
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        // own-side trace adjoints back to the nodes: trace = sum_i l_i(s) v(line node i)
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const int aj = digit<S::D, S::P1>(a, j);
+            const int q = face_q<S::D, S::P1>(a, j);
+            const double cm = A.ref.lm[aj], cp = A.ref.lp[aj];
+            const double *tmn = s_ta + ((size_t)(el * S::NFACE + 2 * j) * S::NTR) * S::NFP1 + q;
+            const double *tpl = s_ta + ((size_t)(el * S::NFACE + 2 * j + 1) * S::NTR) * S::NFP1 + q;
+#pragma unroll
+            for (int fld = 0; fld < S::NTR; ++fld)
+                xbar[fld] += cm * tmn[fld * S::NFP1] + cp * tpl[fld * S::NFP1];
+        }
+        const size_t gi = (size_t)e * S::NP + a;
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) A.ubar_part[fld * nodes + gi] = xbar[fld];
+    }
+}
+
+// Split Eq. (2.8) differentiated at one node: given the adjoints of T, rho_v
+// and p' = (rho_d R_d + rho_v R_v) T - p_bar, add the adjoints of the totals
+// and of rho e, then of U.  Unsaturated: T = T_ref + (rho e - rho_m L')/C_u,
+// rho_v = rho_m.  Saturated: H(T, x) = 0 gives dT = -(dH/dx dx)/H'(T) and
+// rho_v = rho_vs(T).
+template <class S>
+__device__ __forceinline__ void split_vjp(const double *u, double brd, double brm, double bE,
+                                          double T, double rv, double Tb, double rvb, double ppb,
+                                          double *ub) {
+    const double rd = brd + u[0], rm = brm + u[1], rr = S::RAIN ? u[2] : 0.0;
+    const double rho = rd + rm + rr;
+    double msq = 0.0;
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) msq += u[S::IM + j] * u[S::IM + j];
+    // p'
+    double rdb = ppb * kRd * T, rmb = 0.0, rrb = 0.0;
+    Tb += ppb * (rd * kRd + rv * kRv);
+    rvb += ppb * kRv * T;
+    double reb;
+    const bool sat = rm - rv > 0.0;
+    if (!sat) {
+        // rho_v = rho_m; T = T_ref + (re - rm L') / C_u
+        rmb += rvb;
+        const double cu = kCvd * rd + kCvv * rm + kCl * rr;
+        const double dT = (T - kTref);
+        reb = Tb / cu;
+        rmb += Tb * (-kLprime - kCvv * dT) / cu;
+        rdb += Tb * (-kCvd * dT) / cu;
+        rrb += Tb * (-kCl * dT) / cu;
+    } else {
+        const double invT = 1.0 / T;
+        const double rvs = rho_vs(T, invT);
+        const double drvs = rvs * invT * ((kEsA - 1.0) + kEsB * invT);
+        Tb += rvb * drvs;                              // rho_v = rho_vs(T)
+        const double heat = kCvd * rd + kCvv * rvs + kCl * (rm - rvs + rr);
+        const double dH = heat + ((kCvv - kCl) * (T - kTref) + kLprime) * drvs;
+        const double lam = Tb / dH;                    // dT = -(H_x dx) / H'
+        const double dT = (T - kTref);
+        rdb -= lam * kCvd * dT;
+        rmb -= lam * kCl * dT;
+        rrb -= lam * kCl * dT;
+        reb = lam;                                     // H_re = -1
+    }
+    // re = E - |m|^2 / (2 rho)
+    const double rhob = reb * msq / (2.0 * rho * rho);
+    ub[0] += rdb + rhob;
+    ub[1] += rmb + rhob;
+    if (S::RAIN) ub[2] += rrb + rhob;
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) ub[S::IM + j] -= reb * u[S::IM + j] / rho;
+    ub[S::IE] += reb;
+    (void)bE;
+}
+
+template <class S>
+__global__ void k_adj_gather(AdjArgs A) {
+    const MeshData &M = A.M;
+    const int ne = M.ne;
+    const size_t nodes = (size_t)ne * S::NP;
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < nodes;
+         gi += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(gi / S::NP), a = (int)(gi - (size_t)e * S::NP);
+        double xb[S::NTR];
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) xb[fld] = A.ubar_part[fld * nodes + gi];
+        // neighbours' contributions to this element's traces
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const int aj = digit<S::D, S::P1>(a, j);
+            const int q = face_q<S::D, S::P1>(a, j);
+#pragma unroll
+            for (int sd = 0; sd < 2; ++sd) {
+                const int s = sd ? 1 : -1;
+                if (neighbour<S::D>(M, e, j, s) < 0) continue;
+                const int face = 2 * j + sd;
+                const double c = sd ? A.ref.lp[aj] : A.ref.lm[aj];
+#pragma unroll
+                for (int fld = 0; fld < S::NTR; ++fld)
+                    xb[fld] += c * A.tadj[(((size_t)face * S::NTR + fld) * ne + e) * S::NFP1 + q];
+            }
+        }
+        double u[S::NF];
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) u[f] = A.U[f * nodes + gi];
+        const int lev = vert_index<S::D>(M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        double brd, brm, bE, bp;
+        load_base<S, double>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
+        split_vjp<S>(u, brd, brm, bE, A.derived[gi], A.derived[nodes + gi], xb[S::NF], xb[S::NF + 1],
+                     xb[S::NF + 2], xb);
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) {
+            const size_t o = f * nodes + gi;
+            double v = A.gamma * xb[f];
+            if (A.beta != 0.0) v += A.beta * A.w[o];
+            if (A.alpha != 0.0) v += A.alpha * A.out[o];
+            A.out[o] = v;
+        }
+    }
+}
+
+// Cloud-water functional J = sum_nodes W_a |K|/2^d rho_c and its gradient
+// dJ/dU (rho_c = rho_m - rho_v from the split at the nodes).
+template <class S>
+__global__ void __launch_bounds__(kRedThreads) k_cloud(AdjArgs A, double *partials) {
+    __shared__ double sh[kRedThreads];
+    const MeshData &M = A.M;
+    const size_t nodes = (size_t)M.ne * S::NP;
+    double acc = 0.0;
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < nodes;
+         gi += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(gi / S::NP), a = (int)(gi - (size_t)e * S::NP);
+        double W = M.jac;
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) W *= A.ref.w[digit<S::D, S::P1>(a, j)];
+        double u[S::NF], ub[S::NF];
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) {
+            u[f] = A.U[f * nodes + gi];
+            ub[f] = 0.0;
+        }
+        const int lev = vert_index<S::D>(M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        double brd, brm, bE, bp;
+        load_base<S, double>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
+        const double T = A.derived[gi], rv = A.derived[nodes + gi];
+        acc += W * (brm + u[1] - rv);
+        ub[1] += W;                                       // d rho_c / d rho_m'
+        split_vjp<S>(u, brd, brm, bE, T, rv, 0.0, -W, 0.0, ub);
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) A.out[f * nodes + gi] = ub[f];
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+}  // namespace dgm

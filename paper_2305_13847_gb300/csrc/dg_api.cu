@@ -206,6 +206,12 @@ struct dg_ctx {
     unsigned long long *flags = nullptr;
     double *partials = nullptr;
     double *rvs_tab = nullptr;
+    // adjoint scratch (allocated on first use): stage states, adjoint vectors,
+    // partial node adjoints, neighbour trace adjoints
+    const AdjLaunchers *LA = nullptr;
+    void *adjX[3] = {nullptr, nullptr, nullptr};
+    double *adjL[3] = {nullptr, nullptr, nullptr};
+    double *ubar_part = nullptr, *tadj = nullptr;
     int nred = 0;
     std::vector<double> z_node, z_face;
     bool base_set = false, state_set = false, derived_valid = false;
@@ -268,7 +274,9 @@ int stage(dg_ctx *c, int mode, const void *Uin, const void *Un, void *Uout, int 
 
 void release(dg_ctx *c) {
     void *ptrs[] = {c->U[0], c->U[1], c->derived, c->trace[0], c->trace[1], c->bnode_d,
-                    c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab};
+                    c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab,
+                    c->adjX[0], c->adjX[1], c->adjX[2], c->adjL[0], c->adjL[1], c->adjL[2],
+                    c->ubar_part, c->tadj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -307,6 +315,51 @@ int upload_base(dg_ctx *c, const double *node_tab, const double *face_tab) {
     }
     c->base_set = true;
     c->derived_valid = false;
+    return DG_OK;
+}
+
+int ensure_adjoint(dg_ctx *c) {
+    if (c->ubar_part) return DG_OK;
+    const size_t state = (size_t)c->nodes * c->nf * sizeof(double);
+    const size_t trace = (size_t)2 * c->cfg.dim * c->ntr * c->ne * c->nfp1 * sizeof(double);
+    int st = DG_OK;
+    for (int i = 0; i < 3 && st == DG_OK; ++i) st = alloc(c, &c->adjX[i], state);
+    for (int i = 0; i < 3 && st == DG_OK; ++i) st = alloc(c, (void **)&c->adjL[i], state);
+    if (st == DG_OK) st = alloc(c, (void **)&c->tadj, trace);
+    if (st == DG_OK) st = alloc(c, (void **)&c->ubar_part, (size_t)c->nodes * c->ntr * sizeof(double));
+    return st;
+}
+
+AdjArgs adj_args(const dg_ctx *c, const void *U, const double *w, double *out, double alpha,
+                 double beta, double gamma) {
+    AdjArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.M = c->M;
+    A.ref = c->ref64;
+    A.U = (const double *)U;
+    A.derived = (const double *)c->derived;
+    A.trace = (const double *)c->trace[0];
+    A.bnode = c->bnode_d;
+    A.bface = c->bface_d;
+    A.w = w;
+    A.ubar_part = c->ubar_part;
+    A.tadj = c->tadj;
+    A.out = out;
+    A.alpha = alpha;
+    A.beta = beta;
+    A.gamma = gamma;
+    return A;
+}
+
+// out = alpha out + beta w + gamma (dR/dU (U))^T w
+int rhs_adjoint_into(dg_ctx *c, const void *U, const double *w, double *out, double alpha,
+                     double beta, double gamma) {
+    c->derived_valid = false;
+    int st = prepare(c, U, 0);
+    if (st != DG_OK) return st;
+    AdjArgs A = adj_args(c, U, w, out, alpha, beta, gamma);
+    if (c->LA->local(A, c->stream) != cudaSuccess) return DG_ECUDA;
+    if (c->LA->gather(A, c->stream) != cudaSuccess) return DG_ECUDA;
     return DG_OK;
 }
 
@@ -370,6 +423,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
         c->nd = c->L32->nd; c->ntr = c->L32->ntr; c->epb = c->L32->epb;
     } else {
         c->L64 = g.dim == 2 ? launchers_d2_f64(g.order, g.rain) : launchers_d3_f64(g.order, g.rain);
+        c->LA = g.dim == 2 ? adj_launchers_d2(g.order, g.rain) : adj_launchers_d3(g.order, g.rain);
         c->nf = c->L64->nf; c->np = c->L64->np; c->nfp1 = c->L64->nfp1;
         c->nd = c->L64->nd; c->ntr = c->L64->ntr; c->epb = c->L64->epb;
     }
@@ -394,6 +448,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     M.kvr = 130.0 * std::tgamma(4.5) / 6.0 * std::pow(M_PI * 8.0e6, -0.125);
     M.jac = 1.0;
     for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
+    M.rain_floor = kRainFloorLin;
     c->ref64 = make_ref<double>(g.order);
     c->ref32 = make_ref<float>(g.order);
 
@@ -712,9 +767,65 @@ int dg_reduce(dg_ctx *c, double out[DG_NREDUCE]) {
     return DG_OK;
 }
 
+int dg_rhs_adjoint(dg_ctx *c, const void *U, const double *w, double *ubar) {
+    if (!c || !U || !w || !ubar || (const void *)ubar == U || ubar == w) return DG_EINVAL;
+    if (c->fp32 || !c->LA) return DG_ENOTIMPL;
+    if (!c->base_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    int st = ensure_adjoint(c);
+    if (st != DG_OK) return st;
+    return rhs_adjoint_into(c, U, w, ubar, 0.0, 0.0, 1.0);
+}
+
 int dg_adjoint_step(dg_ctx *c, double dt, const void *U_n, const double *lam_np1, double *lam_n) {
-    (void)c; (void)dt; (void)U_n; (void)lam_np1; (void)lam_n;
-    return DG_ENOTIMPL;
+    if (!c || !U_n || !lam_np1 || !lam_n || !std::isfinite(dt)) return DG_EINVAL;
+    if ((const void *)lam_n == U_n || lam_n == lam_np1) return DG_EINVAL;
+    if (c->fp32 || !c->LA) return DG_ENOTIMPL;
+    if (!c->base_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    int st = ensure_adjoint(c);
+    if (st != DG_OK) return st;
+    c->derived_valid = false;
+    // forward stages of SSPRK(4,3) from U^n (Shu-Osher form):
+    //   U1 = U^n + dt/2 R(U^n); U2 = U1 + dt/2 R(U1); U3 = 2/3 U^n + 1/3 U2 + dt/6 R(U2)
+    void *X1 = c->adjX[0], *X2 = c->adjX[1], *X3 = c->adjX[2];
+    st = prepare(c, U_n, 0);
+    if (st == DG_OK) st = stage(c, MODE_STAGE, U_n, U_n, X1, 0, 0.0, 1.0, 0.5 * dt);
+    if (st == DG_OK) st = stage(c, MODE_STAGE, X1, X1, X2, 1, 0.0, 1.0, 0.5 * dt);
+    if (st == DG_OK) st = stage(c, MODE_STAGE, X2, U_n, X3, 0, 2.0 / 3.0, 1.0 / 3.0, dt / 6.0);
+    if (st != DG_OK) return st;
+    // reverse: U^{n+1} = U3 + dt/2 R(U3)
+    double *l3 = c->adjL[0], *l2 = c->adjL[1], *l1 = c->adjL[2];
+    st = rhs_adjoint_into(c, X3, lam_np1, l3, 0.0, 1.0, 0.5 * dt);            // l3 = l + dt/2 J3^T l
+    if (st == DG_OK) st = rhs_adjoint_into(c, X2, l3, l2, 0.0, 1.0 / 3.0, dt / 6.0);  // l2
+    if (st == DG_OK) st = rhs_adjoint_into(c, X1, l2, l1, 0.0, 1.0, 0.5 * dt);        // l1
+    if (st != DG_OK) return st;
+    // lam_n = 2/3 l3 + l1 + dt/2 J(U^n)^T l1
+    const size_t bytes = (size_t)c->nodes * c->nf * sizeof(double);
+    if (cudaMemcpyAsync(lam_n, l3, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+        return DG_ECUDA;
+    return rhs_adjoint_into(c, U_n, l1, lam_n, 2.0 / 3.0, 1.0, 0.5 * dt);
+}
+
+int dg_cloud_functional(dg_ctx *c, const void *U, double *J, double *dJdU) {
+    if (!c || !U || !J || !dJdU || (const void *)dJdU == U) return DG_EINVAL;
+    if (c->fp32 || !c->LA) return DG_ENOTIMPL;
+    if (!c->base_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    c->derived_valid = false;
+    int st = prepare(c, U, 0);
+    if (st != DG_OK) return st;
+    AdjArgs A = adj_args(c, U, nullptr, dJdU, 0.0, 0.0, 1.0);
+    if (c->LA->cloud(A, c->partials, c->nred, c->stream) != cudaSuccess) return DG_ECUDA;
+    std::vector<double> h(c->nred);
+    if (cudaMemcpyAsync(h.data(), c->partials, sizeof(double) * c->nred, cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return DG_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    double sum = 0.0;
+    for (int b = 0; b < c->nred; ++b) sum += h[b];
+    *J = sum;
+    return DG_OK;
 }
 
 }  // extern "C"

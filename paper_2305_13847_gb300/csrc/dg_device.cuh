@@ -52,6 +52,13 @@ constexpr double kSevC = 9.1;
 constexpr double kSau = 1.0e-3;
 constexpr double kSac = 1.72;
 
+// Linearisation (adjoint) only: fractional rain powers are differentiated at
+// max(rho_r, kRainFloorLin).  Their derivatives are unbounded as rho_r -> 0+,
+// and the rain that the DG discretisation leaks into cloud-free elements
+// (1e-20 .. 1e-9 kg/m^3) makes the exact linearisation grow without bound over
+// a few dozen steps; below 1e-12 kg/m^3 (1e-9 g/m^3) no rain is physical.
+constexpr double kRainFloorLin = 1e-12;
+
 constexpr int kMaxNewton = 50;
 constexpr double kNewtonTol = 1e-12;
 
@@ -71,6 +78,7 @@ struct MeshData {
     double rho_w;          // <= 0: rho_m + rho_r
     double kvr;            // v0 Gamma(4.5)/6 (pi N0)^(-1/8)
     double jac;            // |K| / 2^d
+    double rain_floor;     // linearisation only: rain powers differentiated at max(rho_r, floor)
 };
 
 template <typename Real>

@@ -129,3 +129,70 @@ const Launchers<float> *launchers_d3_f32(int K, int rain);
         return &t[K - 1][rain ? 1 : 0];                                                \
     }                                                                                  \
     }
+
+// ---------------------------------------------------------------------------
+// Adjoint launchers (float64 only), instantiated in dg_adj_*.cu
+// ---------------------------------------------------------------------------
+#include "dg_adjoint.cuh"
+
+namespace dgm {
+
+struct AdjLaunchers {
+    int ntr;
+    cudaError_t (*local)(const AdjArgs &, cudaStream_t);
+    cudaError_t (*gather)(const AdjArgs &, cudaStream_t);
+    cudaError_t (*cloud)(const AdjArgs &, double *partials, int nblocks, cudaStream_t);
+};
+
+template <class S>
+struct AdjImpl {
+    static constexpr size_t smem = adj_smem_bytes<S>();
+    static cudaError_t local(const AdjArgs &A, cudaStream_t st) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t err = cudaFuncSetAttribute(k_adj_local<S>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            attr = true;
+        }
+        k_adj_local<S><<<(A.M.ne + S::EPB - 1) / S::EPB, S::NT, smem, st>>>(A);
+        return cudaGetLastError();
+    }
+    static cudaError_t gather(const AdjArgs &A, cudaStream_t st) {
+        const size_t nodes = (size_t)A.M.ne * S::NP;
+        k_adj_gather<S><<<grid_for(nodes, 256), 256, 0, st>>>(A);
+        return cudaGetLastError();
+    }
+    static cudaError_t cloud(const AdjArgs &A, double *partials, int nblocks, cudaStream_t st) {
+        k_cloud<S><<<nblocks, kRedThreads, 0, st>>>(A, partials);
+        return cudaGetLastError();
+    }
+    static AdjLaunchers table() {
+        AdjLaunchers L;
+        L.ntr = S::NTR;
+        L.local = &local;
+        L.gather = &gather;
+        L.cloud = &cloud;
+        return L;
+    }
+};
+
+const AdjLaunchers *adj_launchers_d2(int K, int rain);
+const AdjLaunchers *adj_launchers_d3(int K, int rain);
+
+}  // namespace dgm
+
+#define DGM_DEFINE_ADJ_LAUNCHERS(NAME, DIM)                                             \
+    namespace dgm {                                                                    \
+    const AdjLaunchers *NAME(int K, int rain) {                                        \
+        static const AdjLaunchers t[5][2] = {                                          \
+            {AdjImpl<Shape<DIM, 1, false>>::table(), AdjImpl<Shape<DIM, 1, true>>::table()}, \
+            {AdjImpl<Shape<DIM, 2, false>>::table(), AdjImpl<Shape<DIM, 2, true>>::table()}, \
+            {AdjImpl<Shape<DIM, 3, false>>::table(), AdjImpl<Shape<DIM, 3, true>>::table()}, \
+            {AdjImpl<Shape<DIM, 4, false>>::table(), AdjImpl<Shape<DIM, 4, true>>::table()}, \
+            {AdjImpl<Shape<DIM, 5, false>>::table(), AdjImpl<Shape<DIM, 5, true>>::table()}, \
+        };                                                                             \
+        if (K < 1 || K > 5) return nullptr;                                            \
+        return &t[K - 1][rain ? 1 : 0];                                                \
+    }                                                                                  \
+    }

@@ -81,6 +81,8 @@ SIGNATURES = [
     ("dg_adjoint_step", _I, [_VP, ctypes.c_double, _VP, _VP, _VP]),
     ("dg_strerror", ctypes.c_char_p, [_I]),
     ("dg_rhs_noalloc", _I, [ctypes.POINTER(dg_config), _VP, _VP, _VP, _VP, _VP]),
+    ("dg_rhs_adjoint", _I, [_VP, _VP, _VP, _VP]),
+    ("dg_cloud_functional", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
 ]
 
 
@@ -239,7 +241,24 @@ def dg_reduce(ctx):
 
 
 def dg_adjoint_step(ctx, dt, U_n, lam_np1, lam_n):
+    _check(lib().dg_adjoint_step(ctx, float(dt), _addr(U_n), _addr(lam_np1), _addr(lam_n)),
+           "dg_adjoint_step")
+
+
+def dg_adjoint_step_status(ctx, dt, U_n, lam_np1, lam_n):
+    """Raw status of dg_adjoint_step."""
     return lib().dg_adjoint_step(ctx, float(dt), _addr(U_n), _addr(lam_np1), _addr(lam_n))
+
+
+def dg_rhs_adjoint(ctx, U, w, ubar):
+    _check(lib().dg_rhs_adjoint(ctx, _addr(U), _addr(w), _addr(ubar)), "dg_rhs_adjoint")
+
+
+def dg_cloud_functional(ctx, U, dJdU):
+    J = ctypes.c_double(0.0)
+    _check(lib().dg_cloud_functional(ctx, _addr(U), ctypes.byref(J), _addr(dJdU)),
+           "dg_cloud_functional")
+    return J.value
 
 
 def dg_rhs_noalloc(cfg, base_node, base_face, U, dUdt, stream=None):

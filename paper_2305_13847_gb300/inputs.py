@@ -58,7 +58,7 @@ WORKLOADS = {
         radius=(2.0e3, 2.0e3, 2.0e3), amplitude=(1.5, 2.5), noise=0.1),
     "adjoint2d_q4": dict(
         index=4, dim=2, n=(128, 64), L=(20.0e3, 10.0e3), order=4, rain=1,
-        precision="fp64", steps=500, cfl=0.1, centre=(10.0e3, 2.0e3),
+        precision="fp64", steps=500, cfl=0.05, centre=(10.0e3, 2.0e3),
         radius=(2.0e3, 2.0e3), amplitude=(1.5, 2.5), noise=0.0),
 }
 

@@ -248,7 +248,7 @@ def test_status_and_error_paths():
         with pytest.raises(dm.DGError) as ei:
             dm.dg_rhs(ctx, Ud, out)               # no base state yet
         assert ei.value.code == dm.DG_ESTATE
-        assert dm.dg_adjoint_step(ctx, 0.1, None, None, None) == dm.DG_ENOTIMPL
+        assert dm.dg_adjoint_step_status(ctx, 0.1, None, None, None) == dm.DG_EINVAL
     finally:
         dm.dg_free(ctx)
     # a non-finite state is reported as DG_ENONPHYS, the context stays usable
