@@ -237,6 +237,36 @@ def _roofline(info, word, t_total, steps, peak, peak_kind):
             "avg_launch_ms": 1000.0 * launch_s}
 
 
+def measure_ensemble(torch, dm, inputs, args, world, dist):
+    from paper_2305_13847_gb300 import ensemble
+    members = inputs.ensemble_members()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ens = ensemble.open_ensemble(members, stream)
+        try:
+            dts = ensemble.member_dt(ens, members)
+            best, table = ensemble.autotune(ens, dts, stream, steps=1)
+            dm.dg_ensemble_step(ens, args.warmup)
+            ms = ensemble.time_steps(ens, args.steps, stream)
+            st = dm.dg_ensemble_step(ens, 0)
+            dofs = dm.dg_ensemble_dofs(ens)
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            if dist is not None:
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            ks = sorted(set(m["order"] for m in members))
+            return {
+                "workload": "ensemble: %d 2-D warm-rain bubbles, meshes %dx%d..%dx%d, orders %s, "
+                            "FP32-bulk, one persistent launch per stage in a CUDA graph"
+                            % (len(members), min(m["n"][0] for m in members),
+                               min(m["n"][1] for m in members), max(m["n"][0] for m in members),
+                               max(m["n"][1] for m in members), ks),
+                "dofs": dofs, "value": world * dofs * STAGES / (ms / 1000.0), "unit": UNIT,
+                "ms_per_step": ms, "autotuned": best, "candidates": len(table)}
+        finally:
+            dm.dg_ensemble_free(ens)
+
+
 def run_gb300(args):
     import torch
     from paper_2305_13847_gb300 import dgmoist as dm
@@ -304,6 +334,10 @@ def run_gb300(args):
                 "roofline": _roofline(info2, 4, t2, args.steps, peak, peak_kind)}
             dm.dg_free(ctx2)
 
+    # the batched ensemble: 256 uneven 2-D warm-rain bubbles, orders 2-5, FP32-bulk
+    if not args.no_ensemble:
+        extra["ensemble"] = measure_ensemble(torch, dm, inputs, args, world, dist)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -341,6 +375,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurements")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--mesh", default=None,
                     help="override the element counts, e.g. 40,40,20 (profiling runs only)")
     args = ap.parse_args()

@@ -258,6 +258,54 @@ int dg_adjoint_step(dg_ctx *ctx, double dt, const void *U_n, const double *lam_n
  * double; the call synchronises.  DG_ENOTIMPL for DG_FP32_BULK contexts. */
 int dg_cloud_functional(dg_ctx *ctx, const void *U, double *J, double *dJdU);
 
+/* ---- Batched ensemble (SURVEY NEXT-3 form; the paper runs one case at a time) ----
+ * Many independent 2-D meshes (any sizes, orders 1..5, rain on or off),
+ * FP32-bulk, advanced together: each SSPRK(4,3) stage is one persistent
+ * launch whose CTAs take element tiles of any member from an atomic work
+ * counter and run the single-mesh stage code for that member's order; one
+ * step (counter resets + four stage launches) is captured in a CUDA graph
+ * and replayed.  Results are bitwise those of dg_step on each member. */
+typedef struct dg_ensemble dg_ensemble;
+
+/* Create n members (cfgs[i].dim == 2, precision DG_FP32_BULK) and build
+ * each one's warm bubble (dg_init_bubble with bubbles[i], no noise).  Work
+ * goes to cuda_stream, which must not be the legacy default stream (the
+ * steps are captured in a graph); NULL creates a private stream.
+ * Errors: DG_EINVAL, DG_ENOMEM, DG_ECUDA. */
+int dg_ensemble_create(dg_ensemble **out, int n, const dg_config *cfgs, const dg_bubble *bubbles,
+                       void *cuda_stream);
+
+/* Member i's context (owned by the ensemble; use it for dg_get_state,
+ * dg_reduce, ...; do not free it). */
+int dg_ensemble_member(dg_ensemble *ens, int i, dg_ctx **ctx);
+
+/* Total DOFs over all members. */
+long long dg_ensemble_dofs(const dg_ensemble *ens);
+
+/* Set the members' time steps dt[n] (s, host) and the launch shape:
+ * blocks_per_sm persistent CTAs per SM (capped by occupancy), the order of
+ * work items (0 member by member, 1 round-robin over members, 2 largest
+ * members first) and the register budget regs (0: 128 registers per thread,
+ * two CTAs per SM; 1: 80 registers, three CTAs per SM); re-derives each
+ * member's split and traces if needed and re-captures the step graph.
+ * Synchronises. */
+int dg_ensemble_configure(dg_ensemble *ens, const double *dt, int blocks_per_sm, int item_order,
+                          int regs);
+
+/* The persistent grid size and the number of work items (element tiles)
+ * of the captured step. */
+int dg_ensemble_launch_shape(const dg_ensemble *ens, int *grid, int *n_items);
+
+/* Replay the captured step nsteps times.  dg_ensemble_step synchronises and
+ * returns the worst member status (DG_ENONPHYS before DG_ENOCONV);
+ * dg_ensemble_step_async only enqueues.  DG_ESTATE before
+ * dg_ensemble_configure. */
+int dg_ensemble_step(dg_ensemble *ens, int nsteps);
+int dg_ensemble_step_async(dg_ensemble *ens, int nsteps);
+
+/* Free the ensemble and its members (NULL is ignored). */
+void dg_ensemble_free(dg_ensemble *ens);
+
 /* Text for a status code. */
 const char *dg_strerror(int code);
 

@@ -1,0 +1,51 @@
+// Private: the context structure shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "dg_launch.cuh"
+#include "dgmoist.h"
+
+using namespace dgm;
+
+struct dg_ctx {
+    dg_config cfg;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int fp32 = 0;
+    const Launchers<double> *L64 = nullptr;
+    const Launchers<float> *L32 = nullptr;
+    int nf = 0, np = 0, nfp1 = 0, nd = 0, ntr = 0, epb = 0;
+    long long ne = 0, nodes = 0;
+    size_t rsz = 8;
+    MeshData M;
+    RefData<double> ref64;
+    RefData<float> ref32;
+    void *U[2] = {nullptr, nullptr};   // U^n, work state
+    void *derived = nullptr;
+    void *trace[2] = {nullptr, nullptr};
+    double *bnode_d = nullptr, *bface_d = nullptr;
+    void *bnode_r = nullptr, *bface_r = nullptr;
+    unsigned long long *flags = nullptr;
+    double *partials = nullptr;
+    double *rvs_tab = nullptr;
+    // adjoint scratch (allocated on first use): stage states, adjoint vectors,
+    // partial node adjoints, neighbour trace adjoints
+    const AdjLaunchers *LA = nullptr;
+    void *adjX[3] = {nullptr, nullptr, nullptr};
+    double *adjL[3] = {nullptr, nullptr, nullptr};
+    double *ubar_part = nullptr, *tadj = nullptr;
+    int nred = 0;
+    std::vector<double> z_node, z_face;
+    bool base_set = false, state_set = false, derived_valid = false;
+    int parity = 0;  // trace buffer holding the traces of U^n
+    size_t device_bytes = 0;
+};
+
+
+namespace dgm {
+// Launch helpers of dg_api.cu used by other units.
+int ctx_prepare(dg_ctx *c, const void *U, int tb);
+}

@@ -564,17 +564,18 @@ __device__ __forceinline__ Real interp_face(const Real *v, const Real *ls, int j
 // k_prepare: split at every node and traces of every face
 // ---------------------------------------------------------------------------
 template <class S, typename Real>
-__device__ __forceinline__ void write_traces(const KArgs<Real> &A, const Real *s_tr, Real *trace_out) {
+__device__ __forceinline__ void write_traces(const KArgs<Real> &A, const RefData<Real> &ref,
+                                             const Real *s_tr, Real *trace_out, int bidx) {
     const int ne = A.M.ne;
     for (int item = threadIdx.x; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
         const int el = item / (S::NFACE * S::NFP1);
         const int rem = item - el * (S::NFACE * S::NFP1);
         const int face = rem / S::NFP1;
         const int q = rem - face * S::NFP1;
-        const int e = blockIdx.x * S::EPB + el;
+        const int e = bidx * S::EPB + el;
         if (e >= ne) continue;
         const int j = face >> 1;
-        const Real *ls = (face & 1) ? A.ref.lp : A.ref.lm;
+        const Real *ls = (face & 1) ? ref.lp : ref.lm;
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld) {
             const Real *v = s_tr + (size_t)fld * S::EPB * S::NP + el * S::NP;
@@ -658,7 +659,7 @@ __global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
         split_and_store<S, Real>(A, u, e, a, s_tr, t);
     }
     __syncthreads();
-    write_traces<S, Real>(A, s_tr, A.trace_out);
+    write_traces<S, Real>(A, A.ref, s_tr, A.trace_out, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -687,13 +688,14 @@ __device__ __forceinline__ void load_base(const Real *tab, int nlev, int lev, Re
 // shared memory, neighbour trace from the trace buffer, slip-wall ghost state
 // m+ = m- - 2 (m-.n) n with everything else copied.
 template <class S, typename Real, int J>
-__device__ __forceinline__ void face_point(const KArgs<Real> &A, const Real *s_tr, Real *s_fh, int el2,
-                                           int face, int q, int e2) {
+__device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<Real> &ref,
+                                           const Real *s_tr, Real *s_fh, int el2, int face, int q,
+                                           int e2) {
     constexpr int STR = S::EPB * S::NP;
     const MeshData &M = A.M;
     const int ne = M.ne;
     const int s = (face & 1) ? 1 : -1;
-    const Real *ls = (face & 1) ? A.ref.lp : A.ref.lm;
+    const Real *ls = (face & 1) ? ref.lp : ref.lm;
     Real tm[S::NTR], tp[S::NTR];
     if (sizeof(Real) == sizeof(double)) {
         // float64 form: the own trace was written with the same interpolation
@@ -744,9 +746,11 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const Real *s_t
         out[f * S::NFP1] = hs * (Fm[f] + Fp[f]) + Real(0.5) * lam * (tm[f] - tp[f]);
 }
 
+// One tile of EPB consecutive elements (tile index bidx) of the stage
+// kernel; every thread of the CTA takes part (the body has barriers).
 template <class S, typename Real, int MODE>
-__global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<Real> &ref, int bidx,
+                                            unsigned char *smem_raw) {
     constexpr int STR = S::EPB * S::NP;
     Real *s_tr = reinterpret_cast<Real *>(smem_raw);          // [NTR][STR]
     Real *s_fl = s_tr + S::NTR * STR;                         // [D][NF][STR]
@@ -756,7 +760,7 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
     const size_t nodes = (size_t)ne * S::NP;
     const int t = threadIdx.x;
     const int el = t / S::NP, a = t - el * S::NP;
-    const int e = blockIdx.x * S::EPB + el;
+    const int e = bidx * S::EPB + el;
     const bool valid = (t < STR) && (e < ne);
 
     Real u[S::NF], R[S::NF];
@@ -812,7 +816,7 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
                 const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
                 Real acc = Real(0);
 #pragma unroll
-                for (int i = 0; i < S::P1; ++i) acc = fma(A.ref.dhat[aj][i], fl[i * st], acc);
+                for (int i = 0; i < S::P1; ++i) acc = fma(ref.dhat[aj][i], fl[i * st], acc);
                 R[f] = fma(sc, acc, R[f]);
             }
         }
@@ -824,12 +828,12 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
         const int rem = item - el2 * (S::NFACE * S::NFP1);
         const int face = rem / S::NFP1;
         const int q = rem - face * S::NFP1;
-        const int e2 = blockIdx.x * S::EPB + el2;
+        const int e2 = bidx * S::EPB + el2;
         if (e2 >= ne) continue;
         switch (face >> 1) {
-            case 0: face_point<S, Real, 0>(A, s_tr, s_fh, el2, face, q, e2); break;
-            case 1: face_point<S, Real, 1>(A, s_tr, s_fh, el2, face, q, e2); break;
-            default: face_point<S, Real, (S::D == 3 ? 2 : 1)>(A, s_tr, s_fh, el2, face, q, e2); break;
+            case 0: face_point<S, Real, 0>(A, ref, s_tr, s_fh, el2, face, q, e2); break;
+            case 1: face_point<S, Real, 1>(A, ref, s_tr, s_fh, el2, face, q, e2); break;
+            default: face_point<S, Real, (S::D == 3 ? 2 : 1)>(A, ref, s_tr, s_fh, el2, face, q, e2); break;
         }
     }
     __syncthreads();
@@ -843,7 +847,7 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
             const Real sc = Real(M.two_over_h[j]);
             const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * S::NF) * S::NFP1 + q;
             const Real *fp = s_fh + ((el * S::NFACE + 2 * j + 1) * S::NF) * S::NFP1 + q;
-            const Real cm = sc * A.ref.liftm[aj], cp = sc * A.ref.liftp[aj];
+            const Real cm = sc * ref.liftm[aj], cp = sc * ref.liftp[aj];
 #pragma unroll
             for (int f = 0; f < S::NF; ++f)
                 R[f] -= cp * fp[f * S::NFP1] + cm * fm[f * S::NFP1];
@@ -866,8 +870,14 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
     }
     if (MODE == MODE_STAGE) {
         __syncthreads();
-        write_traces<S, Real>(A, s_tr, A.trace_out);
+        write_traces<S, Real>(A, ref, s_tr, A.trace_out, bidx);
     }
+}
+
+template <class S, typename Real, int MODE>
+__global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_block<S, Real, MODE>(A, A.ref, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,386 @@
+// Batched ensemble: many independent 2-D meshes of different sizes and
+// orders advanced together, one persistent launch per SSPRK(4,3) stage.
+//
+// Work items are tiles (EPB consecutive elements) of any member; CTAs of a
+// persistent grid take items from an atomic counter, copy the member's
+// kernel arguments to shared memory and run the same tile code as the
+// single-mesh stage kernel (stage_block), specialised by the member's order.
+// One step (counter resets + four stage launches) is captured once in a CUDA
+// graph and replayed.  Members are independent, so there is no exchange
+// between them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dg_ctx.h"
+
+using namespace dgm;
+
+namespace {
+
+constexpr int kEnsThreads = 256;
+
+struct EnsMember {
+    KArgs<float> args;   // mesh, reference tables, derived / base / table / flag pointers
+    float *U[2];         // U^n, work stage
+    float *trace[2];
+    float g_half, g_sixth;
+    int K, rain;
+};
+
+template <int K, bool RAIN>
+struct EnsShape : Shape<2, K, RAIN> {};
+
+template <class S>
+constexpr size_t ens_smem() { return stage_smem_bytes<S, float>(); }
+
+constexpr size_t max2(size_t a, size_t b) { return a > b ? a : b; }
+
+constexpr size_t kEnsSmem =
+    max2(max2(max2(ens_smem<EnsShape<1, true>>(), ens_smem<EnsShape<2, true>>()),
+              max2(ens_smem<EnsShape<3, true>>(), ens_smem<EnsShape<4, true>>())),
+         max2(ens_smem<EnsShape<5, true>>(),
+              max2(max2(ens_smem<EnsShape<1, false>>(), ens_smem<EnsShape<2, false>>()),
+                   max2(max2(ens_smem<EnsShape<3, false>>(), ens_smem<EnsShape<4, false>>()),
+                        ens_smem<EnsShape<5, false>>()))));
+
+// reference-element tables per order (identical for all members of one order)
+__constant__ RefData<float> c_ens_ref[5];
+
+template <int K, bool RAIN>
+__device__ __noinline__ void ens_tile(const KArgs<float> &A, int tile, unsigned char *smem) {
+    static_assert(EnsShape<K, RAIN>::NT == kEnsThreads, "2-D tiles use 256 threads for every order");
+    stage_block<EnsShape<K, RAIN>, float, MODE_STAGE>(A, c_ens_ref[K - 1], tile, smem);
+}
+
+// MINB: CTAs per SM the register budget is sized for (2: 128 registers per
+// thread, 3: 80); one of the autotuner's knobs.
+template <int MINB>
+__global__ void __launch_bounds__(kEnsThreads, MINB) k_ens_stage(const EnsMember *members,
+                                                             const int2 *items, int n_items,
+                                                             int stage, unsigned int *counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ KArgs<float> s_args;
+    __shared__ int s_item, s_k, s_rain;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int2 wi = items[it];
+        const EnsMember *m = members + wi.x;
+        {
+            const int *src = reinterpret_cast<const int *>(&m->args);
+            int *dst = reinterpret_cast<int *>(&s_args);
+            for (int i = threadIdx.x; i < (int)(sizeof(KArgs<float>) / sizeof(int)); i += blockDim.x)
+                dst[i] = src[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // SSPRK(4,3) Shu-Osher stages; the traces of U^n sit in trace[0] at each step start
+            float *Un = m->U[0], *Uw = m->U[1];
+            switch (stage) {
+                case 0: s_args.Uin = Un; s_args.Un = Un; s_args.Uout = Uw;
+                        s_args.alpha = 0.0f; s_args.beta = 1.0f; s_args.gdt = m->g_half;
+                        s_args.trace_in = m->trace[0]; s_args.trace_out = m->trace[1]; break;
+                case 1: s_args.Uin = Uw; s_args.Un = Uw; s_args.Uout = Uw;
+                        s_args.alpha = 0.0f; s_args.beta = 1.0f; s_args.gdt = m->g_half;
+                        s_args.trace_in = m->trace[1]; s_args.trace_out = m->trace[0]; break;
+                case 2: s_args.Uin = Uw; s_args.Un = Un; s_args.Uout = Uw;
+                        s_args.alpha = (float)(2.0 / 3.0); s_args.beta = (float)(1.0 / 3.0);
+                        s_args.gdt = m->g_sixth;
+                        s_args.trace_in = m->trace[0]; s_args.trace_out = m->trace[1]; break;
+                default: s_args.Uin = Uw; s_args.Un = Uw; s_args.Uout = Un;
+                         s_args.alpha = 0.0f; s_args.beta = 1.0f; s_args.gdt = m->g_half;
+                         s_args.trace_in = m->trace[1]; s_args.trace_out = m->trace[0]; break;
+            }
+            s_k = m->K;
+            s_rain = m->rain;
+        }
+        __syncthreads();
+        const int tile = wi.y;
+        if (s_rain) {
+            switch (s_k) {
+                case 1: ens_tile<1, true>(s_args, tile, smem_raw); break;
+                case 2: ens_tile<2, true>(s_args, tile, smem_raw); break;
+                case 3: ens_tile<3, true>(s_args, tile, smem_raw); break;
+                case 4: ens_tile<4, true>(s_args, tile, smem_raw); break;
+                default: ens_tile<5, true>(s_args, tile, smem_raw); break;
+            }
+        } else {
+            switch (s_k) {
+                case 1: ens_tile<1, false>(s_args, tile, smem_raw); break;
+                case 2: ens_tile<2, false>(s_args, tile, smem_raw); break;
+                case 3: ens_tile<3, false>(s_args, tile, smem_raw); break;
+                case 4: ens_tile<4, false>(s_args, tile, smem_raw); break;
+                default: ens_tile<5, false>(s_args, tile, smem_raw); break;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int epb_of(int K, int rain) {
+    switch (K) {
+        case 1: return rain ? EnsShape<1, true>::EPB : EnsShape<1, false>::EPB;
+        case 2: return rain ? EnsShape<2, true>::EPB : EnsShape<2, false>::EPB;
+        case 3: return rain ? EnsShape<3, true>::EPB : EnsShape<3, false>::EPB;
+        case 4: return rain ? EnsShape<4, true>::EPB : EnsShape<4, false>::EPB;
+        default: return rain ? EnsShape<5, true>::EPB : EnsShape<5, false>::EPB;
+    }
+}
+
+}  // namespace
+
+struct dg_ensemble {
+    int n = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<dg_ctx *> members;
+    std::vector<double> dt;
+    std::vector<int> tiles;          // tiles per member
+    EnsMember *d_members = nullptr;
+    int2 *d_items = nullptr;
+    int n_items = 0;
+    unsigned int *d_counters = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int blocks_per_sm = 2;
+    int item_order = 1;
+    int regs = 0;                    // 0: k_ens_stage<2>, 1: k_ens_stage<3>
+    int sm_count = 0;
+    int grid = 0;
+    long long dofs = 0;
+};
+
+namespace {
+
+void destroy_graph(dg_ensemble *E) {
+    if (E->exec) cudaGraphExecDestroy(E->exec);
+    if (E->graph) cudaGraphDestroy(E->graph);
+    E->exec = nullptr;
+    E->graph = nullptr;
+}
+
+// Upload the member table and the item list (order: 0 member-major,
+// 1 round-robin over members, 2 largest members first); capture one step.
+int build(dg_ensemble *E) {
+    destroy_graph(E);
+    std::vector<EnsMember> h(E->n);
+    for (int i = 0; i < E->n; ++i) {
+        dg_ctx *c = E->members[i];
+        EnsMember &m = h[i];
+        std::memset(&m, 0, sizeof(m));
+        KArgs<float> &A = m.args;
+        A.M = c->M;
+        A.ref = c->ref32;
+        A.derived = (float *)c->derived;
+        A.bnode = (const float *)c->bnode_r;
+        A.bface = (const float *)c->bface_r;
+        A.bnode_d = c->bnode_d;
+        A.rvs_tab = c->rvs_tab;
+        A.flags = c->flags;
+        m.U[0] = (float *)c->U[0];
+        m.U[1] = (float *)c->U[1];
+        m.trace[0] = (float *)c->trace[0];
+        m.trace[1] = (float *)c->trace[1];
+        m.g_half = (float)(0.5 * E->dt[i]);
+        m.g_sixth = (float)(E->dt[i] / 6.0);
+        m.K = c->cfg.order;
+        m.rain = c->cfg.rain;
+    }
+    {
+        RefData<float> refs[5];
+        std::memset(refs, 0, sizeof(refs));
+        for (int i = 0; i < E->n; ++i) refs[E->members[i]->cfg.order - 1] = E->members[i]->ref32;
+        if (cudaMemcpyToSymbolAsync(c_ens_ref, refs, sizeof(refs), 0, cudaMemcpyHostToDevice,
+                                    E->stream) != cudaSuccess)
+            return DG_ECUDA;
+    }
+    std::vector<int2> items;
+    std::vector<int> order(E->n);
+    for (int i = 0; i < E->n; ++i) order[i] = i;
+    if (E->item_order == 2)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return E->members[a]->nodes > E->members[b]->nodes;
+        });
+    if (E->item_order == 1) {
+        int maxt = 0;
+        for (int i = 0; i < E->n; ++i) maxt = std::max(maxt, E->tiles[i]);
+        for (int t = 0; t < maxt; ++t)
+            for (int i : order)
+                if (t < E->tiles[i]) items.push_back(make_int2(i, t));
+    } else {
+        for (int i : order)
+            for (int t = 0; t < E->tiles[i]; ++t) items.push_back(make_int2(i, t));
+    }
+    E->n_items = (int)items.size();
+    if (E->d_members) cudaFree(E->d_members);
+    if (E->d_items) cudaFree(E->d_items);
+    E->d_members = nullptr;
+    E->d_items = nullptr;
+    if (cudaMalloc(&E->d_members, sizeof(EnsMember) * E->n) != cudaSuccess) return DG_ENOMEM;
+    if (cudaMalloc(&E->d_items, sizeof(int2) * items.size()) != cudaSuccess) return DG_ENOMEM;
+    if (cudaMemcpyAsync(E->d_members, h.data(), sizeof(EnsMember) * E->n, cudaMemcpyHostToDevice,
+                        E->stream) != cudaSuccess)
+        return DG_ECUDA;
+    if (cudaMemcpyAsync(E->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                        E->stream) != cudaSuccess)
+        return DG_ECUDA;
+    if (cudaStreamSynchronize(E->stream) != cudaSuccess) return DG_ECUDA;
+
+    auto kern = E->regs ? k_ens_stage<3> : k_ens_stage<2>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsSmem) !=
+        cudaSuccess)
+        return DG_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kEnsThreads, kEnsSmem) !=
+        cudaSuccess)
+        return DG_ECUDA;
+    const int bps = std::max(1, std::min(E->blocks_per_sm, per_sm));
+    const int grid = bps * E->sm_count;
+    E->grid = grid;
+
+    if (cudaStreamBeginCapture(E->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return DG_ECUDA;
+    cudaError_t err = cudaMemsetAsync(E->d_counters, 0, 4 * sizeof(unsigned int), E->stream);
+    for (int s = 0; s < 4 && err == cudaSuccess; ++s) {
+        kern<<<grid, kEnsThreads, kEnsSmem, E->stream>>>(E->d_members, E->d_items, E->n_items, s,
+                                                         E->d_counters + s);
+        err = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t end = cudaStreamEndCapture(E->stream, &g);
+    if (err != cudaSuccess || end != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return DG_ECUDA;
+    }
+    E->graph = g;
+    if (cudaGraphInstantiate(&E->exec, g, 0) != cudaSuccess) return DG_ECUDA;
+    return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_ensemble_create(dg_ensemble **out, int n, const dg_config *cfgs, const dg_bubble *bubbles,
+                       void *cuda_stream) {
+    if (!out || n < 1 || !cfgs || !bubbles) return DG_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (cfgs[i].dim != 2 || cfgs[i].precision != DG_FP32_BULK) return DG_EINVAL;
+    dg_ensemble *E = new (std::nothrow) dg_ensemble();
+    if (!E) return DG_ENOMEM;
+    E->n = n;
+    cudaGetDevice(&E->device);
+    cudaDeviceGetAttribute(&E->sm_count, cudaDevAttrMultiProcessorCount, E->device);
+    if (cuda_stream) {
+        E->stream = (cudaStream_t)cuda_stream;
+    } else {
+        // graph capture needs a stream other than the legacy default stream
+        if (cudaStreamCreateWithFlags(&E->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete E;
+            return DG_ECUDA;
+        }
+        E->own_stream = true;
+    }
+    int st = DG_OK;
+    for (int i = 0; i < n && st == DG_OK; ++i) {
+        dg_ctx *c = nullptr;
+        st = dg_init_mesh(&c, &cfgs[i], E->stream);
+        if (st == DG_OK) {
+            E->members.push_back(c);
+            st = dg_init_bubble(c, &bubbles[i], nullptr, DG_HOST);
+        }
+        if (st == DG_OK) {
+            E->tiles.push_back((int)((c->ne + epb_of(c->cfg.order, c->cfg.rain) - 1) /
+                                     epb_of(c->cfg.order, c->cfg.rain)));
+            E->dofs += c->nodes * c->nf;
+        }
+    }
+    if (st == DG_OK && cudaMalloc(&E->d_counters, 4 * sizeof(unsigned int)) != cudaSuccess) st = DG_ENOMEM;
+    if (st != DG_OK) {
+        dg_ensemble_free(E);
+        return st;
+    }
+    E->dt.assign(n, 0.0);
+    *out = E;
+    return DG_OK;
+}
+
+void dg_ensemble_free(dg_ensemble *E) {
+    if (!E) return;
+    cudaStreamSynchronize(E->stream);
+    destroy_graph(E);
+    for (dg_ctx *c : E->members) dg_free(c);
+    if (E->d_members) cudaFree(E->d_members);
+    if (E->d_items) cudaFree(E->d_items);
+    if (E->d_counters) cudaFree(E->d_counters);
+    if (E->own_stream) cudaStreamDestroy(E->stream);
+    delete E;
+}
+
+int dg_ensemble_member(dg_ensemble *E, int i, dg_ctx **ctx) {
+    if (!E || !ctx || i < 0 || i >= E->n) return DG_EINVAL;
+    *ctx = E->members[i];
+    return DG_OK;
+}
+
+long long dg_ensemble_dofs(const dg_ensemble *E) { return E ? E->dofs : 0; }
+
+int dg_ensemble_launch_shape(const dg_ensemble *E, int *grid, int *n_items) {
+    if (!E || !grid || !n_items) return DG_EINVAL;
+    *grid = E->grid;
+    *n_items = E->n_items;
+    return DG_OK;
+}
+
+int dg_ensemble_configure(dg_ensemble *E, const double *dt, int blocks_per_sm, int item_order,
+                          int regs) {
+    if (!E || !dt || blocks_per_sm < 1 || item_order < 0 || item_order > 2) return DG_EINVAL;
+    if (regs != 0 && regs != 1) return DG_EINVAL;
+    E->regs = regs;
+    for (int i = 0; i < E->n; ++i) {
+        if (!(dt[i] > 0.0)) return DG_EINVAL;
+        E->dt[i] = dt[i];
+    }
+    E->blocks_per_sm = blocks_per_sm;
+    E->item_order = item_order;
+    // each member starts a step with the split and traces of U^n in trace buffer 0
+    for (dg_ctx *c : E->members) {
+        if (!c->derived_valid || c->parity != 0) {
+            const int st = ctx_prepare(c, c->U[0], 0);
+            if (st != DG_OK) return st;
+            c->parity = 0;
+            c->derived_valid = true;
+        }
+    }
+    return build(E);
+}
+
+int dg_ensemble_step_async(dg_ensemble *E, int nsteps) {
+    if (!E || nsteps < 0) return DG_EINVAL;
+    if (!E->exec) return DG_ESTATE;
+    for (int s = 0; s < nsteps; ++s)
+        if (cudaGraphLaunch(E->exec, E->stream) != cudaSuccess) return DG_ECUDA;
+    return DG_OK;
+}
+
+int dg_ensemble_step(dg_ensemble *E, int nsteps) {
+    int st = dg_ensemble_step_async(E, nsteps);
+    if (st != DG_OK) return st;
+    int worst = DG_OK;
+    for (dg_ctx *c : E->members) {
+        const int s = dg_check_status(c, nullptr);
+        if (s == DG_ECUDA) return s;
+        if (s == DG_ENONPHYS || (s == DG_ENOCONV && worst == DG_OK)) worst = s;
+    }
+    return worst;
+}
+
+}  // extern "C"

@@ -83,6 +83,14 @@ SIGNATURES = [
     ("dg_rhs_noalloc", _I, [ctypes.POINTER(dg_config), _VP, _VP, _VP, _VP, _VP]),
     ("dg_rhs_adjoint", _I, [_VP, _VP, _VP, _VP]),
     ("dg_cloud_functional", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
+    ("dg_ensemble_create", _I, [ctypes.POINTER(_VP), _I, _VP, _VP, _VP]),
+    ("dg_ensemble_member", _I, [_VP, _I, ctypes.POINTER(_VP)]),
+    ("dg_ensemble_dofs", ctypes.c_longlong, [_VP]),
+    ("dg_ensemble_configure", _I, [_VP, _VP, _I, _I, _I]),
+    ("dg_ensemble_launch_shape", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("dg_ensemble_step", _I, [_VP, _I]),
+    ("dg_ensemble_step_async", _I, [_VP, _I]),
+    ("dg_ensemble_free", None, [_VP]),
 ]
 
 
@@ -275,3 +283,48 @@ def dg_rhs_noalloc_status(cfg, base_node, base_face, U, dUdt, stream=None):
 
 def dg_strerror(code):
     return lib().dg_strerror(code).decode()
+
+
+def dg_ensemble_create(cfgs, bubbles, stream=None):
+    n = len(cfgs)
+    ca = (dg_config * n)(*cfgs)
+    ba = (dg_bubble * n)(*bubbles)
+    ens = _VP()
+    _check(lib().dg_ensemble_create(ctypes.byref(ens), n, ctypes.cast(ca, _VP), ctypes.cast(ba, _VP),
+                                    _stream_handle(stream)), "dg_ensemble_create")
+    return ens
+
+
+def dg_ensemble_member(ens, i):
+    ctx = _VP()
+    _check(lib().dg_ensemble_member(ens, int(i), ctypes.byref(ctx)), "dg_ensemble_member")
+    return ctx
+
+
+def dg_ensemble_dofs(ens):
+    return int(lib().dg_ensemble_dofs(ens))
+
+
+def dg_ensemble_configure(ens, dt, blocks_per_sm, item_order, regs):
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    _check(lib().dg_ensemble_configure(ens, _addr(dt), int(blocks_per_sm), int(item_order), int(regs)),
+           "dg_ensemble_configure")
+
+
+def dg_ensemble_launch_shape(ens):
+    g, n = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().dg_ensemble_launch_shape(ens, ctypes.byref(g), ctypes.byref(n)),
+           "dg_ensemble_launch_shape")
+    return g.value, n.value
+
+
+def dg_ensemble_step(ens, nsteps):
+    _check(lib().dg_ensemble_step(ens, int(nsteps)), "dg_ensemble_step")
+
+
+def dg_ensemble_step_async(ens, nsteps):
+    _check(lib().dg_ensemble_step_async(ens, int(nsteps)), "dg_ensemble_step_async")
+
+
+def dg_ensemble_free(ens):
+    lib().dg_ensemble_free(ens)

@@ -1,0 +1,64 @@
+"""Batched ensemble of independent warm bubbles: set-up and launch-shape autotuner.
+
+The stepping runs in the CUDA library (dg_ensemble_*): one persistent
+launch per stage, captured in a CUDA graph.  This module marshals the
+member descriptions (paper_2305_13847_gb300.inputs.ensemble_members), picks
+each member's time step from its own wave speed, and times the library's
+launch-shape knobs -- persistent CTAs per SM, work-item order, register
+budget -- keeping the fastest and writing the measured table as JSON.
+"""
+import itertools
+import json
+import time
+
+import torch
+
+from . import dgmoist as dm
+from . import workloads
+
+
+def open_ensemble(members, stream=None):
+    cfgs = [workloads.config_for(m) for m in members]
+    bubs = [workloads.bubble_for(m) for m in members]
+    return dm.dg_ensemble_create(cfgs, bubs, stream)
+
+
+def member_dt(ens, members):
+    """dt_i = cfl_i * min h / max(|u| + v_r + c_m) of member i's initial state."""
+    dts = []
+    for i, m in enumerate(members):
+        ctx = dm.dg_ensemble_member(ens, i)
+        lam = dm.dg_reduce(ctx)[5]
+        dts.append(m["cfl"] * min(L / n for L, n in zip(m["L"], m["n"])) / lam)
+    return dts
+
+
+def time_steps(ens, steps, stream):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dm.dg_ensemble_step_async(ens, steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def autotune(ens, dt, stream, steps=2, json_path=None,
+             blocks_per_sm=(1, 2, 3), orders=(0, 1, 2), regs=(0, 1)):
+    """Time every launch shape for `steps` steps (after one warm-up step);
+    configure the fastest and return (best, table)."""
+    table = []
+    for r, b, o in itertools.product(regs, blocks_per_sm, orders):
+        dm.dg_ensemble_configure(ens, dt, b, o, r)
+        grid, items = dm.dg_ensemble_launch_shape(ens)
+        dm.dg_ensemble_step(ens, 1)
+        ms = time_steps(ens, steps, stream)
+        table.append({"regs": r, "blocks_per_sm": b, "item_order": o, "grid": grid,
+                      "items": items, "ms_per_step": ms})
+    best = min(table, key=lambda t: t["ms_per_step"])
+    dm.dg_ensemble_configure(ens, dt, best["blocks_per_sm"], best["item_order"], best["regs"])
+    if json_path:
+        with open(json_path, "w") as f:
+            json.dump({"when": time.strftime("%Y-%m-%dT%H:%M:%S"), "device": torch.cuda.get_device_name(),
+                       "dofs": dm.dg_ensemble_dofs(ens), "best": best, "table": table}, f, indent=1)
+    return best, table
