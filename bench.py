@@ -287,7 +287,7 @@ def run_gb300(args):
 
     stream = torch.cuda.current_stream()
     peak, peak_kind = measured_peaks()
-    word = 4 if args.precision == "fp32_bulk" else 8
+    word = 4 if args.precision.startswith("fp32") else 8
     w, ctx, info, dt = _open(dm, workloads, inputs, WORKLOAD, args.precision, stream, args.mesh)
 
     sampler = ClockSampler(local)
@@ -321,14 +321,18 @@ def run_gb300(args):
     # the FP32-bulk form: its own workload (128x128x64, Q3) and the same mesh
     extra = {}
     if args.precision == "fp64" and not args.no_fp32:
-        for key, name, mesh in (("fp32_bulk", "rain3d_q3_fp32", None),
-                                ("fp32_bulk_same_mesh", WORKLOAD, args.mesh)):
-            w2, ctx2, info2, dt2 = _open(dm, workloads, inputs, name, "fp32_bulk", stream, mesh)
+        forms = {"fp32_bulk": "float32 state and flux, float64 split",
+                 "fp32_pert": "float32 throughout, split in perturbation variables"}
+        for key, name, mesh, form in (("fp32_bulk", "rain3d_q3_fp32", None, "fp32_bulk"),
+                                      ("fp32_bulk_same_mesh", WORKLOAD, args.mesh, "fp32_bulk"),
+                                      ("fp32_pert", "rain3d_q3_fp32", None, "fp32_pert")):
+            w2, ctx2, info2, dt2 = _open(dm, workloads, inputs, name, form, stream, mesh)
             t2, sm2 = _measure(torch, dm, ctx2, info2, dt2, args.steps, args.warmup, stream, barrier,
                                dist)
             extra[key] = {
-                "workload": "%s: %s hex, Q%d, 7 fields, %d DOFs, float32 state and flux, float64 split"
-                            % (name, "x".join(map(str, w2["n"])), w2["order"], info2.n_dofs),
+                "workload": "%s: %s hex, Q%d, 7 fields, %d DOFs, %s"
+                            % (name, "x".join(map(str, w2["n"])), w2["order"], info2.n_dofs,
+                               forms[form]),
                 "value": world * info2.n_dofs * STAGES * args.steps / t2, "unit": UNIT,
                 "ms_per_step": 1000.0 * t2 / args.steps,
                 "roofline": _roofline(info2, 4, t2, args.steps, peak, peak_kind)}
@@ -372,7 +376,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk", "fp32_pert"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurements")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")

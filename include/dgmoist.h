@@ -67,6 +67,7 @@ extern "C" {
 
 #define DG_FP64 0
 #define DG_FP32_BULK 1
+#define DG_FP32_PERT 2
 
 #define DG_HOST 0
 #define DG_DEVICE 1
@@ -83,8 +84,12 @@ typedef struct dg_config {
     double L[3];        /* domain lengths in m (L[2] unused for dim 2) */
     int periodic_mask;  /* bit j set: direction j periodic; the vertical is always walls */
     int rain;           /* 0: no rain (3+d fields); 1: warm rain (4+d fields) */
-    int precision;      /* DG_FP64, or DG_FP32_BULK: float state and flux arithmetic,
-                           float64 split / temperature recovery / reductions */
+    int precision;      /* DG_FP64; DG_FP32_BULK: float state and flux arithmetic,
+                           float64 split / temperature recovery / reductions;
+                           DG_FP32_PERT: float throughout, the split solved in
+                           the perturbation variables T - T_bar, rho_v - rho_v_bar
+                           against a float64 split of the base state (no
+                           cancellation, so float32 suffices there) */
     double g;           /* gravity in m/s^2 (the paper does not print it; 9.81 usual) */
     double rho_w;       /* water density in the rain speed: <= 0 takes the paper's
                            rho_w = rho_v + rho_c + rho_r; > 0 a constant (kg/m^3) */
@@ -267,7 +272,7 @@ int dg_cloud_functional(dg_ctx *ctx, const void *U, double *J, double *dJdU);
  * and replayed.  Results are bitwise those of dg_step on each member. */
 typedef struct dg_ensemble dg_ensemble;
 
-/* Create n members (cfgs[i].dim == 2, precision DG_FP32_BULK) and build
+/* Create n members (cfgs[i].dim == 2, precision DG_FP32_BULK or DG_FP32_PERT) and build
  * each one's warm bubble (dg_init_bubble with bubbles[i], no noise).  Work
  * goes to cuda_stream, which must not be the legacy default stream (the
  * steps are captured in a graph); NULL creates a private stream.

@@ -201,6 +201,7 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     A.bface = (const Real *)c->bface_r;
     A.bnode_d = c->bnode_d;
     A.rvs_tab = c->rvs_tab;
+    A.bsplit = c->bsplit;
     A.flags = c->flags;
     return A;
 }
@@ -243,7 +244,7 @@ void release(dg_ctx *c) {
     void *ptrs[] = {c->U[0], c->U[1], c->derived, c->trace[0], c->trace[1], c->bnode_d,
                     c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab,
                     c->adjX[0], c->adjX[1], c->adjX[2], c->adjL[0], c->adjL[1], c->adjL[2],
-                    c->ubar_part, c->tadj};
+                    c->ubar_part, c->tadj, c->bsplit};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -279,6 +280,12 @@ int upload_base(dg_ctx *c, const double *node_tab, const double *face_tab) {
         if (e != cudaSuccess) return DG_ECUDA;
     } else {
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    }
+    if (c->bsplit) {
+        // the split of the base state, per node level, for the perturbation-form split
+        k_base_split<<<(nn + 127) / 128, 128, 0, c->stream>>>(c->bnode_d, nn, c->bsplit, c->rvs_tab);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return DG_ECUDA;
     }
     c->base_set = true;
     c->derived_valid = false;
@@ -363,7 +370,8 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     const dg_config &g = *cfg;
     if (g.dim != 2 && g.dim != 3) return DG_EINVAL;
     if (g.order < 1 || g.order > 5) return DG_EINVAL;
-    if (g.precision != DG_FP64 && g.precision != DG_FP32_BULK) return DG_EINVAL;
+    if (g.precision != DG_FP64 && g.precision != DG_FP32_BULK && g.precision != DG_FP32_PERT)
+        return DG_EINVAL;
     if (g.rain != 0 && g.rain != 1) return DG_EINVAL;
     long long ne = 1;
     for (int j = 0; j < g.dim; ++j) {
@@ -384,7 +392,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
         delete c;
         return DG_ECUDA;
     }
-    c->fp32 = (g.precision == DG_FP32_BULK);
+    c->fp32 = (g.precision == DG_FP32_BULK || g.precision == DG_FP32_PERT);
     c->rsz = c->fp32 ? sizeof(float) : sizeof(double);
     if (c->fp32) {
         c->L32 = g.dim == 2 ? launchers_d2_f32(g.order, g.rain) : launchers_d3_f32(g.order, g.rain);
@@ -418,6 +426,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     M.jac = 1.0;
     for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
     M.rain_floor = kRainFloorLin;
+    M.pert_split = (g.precision == DG_FP32_PERT) ? 1 : 0;
     c->ref64 = make_ref<double>(g.order);
     c->ref32 = make_ref<float>(g.order);
 
@@ -452,6 +461,8 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     if (st == DG_OK) st = alloc(c, (void **)&c->flags, sizeof(unsigned long long) * 2);
     if (st == DG_OK) st = alloc(c, (void **)&c->partials, sizeof(double) * kNRed * c->nred);
     if (st == DG_OK) st = alloc(c, (void **)&c->rvs_tab, sizeof(double) * 2 * kTabN);
+    if (st == DG_OK && M.pert_split)
+        st = alloc(c, (void **)&c->bsplit, sizeof(float) * kBsN * M.nzlev_node);
     if (st == DG_OK && cudaMemsetAsync(c->flags, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = DG_ECUDA;
     if (st == DG_OK) {

@@ -31,6 +31,7 @@ struct dg_ctx {
     unsigned long long *flags = nullptr;
     double *partials = nullptr;
     double *rvs_tab = nullptr;
+    float *bsplit = nullptr;     // DG_FP32_PERT: base-state split tables
     // adjoint scratch (allocated on first use): stage states, adjoint vectors,
     // partial node adjoints, neighbour trace adjoints
     const AdjLaunchers *LA = nullptr;

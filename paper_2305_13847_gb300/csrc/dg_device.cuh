@@ -79,6 +79,7 @@ struct MeshData {
     double kvr;            // v0 Gamma(4.5)/6 (pi N0)^(-1/8)
     double jac;            // |K| / 2^d
     double rain_floor;     // linearisation only: rain powers differentiated at max(rho_r, floor)
+    int pert_split;        // float32 state: 1 = split in perturbation variables (DG_FP32_PERT)
 };
 
 template <typename Real>
@@ -103,6 +104,7 @@ struct KArgs {
     const Real *bface;     // base at face levels [4][nzlev_face]
     const double *bnode_d; // float64 copy for the split
     const double *rvs_tab; // rho_vs table: [kTabN][2] = (rho_vs(T_i), 1/T_i)
+    const float *bsplit;   // DG_FP32_PERT: split of the base state per node level [kBsN][nzlev_node]
     Real alpha, beta, gdt; // Uout = alpha Un + beta Uin + gdt dU/dt
     unsigned long long *flags;  // [0] Newton failures, [1] non-physical nodes
 };
@@ -339,6 +341,7 @@ __device__ __forceinline__ float rain_velocity(float rr, float rm, const MeshDat
 struct NodeDerived {
     double T, rv, pp, gm, vr;
     float Tf, rvf, ppf, gmf, vrf;   // float32 copies (FP32-bulk form)
+    float rcf;                      // rho_m - rho_v, perturbation form only
     bool conv, phys;
 };
 
@@ -482,6 +485,141 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
 }
 
 // ---------------------------------------------------------------------------
+// Split in perturbation variables (DG_FP32_PERT)
+// ---------------------------------------------------------------------------
+// With the base state split once in float64 at every node level
+// (T_bar, rho_v_bar), the unknowns are the perturbations tau = T - T_bar and
+// nu = rho_v - rho_v_bar.  Subtracting the base identity
+// E_bar = C_bar (T_bar - T_ref) + rho_v_bar L' from Eq. (2.8a) leaves
+//   H(tau) = C tau + (C - C_bar)(T_bar - T_ref) + nu L' - E' + |m|^2/(2 rho),
+//   C - C_bar = c_vd rho_d' + c_l (rho_m' + rho_r') + (c_vv - c_l) nu,
+// and Eq. (2.6) gives rho_vs(T_bar + tau) = R_bar (1 + expm1(phi(tau))),
+//   phi = (a-1) log1p(tau/T_bar) + (b/T_bar) tau / (T_bar + tau).
+// Every term is a perturbation, so float32 resolves T and rho_v to about
+// 1e-7 of tau and nu (T to ~1e-9 relative) without the cancellation of the
+// direct form; p' = R_d (rho_d' T + rho_d_bar tau) + R_v (nu T + rho_v_bar tau)
+// + (p(base split) - p_bar) likewise.
+// The float32-rounded base split (T_bar, rho_v_bar) is taken as the exact
+// reference; the float64 residuals of its identities are tabulated, so the
+// rounding of the reference enters no result.
+constexpr int kBsN = 10;  // 0 T_bar, 1 rho_v_bar, 2 R_bar = rho_vs(T_bar), 3 rho_m_bar - R_bar,
+                          // 4 R_bar - rho_v_bar, 5 p residual (rho_d R_d + rho_v R_v) T - p, 6 C_bar,
+                          // 7 T_bar - T_ref, 8 energy residual E_bar - C_bar (T_bar - T_ref) - rho_v_bar L',
+                          // 9 rho_m_bar - rho_v_bar
+
+__device__ __forceinline__ float phi_of(float tau, float Tb) {
+    const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
+    return am1 * log1pf(tau / Tb) + (bb / Tb) * (tau / (Tb + tau));
+}
+
+template <bool RAIN>
+__device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im, int ie, int d,
+                                                         float brd, float brm, const float *bs,
+                                                         int nl, const MeshData &M) {
+    NodeDerived o;
+    const float Tb = bs[0], rvb = bs[nl], Rb = bs[2 * nl], Qb = bs[3 * nl], Db = bs[4 * nl];
+    const float pres = bs[5 * nl], Cb = bs[6 * nl], dTb = bs[7 * nl], eres = bs[8 * nl];
+    const float cqb = bs[9 * nl];
+    const float cvd = (float)kCvd, cvv = (float)kCvv, cl = (float)kCl, lp = (float)kLprime;
+    const float rdp = u[0], rmp = u[1], rrp = RAIN ? u[2] : 0.0f;
+    const float rho = brd + brm + rdp + rmp + rrp;
+    float msq = 0.0f;
+    for (int j = 0; j < d; ++j) msq = fmaf(u[im + j], u[im + j], msq);
+    // rho e - (base identity) = E' - |m|^2/(2 rho) + energy residual
+    const float de = (u[ie] - 0.5f * msq / rho) + eres;
+    const float c0 = cvd * rdp + cl * (rmp + rrp);            // C - C_bar without the nu part
+    // unsaturated candidate: rho_v = rho_m, nu_u = rho_m' + (rho_m_bar - rho_v_bar)
+    const float nu_u = rmp + cqb;
+    const float Cu = Cb + c0 + (cvv - cl) * nu_u;
+    const float tau_u = (de - (c0 + (cvv - cl) * nu_u) * dTb - nu_u * lp) / Cu;
+    // saturated iff rho_m > rho_vs(T_u) <=> rho_m' + Q_bar - R_bar expm1(phi(tau_u)) > 0
+    const float em_u = expm1f(phi_of(tau_u, Tb));
+    const bool sat = rmp + Qb - Rb * em_u > 0.0f;
+    float tau, nu, deficit = 0.0f;
+    bool conv = true;
+    if (!sat) {
+        tau = tau_u;
+        nu = nu_u;
+        deficit = (Db + Rb * em_u) - nu_u;                     // rho_vs(T) - rho_v
+    } else {
+        tau = tau_u;
+        conv = false;
+        const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
+        float prev = 3.0e38f;
+        for (int it = 0; it < 40; ++it) {
+            const float T = Tb + tau;
+            const float em = expm1f(phi_of(tau, Tb));
+            const float nus = Db + Rb * em;                     // rho_vs(T) - rho_v_bar
+            const float dnu = Rb * (1.0f + em) * (am1 / T + bb / (T * T));
+            const float C = Cb + c0 + (cvv - cl) * nus;
+            const float h = C * tau + (c0 + (cvv - cl) * nus) * dTb + nus * lp - de;
+            const float dh = C + ((cvv - cl) * (tau + dTb) + lp) * dnu;
+            const float step = h / dh;
+            tau -= step;
+            // done once the step is at rounding level (2 ulp of T, or 2e-6 K),
+            // or once it stops shrinking below 1e-4 K (float32 rounding of h
+            // then decides the last bits and the iteration only dithers)
+            const float as = fabsf(step);
+            if (as <= 2.4e-7f * T + 2e-6f || (as <= 1e-4f && as >= 0.5f * prev)) {
+                conv = true;
+                break;
+            }
+            prev = as;
+        }
+        nu = Db + Rb * expm1f(phi_of(tau, Tb));
+    }
+    const float T = Tb + tau;
+    o.Tf = T;
+    o.rvf = rvb + nu;
+    o.rcf = rmp + cqb - nu;                                    // exactly 0 when unsaturated
+    // p' = (rho_d R_d + rho_v R_v) T - p_bar in perturbation form
+    o.ppf = (float)kRd * (rdp * T + brd * tau) + (float)kRv * (nu * T + rvb * tau) + pres;
+    o.T = (double)Tb + (double)tau;
+    o.rv = (double)rvb + (double)nu;
+    o.pp = (double)o.ppf;
+    o.conv = conv;
+    o.phys = (brd + rdp > 0.0f) && (rho > 0.0f) && (T > 50.0f) && (T < 1000.0f) && isfinite(o.ppf);
+    o.gm = 0.0;
+    o.vr = 0.0;
+    o.gmf = 0.0f;
+    o.vrf = 0.0f;
+    if (RAIN) {
+        const float rr = rrp > 0.0f ? rrp : 0.0f;
+        const float x = rr > 0.0f ? exp2f(0.0625f * __log2f(rr)) : 0.0f;
+        const float x2 = x * x, x3 = x2 * x, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
+        const float rc = o.rcf;
+        const float s_ev = ((float)kSevA - (float)kSevB * (T - (float)kTref)) *
+                           (1.0f + (float)kSevC * x3) * deficit * x8;
+        const float s_au = (float)kSau * (rc > 0.0f ? rc : 0.0f);
+        const float s_ac = (float)kSac * rc * x14;
+        o.gmf = s_ev - s_au - s_ac;
+        o.vrf = rain_velocity(rrp, brm + rmp, M);
+    }
+    return o;
+}
+
+// float64 split of the base state at every node level -> the tables above
+static __global__ void k_base_split(const double *bnode, int nl, float *bs, const double *tab) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    const double rd = bnode[l], rm = bnode[nl + l], E = bnode[2 * nl + l], p = bnode[3 * nl + l];
+    const SplitResult r = split_point<false>(rd, rm, 0.0, E, tab);
+    const double T = (double)(float)r.T, rv = (double)(float)r.rv;   // the float32 reference
+    const double R = rho_vs(T, 1.0 / T);
+    const double C = kCvd * rd + kCvv * rv + kCl * (rm - rv);
+    bs[l] = (float)T;
+    bs[nl + l] = (float)rv;
+    bs[2 * nl + l] = (float)R;
+    bs[3 * nl + l] = (float)(rm - R);
+    bs[4 * nl + l] = (float)(R - rv);
+    bs[5 * nl + l] = (float)((rd * kRd + rv * kRv) * T - p);
+    bs[6 * nl + l] = (float)C;
+    bs[7 * nl + l] = (float)(T - kTref);
+    bs[8 * nl + l] = (float)(E - C * (T - kTref) - rv * kLprime);
+    bs[9 * nl + l] = (float)(rm - rv);
+}
+
+// ---------------------------------------------------------------------------
 // Pointwise flux of Eq. (2.11) and the wave-speed bound of Eq. (3.4)
 // ---------------------------------------------------------------------------
 template <int D, bool RAIN, typename Real>
@@ -599,6 +737,9 @@ __device__ __forceinline__ NodeDerived derive_node(const double *u, const KArgs<
 template <class S>
 __device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<float> &A, int lev) {
     const int nl = A.M.nzlev_node;
+    if (A.M.pert_split)
+        return node_derived_pert<S::RAIN>(u, S::IM, S::IE, S::D, A.bnode[lev], A.bnode[nl + lev],
+                                          A.bsplit + lev, nl, A.M);
     return node_derived_bulk<S::RAIN>(u, S::IM, S::IE, S::D, A.bnode_d[lev], A.bnode_d[nl + lev],
                                       A.bnode_d[2 * nl + lev], A.bnode_d[3 * nl + lev],
                                       A.bnode[lev], A.bnode[nl + lev], A.M, A.rvs_tab);
@@ -606,10 +747,10 @@ __device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<f
 
 template <class S, typename Real>
 __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real *u, int e, int a,
-                                                Real *s_tr, int t) {
+                                                int iz, Real *s_tr, int t) {
     const size_t nodes = (size_t)A.M.ne * S::NP;
     const size_t gi = (size_t)e * S::NP + a;
-    const int lev = vert_index<S::D>(A.M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+    const int lev = iz * S::P1 + digit<S::D, S::P1>(a, S::VERT);
     const NodeDerived nd = derive_node<S>(u, A, lev);
     if (!nd.conv) atomicAdd(&A.flags[0], 1ull);
     if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
@@ -656,7 +797,7 @@ __global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
         Real u[S::NF];
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
-        split_and_store<S, Real>(A, u, e, a, s_tr, t);
+        split_and_store<S, Real>(A, u, e, a, vert_index<S::D>(A.M, e), s_tr, t);
     }
     __syncthreads();
     write_traces<S, Real>(A, A.ref, s_tr, A.trace_out, blockIdx.x);
@@ -671,7 +812,20 @@ constexpr int MODE_STAGE = 1;
 template <class S, typename Real>
 constexpr size_t stage_smem_bytes() {
     return sizeof(Real) * ((size_t)S::NTR * S::EPB * S::NP + (size_t)S::D * S::NF * S::EPB * S::NP +
-                           (size_t)S::EPB * S::NFACE * S::NF * S::NFP1);
+                           (size_t)S::EPB * S::NFACE * S::NF * S::NFP1) +
+           sizeof(int) * 8 * (size_t)S::EPB;   // per element: 2D neighbours, vertical index
+}
+
+// neighbour element across face (j, s) from the element's multi-index, or -1 (wall)
+template <int D>
+__device__ __forceinline__ int neighbour_of(const MeshData &M, const int *im, int j, int s) {
+    int v = im[j] + s;
+    if (v < 0 || v >= M.n[j]) {
+        if (!M.periodic[j]) return -1;
+        v = (v < 0) ? v + M.n[j] : v - M.n[j];
+    }
+    const int i0 = j == 0 ? v : im[0], i1 = j == 1 ? v : im[1], i2 = j == 2 ? v : im[2];
+    return i0 + M.n[0] * (i1 + M.n[1] * (D == 3 ? i2 : 0));
 }
 
 template <class S, typename Real>
@@ -690,7 +844,7 @@ __device__ __forceinline__ void load_base(const Real *tab, int nlev, int lev, Re
 template <class S, typename Real, int J>
 __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<Real> &ref,
                                            const Real *s_tr, Real *s_fh, int el2, int face, int q,
-                                           int e2) {
+                                           int e2, int nb, int iz) {
     constexpr int STR = S::EPB * S::NP;
     const MeshData &M = A.M;
     const int ne = M.ne;
@@ -708,7 +862,6 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
         for (int fld = 0; fld < S::NTR; ++fld)
             tm[fld] = interp_face<S, Real>(s_tr + fld * STR + el2 * S::NP, ls, J, q);
     }
-    const int nb = neighbour<S::D>(M, e2, J, s);
     if (nb >= 0) {
         const int fo = 2 * J + (s > 0 ? 0 : 1);
 #pragma unroll
@@ -720,7 +873,6 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
         tp[S::IM + J] = -tm[S::IM + J];
     }
     Real brd, brm, bE, bp;
-    const int iz = vert_index<S::D>(M, e2);
     if (J == S::VERT) {
         load_base<S, Real>(A.bface, M.nzlev_face, iz + (s > 0 ? 1 : 0), brd, brm, bE, bp);
     } else {
@@ -755,6 +907,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     Real *s_tr = reinterpret_cast<Real *>(smem_raw);          // [NTR][STR]
     Real *s_fl = s_tr + S::NTR * STR;                         // [D][NF][STR]
     Real *s_fh = s_fl + S::D * S::NF * STR;                   // [EPB][NFACE][NF][NFP1]
+    int *s_info = reinterpret_cast<int *>(s_fh + S::EPB * S::NFACE * S::NF * S::NFP1);  // [EPB][8]
     const MeshData &M = A.M;
     const int ne = M.ne;
     const size_t nodes = (size_t)ne * S::NP;
@@ -763,6 +916,22 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     const int e = bidx * S::EPB + el;
     const bool valid = (t < STR) && (e < ne);
 
+    // per element: neighbours across the 2D faces and the vertical index
+    if (t < S::EPB) {
+        const int e0 = bidx * S::EPB + t;
+        if (e0 < ne) {
+            int im[3];
+            elem_multi(M, e0, im[0], im[1], im[2]);
+#pragma unroll
+            for (int j = 0; j < S::D; ++j) {
+                s_info[t * 8 + 2 * j] = neighbour_of<S::D>(M, im, j, -1);
+                s_info[t * 8 + 2 * j + 1] = neighbour_of<S::D>(M, im, j, 1);
+            }
+            s_info[t * 8 + 6] = im[S::VERT];
+        }
+    }
+    __syncthreads();
+
     Real u[S::NF], R[S::NF];
     // ---- phase 1: nodal fluxes, sources, node values for own traces
     if (valid) {
@@ -770,7 +939,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
         const Real T = A.derived[gi], rv = A.derived[nodes + gi], pp = A.derived[2 * nodes + gi];
-        const int lev = vert_index<S::D>(M, e) * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        const int lev = s_info[el * 8 + 6] * S::P1 + digit<S::D, S::P1>(a, S::VERT);
         Real brd, brm, bE, bp;
         load_base<S, Real>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
         Prim<S::D, S::RAIN, Real> P;
@@ -830,10 +999,13 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         const int q = rem - face * S::NFP1;
         const int e2 = bidx * S::EPB + el2;
         if (e2 >= ne) continue;
+        const int nb = s_info[el2 * 8 + face], iz2 = s_info[el2 * 8 + 6];
         switch (face >> 1) {
-            case 0: face_point<S, Real, 0>(A, ref, s_tr, s_fh, el2, face, q, e2); break;
-            case 1: face_point<S, Real, 1>(A, ref, s_tr, s_fh, el2, face, q, e2); break;
-            default: face_point<S, Real, (S::D == 3 ? 2 : 1)>(A, ref, s_tr, s_fh, el2, face, q, e2); break;
+            case 0: face_point<S, Real, 0>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2); break;
+            case 1: face_point<S, Real, 1>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2); break;
+            default:
+                face_point<S, Real, (S::D == 3 ? 2 : 1)>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2);
+                break;
         }
     }
     __syncthreads();
@@ -865,7 +1037,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 un[f] = v;
                 A.Uout[f * nodes + gi] = v;
             }
-            split_and_store<S, Real>(A, un, e, a, s_tr, t);
+            split_and_store<S, Real>(A, un, e, a, s_info[el * 8 + 6], s_tr, t);
         }
     }
     if (MODE == MODE_STAGE) {
@@ -900,7 +1072,9 @@ __global__ void k_split(KArgs<Real> A, double *oT, double *orv, double *orc, dou
         if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
         if (oT) oT[gi] = nd.T;
         if (orv) orv[gi] = nd.rv;
-        if (orc) orc[gi] = rm - nd.rv;
+        // the perturbation form decides saturation in float32: rho_c is 0
+        // exactly where it found the node unsaturated
+        if (orc) orc[gi] = (A.M.pert_split && !(nd.rcf > 0.0f)) ? 0.0 : rm - nd.rv;
         if (opp) opp[gi] = nd.pp;
     }
 }

@@ -183,6 +183,7 @@ int build(dg_ensemble *E) {
         A.bface = (const float *)c->bface_r;
         A.bnode_d = c->bnode_d;
         A.rvs_tab = c->rvs_tab;
+        A.bsplit = c->bsplit;
         A.flags = c->flags;
         m.U[0] = (float *)c->U[0];
         m.U[1] = (float *)c->U[1];
@@ -273,7 +274,8 @@ int dg_ensemble_create(dg_ensemble **out, int n, const dg_config *cfgs, const dg
     if (!out || n < 1 || !cfgs || !bubbles) return DG_EINVAL;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
-        if (cfgs[i].dim != 2 || cfgs[i].precision != DG_FP32_BULK) return DG_EINVAL;
+        if (cfgs[i].dim != 2 || (cfgs[i].precision != DG_FP32_BULK && cfgs[i].precision != DG_FP32_PERT))
+            return DG_EINVAL;
     dg_ensemble *E = new (std::nothrow) dg_ensemble();
     if (!E) return DG_ENOMEM;
     E->n = n;

@@ -24,6 +24,7 @@ DG_ESTATE = -6
 DG_ENOTIMPL = -7
 DG_FP64 = 0
 DG_FP32_BULK = 1
+DG_FP32_PERT = 2
 DG_HOST = 0
 DG_DEVICE = 1
 DG_NREDUCE = 8
