@@ -216,10 +216,13 @@ def _measure(torch, dm, ctx, info, dt, steps, warmup, stream, barrier, dist):
     return float(t.item()) / 1000.0, step_ms
 
 
-def _open(dm, workloads, inputs, name, precision, stream, mesh=None):
+FACES = {"auto": 0, "inline": 1, "pass": 2}
+
+
+def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto"):
     over = {"n": tuple(int(v) for v in mesh.split(","))} if mesh else {}
     w = inputs.workload(name, **over)
-    ctx = workloads.open_workload(w, stream=stream, precision=precision)
+    ctx = workloads.open_workload(w, stream=stream, precision=precision, faces=FACES[faces])
     info = dm.dg_get_info(ctx)
     red = dm.dg_reduce(ctx)
     dt = w["cfl"] * min(L / n for L, n in zip(w["L"], w["n"])) / red[5]
@@ -227,10 +230,14 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None):
 
 
 def _roofline(info, word, t_total, steps, peak, peak_kind):
+    # one SSPRK stage: k_stage, preceded by k_face when the face pass is on
     launch_s = t_total / (STAGES * steps)
     bytes_per_launch = algorithmic_bytes_per_node(info.n_fields, word) * info.n_nodes
     achieved = bytes_per_launch / launch_s / 1e9
-    return {"bound": "hbm", "kernel": "k_stage (fused RHS + SSPRK stage + next split)",
+    kernel = ("k_face + k_stage (face pass, then volume + lift + sources + SSPRK stage + next split)"
+              if info.launches_per_stage == 2 else
+              "k_stage (fused RHS + SSPRK stage + next split)")
+    return {"bound": "hbm", "kernel": kernel,
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
             "algorithmic_bytes_per_launch": bytes_per_launch,
@@ -288,7 +295,8 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
     peak, peak_kind = measured_peaks()
     word = 4 if args.precision.startswith("fp32") else 8
-    w, ctx, info, dt = _open(dm, workloads, inputs, WORKLOAD, args.precision, stream, args.mesh)
+    w, ctx, info, dt = _open(dm, workloads, inputs, args.workload, args.precision, stream, args.mesh,
+                             args.faces)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -320,13 +328,13 @@ def run_gb300(args):
 
     # the FP32-bulk form: its own workload (128x128x64, Q3) and the same mesh
     extra = {}
-    if args.precision == "fp64" and not args.no_fp32:
+    if args.precision == "fp64" and args.workload == WORKLOAD and not args.no_fp32:
         forms = {"fp32_bulk": "float32 state and flux, float64 split",
                  "fp32_pert": "float32 throughout, split in perturbation variables"}
         for key, name, mesh, form in (("fp32_bulk", "rain3d_q3_fp32", None, "fp32_bulk"),
                                       ("fp32_bulk_same_mesh", WORKLOAD, args.mesh, "fp32_bulk"),
                                       ("fp32_pert", "rain3d_q3_fp32", None, "fp32_pert")):
-            w2, ctx2, info2, dt2 = _open(dm, workloads, inputs, name, form, stream, mesh)
+            w2, ctx2, info2, dt2 = _open(dm, workloads, inputs, name, form, stream, mesh, args.faces)
             t2, sm2 = _measure(torch, dm, ctx2, info2, dt2, args.steps, args.warmup, stream, barrier,
                                dist)
             extra[key] = {
@@ -349,10 +357,11 @@ def run_gb300(args):
             "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if word == 4 else "f64", "data": "synthetic",
-            "config": {"workload": "rain3d_q4: 3-D warm-rain bubble, %s hex, Q4 (125 nodes/elem), "
-                                   "7 fields, %d DOFs, dt %.4g s" % ("x".join(map(str, w["n"])),
-                                                                    info.n_dofs, dt),
-                       "precision": args.precision, "l2": "inputs larger than L2 (state %.0f MB)"
+            "config": {"workload": "%s: %d-D warm-rain bubble, %s hex, Q%d (%d nodes/elem), "
+                                   "%d fields, %d DOFs, dt %.4g s"
+                                   % (args.workload, w["dim"], "x".join(map(str, w["n"])), w["order"],
+                                      info.nodes_per_elem, info.n_fields, info.n_dofs, dt),
+                       "precision": args.precision, "faces": args.faces, "l2": "inputs larger than L2 (state %.0f MB)"
                        % (info.state_bytes / 1e6), "parallelism": "replicas" if world > 1 else "1 GPU"},
             "step_ms": {"median": float(np.median(step_ms)), "min": float(np.min(step_ms)),
                         "max": float(np.max(step_ms))},
@@ -360,7 +369,7 @@ def run_gb300(args):
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(info.state_bytes),
                     "d2h_bytes_per_step": int(info.state_bytes), "steps": e2e_steps},
-            "gpu_launches": STAGES * args.steps,
+            "gpu_launches": STAGES * info.launches_per_stage * args.steps,
         }
         line.update(extra)
         if not args.no_cpu_baseline:
@@ -380,6 +389,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurements")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--faces", default="auto", choices=sorted(FACES),
+                    help="face fluxes in the stage kernel (inline), in a face pass, or the "
+                         "library's choice per precision (auto)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="workload to time (default: the 64x64x32 Q4 rain case)")
     ap.add_argument("--mesh", default=None,
                     help="override the element counts, e.g. 40,40,20 (profiling runs only)")
     args = ap.parse_args()

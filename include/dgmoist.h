@@ -93,7 +93,19 @@ typedef struct dg_config {
     double g;           /* gravity in m/s^2 (the paper does not print it; 9.81 usual) */
     double rho_w;       /* water density in the rain speed: <= 0 takes the paper's
                            rho_w = rho_v + rho_c + rho_r; > 0 a constant (kg/m^3) */
+    int faces;          /* where the Lax-Friedrichs face fluxes of a stage are
+                           evaluated: DG_FACES_AUTO (0) the library's choice (the
+                           face pass); DG_FACES_INLINE in the stage kernel, by both
+                           elements of a face; DG_FACES_PASS once per face point in a
+                           separate face kernel (an extra flux buffer of
+                           n_f (k+1)^(d-1) values per face).  The results agree to
+                           rounding; in both the two sides of a face get exactly
+                           opposite fluxes. */
 } dg_config;
+
+#define DG_FACES_AUTO 0
+#define DG_FACES_INLINE 1
+#define DG_FACES_PASS 2
 
 typedef struct dg_info {
     int n_fields;               /* n_f */
@@ -107,6 +119,8 @@ typedef struct dg_info {
     long long n_dofs;           /* n_nodes * n_fields (the paper's DOF count) */
     size_t state_bytes;         /* bytes of one state in ABI layout */
     size_t device_bytes;        /* device memory held by the context */
+    int launches_per_stage;     /* kernels per SSPRK stage: 1 (faces in the stage
+                                   kernel) or 2 (face pass + stage kernel) */
 } dg_info;
 
 /* Warm-bubble workload: hydrostatic column of constant dry potential

@@ -202,6 +202,7 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     A.bnode_d = c->bnode_d;
     A.rvs_tab = c->rvs_tab;
     A.bsplit = c->bsplit;
+    A.fbuf = (Real *)c->fbuf;
     A.flags = c->flags;
     return A;
 }
@@ -231,7 +232,11 @@ int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int 
     A.alpha = (Real)alpha;
     A.beta = (Real)beta;
     A.gdt = (Real)gdt;
-    return cuda_status(L->stage(A, mode, c->stream));
+    if (c->face_pass) {
+        const int st = cuda_status(L->face(A, c->stream));
+        if (st != DG_OK) return st;
+    }
+    return cuda_status(L->stage(A, mode, c->face_pass, c->stream));
 }
 
 int stage(dg_ctx *c, int mode, const void *Uin, const void *Un, void *Uout, int tin, double alpha,
@@ -244,7 +249,7 @@ void release(dg_ctx *c) {
     void *ptrs[] = {c->U[0], c->U[1], c->derived, c->trace[0], c->trace[1], c->bnode_d,
                     c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab,
                     c->adjX[0], c->adjX[1], c->adjX[2], c->adjL[0], c->adjL[1], c->adjL[2],
-                    c->ubar_part, c->tadj, c->bsplit};
+                    c->ubar_part, c->tadj, c->bsplit, c->fbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -373,6 +378,8 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     if (g.precision != DG_FP64 && g.precision != DG_FP32_BULK && g.precision != DG_FP32_PERT)
         return DG_EINVAL;
     if (g.rain != 0 && g.rain != 1) return DG_EINVAL;
+    if (g.faces != DG_FACES_AUTO && g.faces != DG_FACES_INLINE && g.faces != DG_FACES_PASS)
+        return DG_EINVAL;
     long long ne = 1;
     for (int j = 0; j < g.dim; ++j) {
         if (g.n[j] < 1 || !(g.L[j] > 0.0) || !std::isfinite(g.L[j])) return DG_EINVAL;
@@ -427,6 +434,23 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
     M.rain_floor = kRainFloorLin;
     M.pert_split = (g.precision == DG_FP32_PERT) ? 1 : 0;
+    // face grid and the face-pass flux buffer layout
+    // the face pass is the faster schedule for every precision on GB300
+    // (measured: float64 -21 %, float32 forms -8 to -11 % per step)
+    c->face_pass = g.faces != DG_FACES_INLINE;
+    long long fofs = 0;
+    for (int j = 0; j < 3; ++j) {
+        M.nfn[j] = (j < g.dim) ? M.n[j] + (M.periodic[j] ? 0 : 1) : 1;
+        long long nfj = 0;
+        if (j < g.dim) {
+            nfj = 1;
+            for (int i = 0; i < g.dim; ++i) nfj *= (i == j) ? M.nfn[i] : M.n[i];
+        }
+        M.nfaces[j] = (int)nfj;
+        M.fblk[j] = (int)((nfj * c->nfp1 + kFaceThreads - 1) / kFaceThreads);
+        M.fofs[j] = fofs;
+        fofs += nfj * c->nfp1 * nf;
+    }
     c->ref64 = make_ref<double>(g.order);
     c->ref32 = make_ref<float>(g.order);
 
@@ -463,6 +487,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     if (st == DG_OK) st = alloc(c, (void **)&c->rvs_tab, sizeof(double) * 2 * kTabN);
     if (st == DG_OK && M.pert_split)
         st = alloc(c, (void **)&c->bsplit, sizeof(float) * kBsN * M.nzlev_node);
+    if (st == DG_OK && c->face_pass) st = alloc(c, &c->fbuf, (size_t)fofs * c->rsz);
     if (st == DG_OK && cudaMemsetAsync(c->flags, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = DG_ECUDA;
     if (st == DG_OK) {
@@ -512,6 +537,7 @@ int dg_get_info(const dg_ctx *c, dg_info *info) {
     info->n_dofs = c->nodes * c->nf;
     info->state_bytes = (size_t)c->nodes * c->nf * c->rsz;
     info->device_bytes = c->device_bytes;
+    info->launches_per_stage = c->face_pass ? 2 : 1;
     return DG_OK;
 }
 

@@ -32,6 +32,8 @@ struct dg_ctx {
     double *partials = nullptr;
     double *rvs_tab = nullptr;
     float *bsplit = nullptr;     // DG_FP32_PERT: base-state split tables
+    bool face_pass = false;      // faces in k_face (DG_FACES_PASS) instead of in the stage kernel
+    void *fbuf = nullptr;        // face pass: fluxes per face point
     // adjoint scratch (allocated on first use): stage states, adjoint vectors,
     // partial node adjoints, neighbour trace adjoints
     const AdjLaunchers *LA = nullptr;

@@ -80,6 +80,15 @@ struct MeshData {
     double jac;            // |K| / 2^d
     double rain_floor;     // linearisation only: rain powers differentiated at max(rho_r, floor)
     int pert_split;        // float32 state: 1 = split in perturbation variables (DG_FP32_PERT)
+    // faces normal to e_j: a grid of nfn[j] (= n_j, + 1 with walls) x the other n,
+    // nfaces[j] of them; face c lies between the elements at coordinates c - 1
+    // and c along e_j.  The face pass stores its fluxes per direction at
+    // fofs[j]: [NF][nfaces[j]][NFP1]; the face kernel covers direction j with
+    // fblk[j] CTAs.
+    int nfn[3];
+    int nfaces[3];
+    int fblk[3];
+    long long fofs[3];
 };
 
 template <typename Real>
@@ -105,6 +114,7 @@ struct KArgs {
     const double *bnode_d; // float64 copy for the split
     const double *rvs_tab; // rho_vs table: [kTabN][2] = (rho_vs(T_i), 1/T_i)
     const float *bsplit;   // DG_FP32_PERT: split of the base state per node level [kBsN][nzlev_node]
+    Real *fbuf;            // face pass: Lax-Friedrichs flux along +e_j per face point (MeshData.fofs)
     Real alpha, beta, gdt; // Uout = alpha Un + beta Uin + gdt dU/dt
     unsigned long long *flags;  // [0] Newton failures, [1] non-physical nodes
 };
@@ -809,11 +819,23 @@ __global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
 constexpr int MODE_RHS = 0;
 constexpr int MODE_STAGE = 1;
 
-template <class S, typename Real>
+// Shared memory of a stage tile: nodal fluxes s_fl [D][NF][EPB NP], node
+// values for the traces s_tr [NTR][EPB NP], face fluxes s_fh
+// [EPB][2D][NF][NFP1] and per-element indices.  s_tr is needed during the
+// face phase only when the float32 inline form interpolates its own traces
+// there; otherwise it is filled after the volume phase and shares s_fl.
+template <class S, typename Real, bool PF>
+__host__ __device__ constexpr bool tr_shares_fl() {
+    return PF || sizeof(Real) == sizeof(double);
+}
+
+template <class S, typename Real, bool PF = false>
 constexpr size_t stage_smem_bytes() {
-    return sizeof(Real) * ((size_t)S::NTR * S::EPB * S::NP + (size_t)S::D * S::NF * S::EPB * S::NP +
+    constexpr size_t str = (size_t)S::EPB * S::NP;
+    constexpr size_t fl = (size_t)S::D * S::NF * str, tr = (size_t)S::NTR * str;
+    return sizeof(Real) * ((tr_shares_fl<S, Real, PF>() ? (fl > tr ? fl : tr) : fl + tr) +
                            (size_t)S::EPB * S::NFACE * S::NF * S::NFP1) +
-           sizeof(int) * 8 * (size_t)S::EPB;   // per element: 2D neighbours, vertical index
+           sizeof(int) * 16 * (size_t)S::EPB;  // per element: 2D neighbours, vertical index, 2D faces
 }
 
 // neighbour element across face (j, s) from the element's multi-index, or -1 (wall)
@@ -826,6 +848,23 @@ __device__ __forceinline__ int neighbour_of(const MeshData &M, const int *im, in
     }
     const int i0 = j == 0 ? v : im[0], i1 = j == 1 ? v : im[1], i2 = j == 2 ? v : im[2];
     return i0 + M.n[0] * (i1 + M.n[1] * (D == 3 ? i2 : 0));
+}
+
+// index of face c (0 <= c < nfn[j]) normal to e_j through the element row of im
+template <int D>
+__device__ __forceinline__ int face_index(const MeshData &M, const int *im, int j, int c) {
+    const int i0 = j == 0 ? c : im[0], i1 = j == 1 ? c : im[1], i2 = j == 2 ? c : im[2];
+    const int n0 = j == 0 ? M.nfn[0] : M.n[0], n1 = j == 1 ? M.nfn[1] : M.n[1];
+    return i0 + n0 * (i1 + n1 * (D == 3 ? i2 : 0));
+}
+
+// face of element im on side s of direction j (the high face of the last
+// element of a periodic row is face 0)
+template <int D>
+__device__ __forceinline__ int element_face(const MeshData &M, const int *im, int j, int s) {
+    int c = im[j] + (s > 0 ? 1 : 0);
+    if (c >= M.nfn[j]) c -= M.n[j];
+    return face_index<D>(M, im, j, c);
 }
 
 template <class S, typename Real>
@@ -898,16 +937,119 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
         out[f * S::NFP1] = hs * (Fm[f] + Fp[f]) + Real(0.5) * lam * (tm[f] - tp[f]);
 }
 
+// ---------------------------------------------------------------------------
+// Face pass: the Lax-Friedrichs flux of Section 3.2 once per face point
+// ---------------------------------------------------------------------------
+// G = {{F_j}} + Lambda/2 (U_lo - U_hi) along +e_j from the traces of the two
+// elements (lo at coordinate c - 1, hi at c); a slip wall stands in for a
+// missing element with the ghost state m -> m - 2 (m.n) n.  The element on
+// the lo side lifts +G, the one on the hi side -G, so the two contributions
+// cancel exactly in the sums of the conserved quantities.
+template <class S, typename Real, int J>
+__device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
+    const MeshData &M = A.M;
+    const int ne = M.ne;
+    int im[3];
+    {
+        const int n0 = J == 0 ? M.nfn[0] : M.n[0], n1 = J == 1 ? M.nfn[1] : M.n[1];
+        im[0] = f % n0;
+        const int r = f / n0;
+        im[1] = S::D == 3 ? r % n1 : r;
+        im[2] = S::D == 3 ? r / n1 : 0;
+    }
+    const int c = im[J];
+    int lo[3] = {im[0], im[1], im[2]};
+    int e_lo = -1, e_hi = -1;
+    if (c > 0 || M.periodic[J]) {
+        lo[J] = c > 0 ? c - 1 : M.n[J] - 1;
+        e_lo = lo[0] + M.n[0] * (lo[1] + M.n[1] * (S::D == 3 ? lo[2] : 0));
+    }
+    if (c < M.n[J]) e_hi = im[0] + M.n[0] * (im[1] + M.n[1] * (S::D == 3 ? im[2] : 0));
+    Real tl[S::NTR], th[S::NTR];
+    if (e_lo >= 0) {
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld)
+            tl[fld] = A.trace_in[(((size_t)(2 * J + 1) * S::NTR + fld) * ne + e_lo) * S::NFP1 + q];
+    }
+    if (e_hi >= 0) {
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld)
+            th[fld] = A.trace_in[(((size_t)(2 * J) * S::NTR + fld) * ne + e_hi) * S::NFP1 + q];
+    }
+    if (e_lo < 0) {
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) tl[fld] = th[fld];
+        tl[S::IM + J] = -th[S::IM + J];
+    }
+    if (e_hi < 0) {
+#pragma unroll
+        for (int fld = 0; fld < S::NTR; ++fld) th[fld] = tl[fld];
+        th[S::IM + J] = -tl[S::IM + J];
+    }
+    Real brd, brm, bE, bp;
+    if (J == S::VERT) {
+        load_base<S, Real>(A.bface, M.nzlev_face, c, brd, brm, bE, bp);
+    } else {
+        load_base<S, Real>(A.bnode, M.nzlev_node, im[S::VERT] * S::P1 + face_q_vert<S::D, S::P1>(J, q),
+                           brd, brm, bE, bp);
+    }
+    Prim<S::D, S::RAIN, Real> Pl, Ph;
+    make_prim<S, Real>(Pl, tl, brd, brm, bE, bp, tl[S::NF], tl[S::NF + 1], tl[S::NF + 2]);
+    make_prim<S, Real>(Ph, th, brd, brm, bE, bp, th[S::NF], th[S::NF + 1], th[S::NF + 2]);
+    if (S::RAIN) {
+        Pl.vr = rain_velocity(Pl.rr, Pl.rm, M);
+        Ph.vr = rain_velocity(Ph.rr, Ph.rm, M);
+    }
+    Real Fl[S::NF], Fh[S::NF];
+    flux_dir<S, Real>(Pl, J, Fl);
+    flux_dir<S, Real>(Ph, J, Fh);
+    const Real ll = wave_speed<S, J, Real>(Pl), lh = wave_speed<S, J, Real>(Ph);
+    const Real lam = ll > lh ? ll : lh;
+    Real *out = A.fbuf + M.fofs[J] + (size_t)f * S::NFP1 + q;
+    const size_t fs = (size_t)M.nfaces[J] * S::NFP1;
+#pragma unroll
+    for (int fld = 0; fld < S::NF; ++fld)
+        out[fld * fs] = Real(0.5) * (Fl[fld] + Fh[fld]) + Real(0.5) * lam * (tl[fld] - th[fld]);
+}
+
+constexpr int kFaceThreads = 128;
+
+template <class S, typename Real>
+__global__ void __launch_bounds__(kFaceThreads) k_face(KArgs<Real> A) {
+    int b = blockIdx.x, J = 0;
+    if (b >= A.M.fblk[0]) {
+        b -= A.M.fblk[0];
+        J = 1;
+        if (S::D == 3 && b >= A.M.fblk[1]) {
+            b -= A.M.fblk[1];
+            J = 2;
+        }
+    }
+    const long long gid = (long long)b * kFaceThreads + threadIdx.x;
+    const int f = (int)(gid / S::NFP1), q = (int)(gid - (long long)f * S::NFP1);
+    if (f >= A.M.nfaces[J]) return;
+    switch (J) {
+        case 0: face_flux<S, Real, 0>(A, f, q); break;
+        case 1: face_flux<S, Real, 1>(A, f, q); break;
+        default: face_flux<S, Real, (S::D == 3 ? 2 : 1)>(A, f, q); break;
+    }
+}
+
 // One tile of EPB consecutive elements (tile index bidx) of the stage
 // kernel; every thread of the CTA takes part (the body has barriers).
-template <class S, typename Real, int MODE>
+// PF: the face fluxes come from the face pass (k_face) instead of being
+// evaluated here on both sides of every face.
+template <class S, typename Real, int MODE, bool PF = false>
 __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<Real> &ref, int bidx,
                                             unsigned char *smem_raw) {
     constexpr int STR = S::EPB * S::NP;
-    Real *s_tr = reinterpret_cast<Real *>(smem_raw);          // [NTR][STR]
-    Real *s_fl = s_tr + S::NTR * STR;                         // [D][NF][STR]
-    Real *s_fh = s_fl + S::D * S::NF * STR;                   // [EPB][NFACE][NF][NFP1]
-    int *s_info = reinterpret_cast<int *>(s_fh + S::EPB * S::NFACE * S::NF * S::NFP1);  // [EPB][8]
+    constexpr bool SHARE = tr_shares_fl<S, Real, PF>();
+    constexpr int FLTR = SHARE ? (S::D * S::NF > S::NTR ? S::D * S::NF : S::NTR) * STR
+                               : (S::D * S::NF + S::NTR) * STR;
+    Real *s_fl = reinterpret_cast<Real *>(smem_raw);          // [D][NF][STR]
+    Real *s_tr = SHARE ? s_fl : s_fl + S::D * S::NF * STR;    // [NTR][STR]
+    Real *s_fh = s_fl + FLTR;                                 // [EPB][NFACE][NF][NFP1]
+    int *s_info = reinterpret_cast<int *>(s_fh + S::EPB * S::NFACE * S::NF * S::NFP1);  // [EPB][16]
     const MeshData &M = A.M;
     const int ne = M.ne;
     const size_t nodes = (size_t)ne * S::NP;
@@ -916,7 +1058,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     const int e = bidx * S::EPB + el;
     const bool valid = (t < STR) && (e < ne);
 
-    // per element: neighbours across the 2D faces and the vertical index
+    // per element: neighbours across the 2D faces (or, with the face pass,
+    // the faces themselves) and the vertical index
     if (t < S::EPB) {
         const int e0 = bidx * S::EPB + t;
         if (e0 < ne) {
@@ -924,10 +1067,15 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             elem_multi(M, e0, im[0], im[1], im[2]);
 #pragma unroll
             for (int j = 0; j < S::D; ++j) {
-                s_info[t * 8 + 2 * j] = neighbour_of<S::D>(M, im, j, -1);
-                s_info[t * 8 + 2 * j + 1] = neighbour_of<S::D>(M, im, j, 1);
+                if (PF) {
+                    s_info[t * 16 + 8 + 2 * j] = element_face<S::D>(M, im, j, -1);
+                    s_info[t * 16 + 8 + 2 * j + 1] = element_face<S::D>(M, im, j, 1);
+                } else {
+                    s_info[t * 16 + 2 * j] = neighbour_of<S::D>(M, im, j, -1);
+                    s_info[t * 16 + 2 * j + 1] = neighbour_of<S::D>(M, im, j, 1);
+                }
             }
-            s_info[t * 8 + 6] = im[S::VERT];
+            s_info[t * 16 + 6] = im[S::VERT];
         }
     }
     __syncthreads();
@@ -939,7 +1087,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
         const Real T = A.derived[gi], rv = A.derived[nodes + gi], pp = A.derived[2 * nodes + gi];
-        const int lev = s_info[el * 8 + 6] * S::P1 + digit<S::D, S::P1>(a, S::VERT);
+        const int lev = s_info[el * 16 + 6] * S::P1 + digit<S::D, S::P1>(a, S::VERT);
         Real brd, brm, bE, bp;
         load_base<S, Real>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
         Prim<S::D, S::RAIN, Real> P;
@@ -953,13 +1101,16 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             for (int f = 0; f < S::NF; ++f) s_fl[(j * S::NF + f) * STR + t] = F[f];
         }
 #pragma unroll
-        for (int f = 0; f < S::NF; ++f) {
-            s_tr[f * STR + t] = u[f];
-            R[f] = Real(0);
+        for (int f = 0; f < S::NF; ++f) R[f] = Real(0);
+        // node values for the own traces (the float64 form reads them back
+        // from the trace buffer)
+        if (!PF && sizeof(Real) == sizeof(float)) {
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) s_tr[f * STR + t] = u[f];
+            s_tr[S::NF * STR + t] = T;
+            s_tr[(S::NF + 1) * STR + t] = rv;
+            s_tr[(S::NF + 2) * STR + t] = pp;
         }
-        s_tr[S::NF * STR + t] = T;
-        s_tr[(S::NF + 1) * STR + t] = rv;
-        s_tr[(S::NF + 2) * STR + t] = pp;
         // sources G (Eq. (2.11)): microphysics and gravity
         if (S::RAIN) {
             const Real gm = A.derived[3 * nodes + gi];
@@ -992,20 +1143,39 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     }
 
     // ---- phase 2b: Lax-Friedrichs flux at every face point of the CTA's elements
-    for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
-        const int el2 = item / (S::NFACE * S::NFP1);
-        const int rem = item - el2 * (S::NFACE * S::NFP1);
-        const int face = rem / S::NFP1;
-        const int q = rem - face * S::NFP1;
-        const int e2 = bidx * S::EPB + el2;
-        if (e2 >= ne) continue;
-        const int nb = s_info[el2 * 8 + face], iz2 = s_info[el2 * 8 + 6];
-        switch (face >> 1) {
-            case 0: face_point<S, Real, 0>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2); break;
-            case 1: face_point<S, Real, 1>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2); break;
-            default:
-                face_point<S, Real, (S::D == 3 ? 2 : 1)>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2);
-                break;
+    if (PF) {
+        // outward fluxes from the face pass: +G on the high face, -G on the low
+        // face; s_fh[el][face][f][q] in the order of the item index
+        for (int item = t; item < S::EPB * S::NFACE * S::NF * S::NFP1; item += S::NT) {
+            const int el2 = item / (S::NFACE * S::NF * S::NFP1);
+            const int rem = item - el2 * (S::NFACE * S::NF * S::NFP1);
+            const int face = rem / (S::NF * S::NFP1);
+            const int r2 = rem - face * (S::NF * S::NFP1);
+            const int fld = r2 / S::NFP1;
+            const int q = r2 - fld * S::NFP1;
+            if (bidx * S::EPB + el2 >= ne) continue;
+            const int j = face >> 1;
+            const Real g = A.fbuf[M.fofs[j] +
+                                  ((size_t)fld * M.nfaces[j] + s_info[el2 * 16 + 8 + face]) * S::NFP1 + q];
+            s_fh[item] = (face & 1) ? g : -g;
+        }
+    } else {
+        for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
+            const int el2 = item / (S::NFACE * S::NFP1);
+            const int rem = item - el2 * (S::NFACE * S::NFP1);
+            const int face = rem / S::NFP1;
+            const int q = rem - face * S::NFP1;
+            const int e2 = bidx * S::EPB + el2;
+            if (e2 >= ne) continue;
+            const int nb = s_info[el2 * 16 + face], iz2 = s_info[el2 * 16 + 6];
+            switch (face >> 1) {
+                case 0: face_point<S, Real, 0>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2); break;
+                case 1: face_point<S, Real, 1>(A, ref, s_tr, s_fh, el2, face, q, e2, nb, iz2); break;
+                default:
+                    face_point<S, Real, (S::D == 3 ? 2 : 1)>(A, ref, s_tr, s_fh, el2, face, q, e2, nb,
+                                                             iz2);
+                    break;
+            }
         }
     }
     __syncthreads();
@@ -1037,7 +1207,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 un[f] = v;
                 A.Uout[f * nodes + gi] = v;
             }
-            split_and_store<S, Real>(A, un, e, a, s_info[el * 8 + 6], s_tr, t);
+            split_and_store<S, Real>(A, un, e, a, s_info[el * 16 + 6], s_tr, t);
         }
     }
     if (MODE == MODE_STAGE) {
@@ -1046,10 +1216,10 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     }
 }
 
-template <class S, typename Real, int MODE>
+template <class S, typename Real, int MODE, bool PF>
 __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_block<S, Real, MODE>(A, A.ref, blockIdx.x, smem_raw);
+    stage_block<S, Real, MODE, PF>(A, A.ref, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

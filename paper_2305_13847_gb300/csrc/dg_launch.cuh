@@ -12,7 +12,9 @@ struct Launchers {
     int nf, np, nfp1, nd, ntr, epb, nt;
     size_t prep_smem, stage_smem;
     cudaError_t (*prepare)(const KArgs<Real> &, cudaStream_t);
-    cudaError_t (*stage)(const KArgs<Real> &, int mode, cudaStream_t);
+    // pf: the stage kernel takes its face fluxes from the face pass
+    cudaError_t (*stage)(const KArgs<Real> &, int mode, bool pf, cudaStream_t);
+    cudaError_t (*face)(const KArgs<Real> &, cudaStream_t);
     cudaError_t (*split)(const KArgs<Real> &, double *, double *, double *, double *, cudaStream_t);
     cudaError_t (*init_bubble)(const KArgs<Real> &, const BubbleArgs &, cudaStream_t);
     cudaError_t (*reduce)(const KArgs<Real> &, double *partials, int nblocks, cudaStream_t);
@@ -29,7 +31,8 @@ inline int grid_for(size_t n, int threads) {
 template <class S, typename Real>
 struct Impl {
     static constexpr size_t prep_smem = sizeof(Real) * (size_t)S::NTR * S::EPB * S::NP;
-    static constexpr size_t stage_smem = stage_smem_bytes<S, Real>();
+    static constexpr size_t stage_smem = stage_smem_bytes<S, Real, false>();
+    static constexpr size_t stage_smem_pf = stage_smem_bytes<S, Real, true>();
 
     static int blocks(const KArgs<Real> &A) { return (A.M.ne + S::EPB - 1) / S::EPB; }
 
@@ -46,26 +49,29 @@ struct Impl {
         return cudaGetLastError();
     }
 
-    static cudaError_t stage(const KArgs<Real> &A, int mode, cudaStream_t st) {
-        static bool attr[2] = {false, false};
-        cudaError_t err = cudaSuccess;
-        if (mode == MODE_RHS) {
-            if (!attr[0]) {
-                err = cudaFuncSetAttribute(k_stage<S, Real, MODE_RHS>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem);
-                if (err != cudaSuccess) return err;
-                attr[0] = true;
-            }
-            k_stage<S, Real, MODE_RHS><<<blocks(A), S::NT, stage_smem, st>>>(A);
-        } else {
-            if (!attr[1]) {
-                err = cudaFuncSetAttribute(k_stage<S, Real, MODE_STAGE>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_smem);
-                if (err != cudaSuccess) return err;
-                attr[1] = true;
-            }
-            k_stage<S, Real, MODE_STAGE><<<blocks(A), S::NT, stage_smem, st>>>(A);
+    template <int MODE, bool PF>
+    static cudaError_t launch_stage(const KArgs<Real> &A, cudaStream_t st) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t err = cudaFuncSetAttribute(k_stage<S, Real, MODE, PF>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(PF ? stage_smem_pf : stage_smem));
+            if (err != cudaSuccess) return err;
+            attr = true;
         }
+        k_stage<S, Real, MODE, PF><<<blocks(A), S::NT, PF ? stage_smem_pf : stage_smem, st>>>(A);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t stage(const KArgs<Real> &A, int mode, bool pf, cudaStream_t st) {
+        if (mode == MODE_RHS)
+            return pf ? launch_stage<MODE_RHS, true>(A, st) : launch_stage<MODE_RHS, false>(A, st);
+        return pf ? launch_stage<MODE_STAGE, true>(A, st) : launch_stage<MODE_STAGE, false>(A, st);
+    }
+
+    static cudaError_t face(const KArgs<Real> &A, cudaStream_t st) {
+        const int nb = A.M.fblk[0] + A.M.fblk[1] + A.M.fblk[2];
+        k_face<S, Real><<<nb, kFaceThreads, 0, st>>>(A);
         return cudaGetLastError();
     }
 
@@ -100,6 +106,7 @@ struct Impl {
         L.stage_smem = stage_smem;
         L.prepare = &prepare;
         L.stage = &stage;
+        L.face = &face;
         L.split = &split;
         L.init_bubble = &init_bubble;
         L.reduce = &reduce;

@@ -174,6 +174,6 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     A.alpha = 0.0;
     A.beta = 1.0;
     A.gdt = 1.0;
-    if (L->stage(A, MODE_RHS, stream) != cudaSuccess) return DG_ECUDA;
+    if (L->stage(A, MODE_RHS, false, stream) != cudaSuccess) return DG_ECUDA;
     return DG_OK;
 }

@@ -25,6 +25,9 @@ DG_ENOTIMPL = -7
 DG_FP64 = 0
 DG_FP32_BULK = 1
 DG_FP32_PERT = 2
+DG_FACES_AUTO = 0
+DG_FACES_INLINE = 1
+DG_FACES_PASS = 2
 DG_HOST = 0
 DG_DEVICE = 1
 DG_NREDUCE = 8
@@ -40,7 +43,8 @@ class DGError(RuntimeError):
 class dg_config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("order", ctypes.c_int),
                 ("L", ctypes.c_double * 3), ("periodic_mask", ctypes.c_int), ("rain", ctypes.c_int),
-                ("precision", ctypes.c_int), ("g", ctypes.c_double), ("rho_w", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("g", ctypes.c_double), ("rho_w", ctypes.c_double),
+                ("faces", ctypes.c_int)]
 
 
 class dg_info(ctypes.Structure):
@@ -49,7 +53,7 @@ class dg_info(ctypes.Structure):
                 ("n_zlev_face", ctypes.c_int), ("elems_per_block", ctypes.c_int),
                 ("n_elem", ctypes.c_longlong), ("n_nodes", ctypes.c_longlong),
                 ("n_dofs", ctypes.c_longlong), ("state_bytes", ctypes.c_size_t),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("launches_per_stage", ctypes.c_int)]
 
 
 class dg_bubble(ctypes.Structure):
@@ -141,7 +145,8 @@ def _stream_handle(stream):
     return stream.cuda_stream  # torch.cuda.Stream
 
 
-def make_config(dim, n, L, order, periodic_mask, rain, precision=DG_FP64, g=9.81, rho_w=0.0):
+def make_config(dim, n, L, order, periodic_mask, rain, precision=DG_FP64, g=9.81, rho_w=0.0,
+                faces=0):
     c = dg_config()
     c.dim = dim
     for j in range(3):
@@ -153,6 +158,7 @@ def make_config(dim, n, L, order, periodic_mask, rain, precision=DG_FP64, g=9.81
     c.precision = precision
     c.g = g
     c.rho_w = rho_w
+    c.faces = faces
     return c
 
 

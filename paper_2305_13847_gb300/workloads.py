@@ -11,13 +11,14 @@ def precision_code(name):
     return {"fp64": dm.DG_FP64, "fp32_bulk": dm.DG_FP32_BULK, "fp32_pert": dm.DG_FP32_PERT}[name]
 
 
-def config_for(w, precision=None, g=9.81, rho_w=0.0):
+def config_for(w, precision=None, g=9.81, rho_w=0.0, faces=0):
     mask = 0
     for j, p in enumerate(w["periodic"]):
         if p:
             mask |= 1 << j
     prec = precision_code(precision or w["precision"])
-    return dm.make_config(w["dim"], w["n"], w["L"], w["order"], mask, w["rain"], prec, g, rho_w)
+    return dm.make_config(w["dim"], w["n"], w["L"], w["order"], mask, w["rain"], prec, g, rho_w,
+                          faces)
 
 
 def bubble_for(w):
@@ -33,9 +34,11 @@ def bubble_for(w):
     return b
 
 
-def open_workload(w, stream=None, precision=None, with_noise=True):
-    """dg_init_mesh + dg_init_bubble for workload ``w``; returns the context."""
-    ctx = dm.dg_init_mesh(config_for(w, precision), stream)
+def open_workload(w, stream=None, precision=None, with_noise=True, faces=0):
+    """dg_init_mesh + dg_init_bubble for workload ``w``; returns the context.
+
+    faces: dm.DG_FACES_AUTO / _INLINE / _PASS (where the face fluxes are evaluated)."""
+    ctx = dm.dg_init_mesh(config_for(w, precision, faces=faces), stream)
     try:
         info = dm.dg_get_info(ctx)
         noise = inputs.node_noise(w, info.n_elem, info.nodes_per_elem) if with_noise else None

@@ -19,11 +19,11 @@ def oracle_problem(dim, n, L, order, periodic, rain, qt0=0.015, g=9.81):
     return dg.Problem(mesh, node, face, rain=rain, g=g), extra
 
 
-def library_context(prob, precision=dm.DG_FP64, stream=None):
+def library_context(prob, precision=dm.DG_FP64, stream=None, faces=dm.DG_FACES_AUTO):
     mesh = prob.mesh
     mask = sum(1 << j for j, p in enumerate(mesh.periodic[:-1]) if p)
     cfg = dm.make_config(mesh.dim, mesh.n, mesh.L, mesh.k, mask, prob.rain, precision, prob.g,
-                         prob.rho_w or 0.0)
+                         prob.rho_w or 0.0, faces)
     ctx = dm.dg_init_mesh(cfg, stream)
     node = np.stack([prob.base_node[k] for k in BASE_KEYS])
     face = np.stack([prob.base_face[k] for k in BASE_KEYS])

@@ -51,11 +51,12 @@ def _setup(name, seed=5):
 FORMS = [dm.DG_FP32_BULK, dm.DG_FP32_PERT]
 
 
+@pytest.mark.parametrize("faces", [dm.DG_FACES_INLINE, dm.DG_FACES_PASS])
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_fp32_rhs_close_to_oracle(name, form):
+def test_fp32_rhs_close_to_oracle(name, form, faces):
     prob, U = _setup(name)
-    ctx = library_context(prob, precision=form)
+    ctx = library_context(prob, precision=form, faces=faces)
     try:
         Ud = to_device(U, torch.float32)
         out = torch.empty_like(Ud)
@@ -92,9 +93,9 @@ def test_fp32_split_float64_accuracy(name, form):
         dm.dg_free(ctx)
 
 
-def _compare_steps(prob, U0, dt, steps, tol, form):
+def _compare_steps(prob, U0, dt, steps, tol, form, faces=dm.DG_FACES_AUTO):
     Uo = dg.run(prob, U0, dt, steps)
-    ctx = library_context(prob, precision=form)
+    ctx = library_context(prob, precision=form, faces=faces)
     try:
         dm.dg_set_state(ctx, np.ascontiguousarray(U0.astype(np.float32)), dm.DG_HOST)
         dm.dg_step(ctx, dt, steps)
@@ -119,8 +120,9 @@ def test_fp32_bubble2d_100_steps_within_1e5(form):
     _compare_steps(prob, U0, dt, 100, 1e-5, form)
 
 
+@pytest.mark.parametrize("faces", [dm.DG_FACES_INLINE, dm.DG_FACES_PASS])
 @pytest.mark.parametrize("form", FORMS)
-def test_fp32_rain3d_20_steps_within_1e5(form):
+def test_fp32_rain3d_20_steps_within_1e5(form, faces):
     prob, U0 = _setup("rain3d_q3")
     dt = dg.cfl_dt(prob, U0, 0.05)
-    _compare_steps(prob, U0, dt, 20, 1e-5, form)
+    _compare_steps(prob, U0, dt, 20, 1e-5, form, faces)

@@ -125,10 +125,16 @@ def test_saturation_split_random_states():
         dm.dg_free(ctx)
 
 
+# where the face fluxes are evaluated: in the stage kernel by both elements,
+# or once per face point in the face pass
+FACES = [dm.DG_FACES_INLINE, dm.DG_FACES_PASS]
+
+
+@pytest.mark.parametrize("faces", FACES)
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_rhs_parity(name):
+def test_rhs_parity(name, faces):
     prob, U = _setup(name)
-    ctx = library_context(prob)
+    ctx = library_context(prob, faces=faces)
     try:
         Ud = to_device(U, torch.float64)
         out = torch.empty_like(Ud)
@@ -146,13 +152,14 @@ def test_rhs_parity(name):
         dm.dg_free(ctx)
 
 
-def test_step_parity_bubble2d_100_steps():
+@pytest.mark.parametrize("faces", FACES)
+def test_step_parity_bubble2d_100_steps(faces):
     w = inputs.workload("bubble2d_q3")
     prob, extra = oracle_problem(w["dim"], w["n"], w["L"], w["order"], w["periodic"], w["rain"])
     U0 = initial.bubble_state(prob, w["A"], w["centre"], w["radius"], H=w["H"])
     dt = dg.cfl_dt(prob, U0, w["cfl"])
     Uo = dg.run(prob, U0, dt, w["steps"])
-    ctx = library_context(prob)
+    ctx = library_context(prob, faces=faces)
     try:
         dm.dg_set_state(ctx, np.ascontiguousarray(U0), dm.DG_HOST)
         dm.dg_step(ctx, dt, w["steps"])
@@ -165,11 +172,12 @@ def test_step_parity_bubble2d_100_steps():
         dm.dg_free(ctx)
 
 
-def test_step_parity_rain3d_small():
+@pytest.mark.parametrize("faces", FACES)
+def test_step_parity_rain3d_small(faces):
     prob, U0 = _setup("rain3d_q4_ragged")
     dt = dg.cfl_dt(prob, U0, 0.05)
     Uo = dg.run(prob, U0, dt, 5)
-    ctx = library_context(prob)
+    ctx = library_context(prob, faces=faces)
     try:
         dm.dg_set_state(ctx, np.ascontiguousarray(U0), dm.DG_HOST)
         dm.dg_step(ctx, dt, 5)
@@ -223,9 +231,10 @@ def test_reduce_matches_oracle_integrals():
         dm.dg_free(ctx)
 
 
-def test_dry_mass_conserved_over_steps():
+@pytest.mark.parametrize("faces", FACES)
+def test_dry_mass_conserved_over_steps(faces):
     prob, U = _setup("rain3d_q4_ragged")
-    ctx = library_context(prob)
+    ctx = library_context(prob, faces=faces)
     try:
         dm.dg_set_state(ctx, np.ascontiguousarray(U), dm.DG_HOST)
         m0 = dm.dg_reduce(ctx)

@@ -58,13 +58,14 @@ def test_strerror(lib):
     dict(dim=4), dict(dim=1), dict(order=0), dict(order=6), dict(n=(0, 4, 4)),
     dict(n=(4, -1, 4)), dict(L=(1e3, 0.0, 1e3)), dict(rain=2), dict(precision=7),
     dict(n=(4096, 4096, 64), order=5),      # n_nodes * n_fields beyond 2^31 - 1
+    dict(faces=3), dict(faces=-1),
 ])
 def test_init_mesh_rejects_bad_configs(lib, kw):
     base = dict(dim=3, n=(4, 4, 4), L=(1e3, 1e3, 1e3), order=3, periodic_mask=3, rain=1,
                 precision=lib.DG_FP64)
     base.update(kw)
     cfg = lib.make_config(base["dim"], base["n"], base["L"], base["order"], base["periodic_mask"],
-                          base["rain"], base["precision"])
+                          base["rain"], base["precision"], faces=base.get("faces", 0))
     assert lib.dg_init_mesh_status(cfg) == lib.DG_EINVAL
 
 
