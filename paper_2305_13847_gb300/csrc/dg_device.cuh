@@ -251,12 +251,18 @@ struct SplitResult {
 // Unsaturated candidate T_u in closed form; if rho_m > rho_vs(T_u) the vapour
 // is saturated and T solves
 //   H(T) = (c_vd rd + c_vv rvs + c_l (rm - rvs + rr)) (T - T_ref) + rvs L' - re = 0,
-// H increasing and convex.  Newton's method runs first in float32 from T_u
-// (to ~1e-7), then two float64 Newton steps reach float64 rounding; if the
-// last float64 step is not below 1e-10 T the float64 iteration continues
-// (bracketed, cap kMaxNewton).  The saturation test is decided in float32
-// unless rho_m is within 1e-5 of rho_vs; the float64 value is always formed
-// when the caller needs the evaporation deficit.
+// H increasing and convex.  The saturation test is decided in float32 unless
+// rho_m is within 1e-5 of rho_vs (then in float64); the float64 rho_vs(T_u)
+// is formed only where the caller needs the evaporation deficit of an
+// unsaturated node.  Saturated: Newton's method in float32 from T_u (to
+// ~1e-7), then one third-order (Chebyshev) step in float64,
+//   d = -H/H',  T = T0 + d - (H''/(2 H')) d^2,
+// with H and H' in float64 and the H'' term in float32: from |d| <= 3e-4 K
+// (the pre-solve lands within ~5e-5 K) the step leaves an error of order
+// (H''/H')^2 d^3 < 2e-13 K, so one float64
+// evaluation of rho_vs gives T and rho_v = rho_vs(T) (second-order Taylor
+// from T0) to float64 rounding.  A larger |d| falls back to the bracketed
+// float64 Newton iteration (cap kMaxNewton).
 template <bool NEED_DEFICIT>
 __device__ __forceinline__ SplitResult split_point(double rd, double rm, double rr, double re,
                                                    const double *__restrict__ tab) {
@@ -266,7 +272,8 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     const float rvs32 = rho_vs_f32((float)tu);
     bool sat;
     double rvs_u = 0.0, invt;
-    if (NEED_DEFICIT || fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tu > 0.0)) {
+    const bool close = fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tu > 0.0);
+    if (close || (NEED_DEFICIT && !(rm > (double)rvs32))) {
         rvs_u = rho_vs_tab(tu, tab, invt);
         sat = rm > rvs_u;
     } else {
@@ -280,12 +287,12 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
         return r;
     }
     const double cdry = kCvd * rd + kCl * (rm + rr);
+    const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
+    const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
     // float32 pre-solve
+    float t = (float)tu;
     {
         const float cdf = (float)cdry, ref = (float)re, tref = (float)kTref;
-        const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
-        const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
-        float t = (float)tu;
         for (int it = 0; it < 30; ++it) {
             const float rvs = rho_vs_f32(t);
             const float it_ = __frcp_rn(t);
@@ -297,34 +304,59 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
             t -= dt;
             if (fabsf(dt) <= 2e-6f * t) break;
         }
-        r.T = (double)t;
     }
-    // float64 Newton steps
-    double t = (r.T > tu) ? r.T : tu;
+    r.deficit = 0.0;
+    // one float64 third-order step from T0
+    {
+        const double t0 = ((double)t > tu) ? (double)t : tu;
+        const double rvs = rho_vs_tab(t0, tab, invt);
+        const double phi1 = invt * fma(kEsB, invt, kEsA - 1.0);     // (ln rho_vs)'
+        const double drvs = rvs * phi1;
+        const double heat = fma(kCvv - kCl, rvs, cdry);
+        const double lat = fma(kCvv - kCl, t0 - kTref, kLprime);
+        const double h = fma(heat, t0 - kTref, fma(rvs, kLprime, -re));
+        const double dh = fma(lat, drvs, heat);
+        const double d = -h * recip(dh);
+        if (fabs(d) <= 3e-4) {
+            // H'' = 2 (c_vv - c_l) rho_vs' + (c_vv - c_l)(T - T_ref) + L') rho_vs'',
+            // rho_vs'' = rho_vs (phi1^2 + phi1'), phi1' = -(a-1)/T^2 - 2b/T^3
+            const float itf = (float)invt, p1f = (float)phi1, rvf = (float)rvs;
+            const float d2rvs = rvf * (p1f * p1f - itf * itf * (am1 + 2.0f * bb * itf));
+            const float d2h = 2.0f * clv * (rvf * p1f) + (float)lat * d2rvs;
+            const float df = (float)d;
+            const float c2 = -0.5f * d2h / (float)dh * df * df;   // second-order term of the step
+            const double dc = d + (double)c2;
+            r.T = t0 + dc;
+            r.rv = fma(drvs, dc, rvs) + (double)(0.5f * d2rvs * (float)dc * (float)dc);
+            r.converged = true;
+            return r;
+        }
+    }
+    // fallback: bracketed float64 Newton iteration
+    double tn0 = ((double)t > tu) ? (double)t : tu;
     double lo = tu, hi = INFINITY, rvs = 0.0, drvs = 0.0, step = INFINITY;
     bool done = false;
     for (int it = 0; it < kMaxNewton; ++it) {
-        rvs = rho_vs_tab(t, tab, invt);
+        rvs = rho_vs_tab(tn0, tab, invt);
         drvs = rvs * invt * fma(kEsB, invt, kEsA - 1.0);
         const double heat = fma(kCvv - kCl, rvs, cdry);
-        const double h = fma(heat, t - kTref, fma(rvs, kLprime, -re));
-        const double dh = fma(fma(kCvv - kCl, t - kTref, kLprime), drvs, heat);
-        if (h < 0.0) lo = t;
-        if (h > 0.0) hi = t;
-        double tn = t - h * recip(dh);
-        if (!(tn >= lo && tn <= hi)) tn = isinf(hi) ? t + 10.0 : 0.5 * (lo + hi);
-        step = tn - t;
-        t = tn;
-        if (it >= 1 && fabs(step) <= 1e-10 * t) {
+        const double h = fma(heat, tn0 - kTref, fma(rvs, kLprime, -re));
+        const double dh = fma(fma(kCvv - kCl, tn0 - kTref, kLprime), drvs, heat);
+        if (h < 0.0) lo = tn0;
+        if (h > 0.0) hi = tn0;
+        double tn = tn0 - h * recip(dh);
+        if (!(tn >= lo && tn <= hi)) tn = isinf(hi) ? tn0 + 10.0 : 0.5 * (lo + hi);
+        step = tn - tn0;
+        tn0 = tn;
+        if (it >= 1 && fabs(step) <= 1e-10 * tn0) {
             done = true;
             break;
         }
     }
-    r.T = t;
+    r.T = tn0;
     // rho_vs at the final T from the last evaluation: the step is below
     // 1e-10 T, so the neglected second-order term is below 1e-20 relative
     r.rv = fma(drvs, step, rvs);
-    r.deficit = 0.0;
     r.converged = done;
     return r;
 }
@@ -699,6 +731,12 @@ __device__ __forceinline__ Real wave_speed(const Prim<S::D, S::RAIN, Real> &P) {
     return lam;
 }
 
+// a + b rounded once, never fused with the products that formed a or b: the
+// face flux sums F- + F+ this way so that the result does not depend on the
+// order of the two sides
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
 // trace of a nodal field on face (j, s) at face point q: sum_i l_i(s) v(line node i)
 template <class S, typename Real>
 __device__ __forceinline__ Real interp_face(const Real *v, const Real *ls, int j, int q) {
@@ -930,11 +968,12 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
     flux_dir<S, Real>(Pp, J, Fp);
     const Real lm = wave_speed<S, J, Real>(Pm), lpp = wave_speed<S, J, Real>(Pp);
     const Real lam = lm > lpp ? lm : lpp;
-    const Real hs = Real(0.5) * Real(s);
+    const Real hs = Real(0.5) * Real(s), hl = Real(0.5) * lam;
     Real *out = s_fh + ((el2 * S::NFACE + face) * S::NF) * S::NFP1 + q;
+    // one explicit fma, as in face_flux: both schedules round identically
 #pragma unroll
     for (int f = 0; f < S::NF; ++f)
-        out[f * S::NFP1] = hs * (Fm[f] + Fp[f]) + Real(0.5) * lam * (tm[f] - tp[f]);
+        out[f * S::NFP1] = fma(hs, add_rn(Fm[f], Fp[f]), hl * (tm[f] - tp[f]));
 }
 
 // ---------------------------------------------------------------------------
@@ -1007,9 +1046,11 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     const Real lam = ll > lh ? ll : lh;
     Real *out = A.fbuf + M.fofs[J] + (size_t)f * S::NFP1 + q;
     const size_t fs = (size_t)M.nfaces[J] * S::NFP1;
+    const Real hl = Real(0.5) * lam;
+    // one explicit fma, as in face_point: both schedules round identically
 #pragma unroll
     for (int fld = 0; fld < S::NF; ++fld)
-        out[fld * fs] = Real(0.5) * (Fl[fld] + Fh[fld]) + Real(0.5) * lam * (tl[fld] - th[fld]);
+        out[fld * fs] = fma(Real(0.5), add_rn(Fl[fld], Fh[fld]), hl * (tl[fld] - th[fld]));
 }
 
 constexpr int kFaceThreads = 128;
