@@ -229,7 +229,25 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto
     return w, ctx, info, dt
 
 
-def _roofline(info, word, t_total, steps, peak, peak_kind):
+# DRAM bytes per node and SSPRK stage (k_face + k_stage, face pass) from ncu
+# captures (dram__bytes_read.sum + dram__bytes_write.sum) of the small cases
+# named below; they scale with the node count for the same dimension, order
+# and form.  None (-> traffic null) for any other configuration.
+PROFILED_TRAFFIC = {
+    (3, 4, "fp64"): 418.1,        # 32x32x32 Q4 capture: k_face 117.7 + k_stage 300.4
+    (3, 3, "fp32_bulk"): 241.3,   # 64x64x32 Q3 capture: k_face 74.2 + k_stage 167.1
+    (3, 3, "fp32_pert"): 241.2,   # 64x64x32 Q3 capture: k_face 74.2 + k_stage 167.0
+}
+
+
+def _traffic(w, precision, info):
+    if info.launches_per_stage != 2:
+        return None
+    b = PROFILED_TRAFFIC.get((w["dim"], w["order"], precision))
+    return None if b is None else b * info.n_nodes
+
+
+def _roofline(info, word, t_total, steps, peak, peak_kind, traffic=None):
     # one SSPRK stage: k_stage, preceded by k_face when the face pass is on
     launch_s = t_total / (STAGES * steps)
     bytes_per_launch = algorithmic_bytes_per_node(info.n_fields, word) * info.n_nodes
@@ -239,7 +257,7 @@ def _roofline(info, word, t_total, steps, peak, peak_kind):
               "k_stage (fused RHS + SSPRK stage + next split)")
     return {"bound": "hbm", "kernel": kernel,
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": 1000.0 * launch_s}
 
@@ -322,7 +340,13 @@ def run_gb300(args):
     if dist is not None:
         dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
     e2e_value = world * info.n_dofs * STAGES * e2e_steps / float(e2e_local.item())
-    roof = _roofline(info, word, t_max, args.steps, peak, peak_kind)
+    roof = _roofline(info, word, t_max, args.steps, peak, peak_kind,
+                     _traffic(w, args.precision, info))
+    if args.precision == "fp64":
+        # the float64 form is bound by the FP64 pipe, not by HBM: ncu's pipe
+        # utilisation of the two kernels of a stage (32x32x32 Q4 capture)
+        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.874, "k_face": 0.851,
+                             "source": "ncu sm__inst_executed_pipe_fp64, 32x32x32 Q4 capture"}
     dm.dg_free(ctx)
     del host
 
@@ -343,7 +367,8 @@ def run_gb300(args):
                                forms[form]),
                 "value": world * info2.n_dofs * STAGES * args.steps / t2, "unit": UNIT,
                 "ms_per_step": 1000.0 * t2 / args.steps,
-                "roofline": _roofline(info2, 4, t2, args.steps, peak, peak_kind)}
+                "roofline": _roofline(info2, 4, t2, args.steps, peak, peak_kind,
+                                      _traffic(w2, form, info2))}
             dm.dg_free(ctx2)
 
     # the batched ensemble: 256 uneven 2-D warm-rain bubbles, orders 2-5, FP32-bulk
