@@ -277,6 +277,36 @@ int dg_adjoint_step(dg_ctx *ctx, double dt, const void *U_n, const double *lam_n
  * double; the call synchronises.  DG_ENOTIMPL for DG_FP32_BULK contexts. */
 int dg_cloud_functional(dg_ctx *ctx, const void *U, double *J, double *dJdU);
 
+/* ---- Stabilisation: artificial diffusion and sponge layer ----------------
+ *
+ * Artificial diffusion (Section 3.5, Eq. (3.7)): every field of U gets the
+ * symmetric interior-penalty form with a continuous coefficient alpha:
+ * per element alpha_K = gamma 0.5 h^(1-d/2) ||w||_{0,K} (h = |K|^(1/d);
+ * w = u, or u - v_r e_z for rho_r), projected to continuous Q1 by averaging
+ * over the elements at each vertex; penalty sigma k^2 / h_j on interior
+ * faces (walls carry no diffusive flux).  The coefficient follows the state
+ * the right-hand side is evaluated on.  Needs the face pass (dg_config.faces
+ * != DG_FACES_INLINE).
+ *
+ * Sponge (Section 3.6, Eq. (3.8)), after every dg_step step:
+ * rho_m', rho_r', m, E' <- (1 - delta) (.) and rho_d' += delta (rho_m' + rho_r')
+ * at every node, delta = alpha/2 (1 - cos(pi (z - z_D)/(z_top - z_D))) above
+ * z_D, 0 below. */
+typedef struct dg_stabilisation {
+    double gamma;         /* diffusion scale; 0 switches the diffusion off */
+    double sigma;         /* interior-penalty parameter (> 0 when gamma > 0), e.g. 10 */
+    double sponge_zd;     /* bottom of the sponge layer in m, 0 <= z_D < top */
+    double sponge_alpha;  /* sponge strength in [0, 1]; 0 switches it off */
+} dg_stabilisation;
+
+/* Set (or clear, with zeros) the stabilisation of ctx for the following
+ * dg_rhs / dg_step calls; allocates the diffusion buffers on first use.
+ * Synchronises ctx's stream.  Errors: DG_EINVAL for out-of-range values;
+ * DG_ENOTIMPL for diffusion without the face pass or for an ensemble member;
+ * DG_ENOMEM; DG_ECUDA.  dg_rhs_adjoint and dg_adjoint_step return
+ * DG_ENOTIMPL while either term is on. */
+int dg_set_stabilisation(dg_ctx *ctx, const dg_stabilisation *s);
+
 /* ---- Batched ensemble (SURVEY NEXT-3 form; the paper runs one case at a time) ----
  * Many independent 2-D meshes (any sizes, orders 1..5, rain on or off),
  * FP32-bulk, advanced together: each SSPRK(4,3) stage is one persistent

@@ -78,6 +78,14 @@ double lagrange_at(const double *x, int n, int a, double s) {
     return v;
 }
 
+// l_a'(s) = l_a(s) sum_{m != a} 1 / (s - x_m), for s not a node (s = +-1 here)
+double lagrange_deriv_at(const double *x, int n, int a, double s) {
+    double sum = 0.0;
+    for (int m = 0; m < n; ++m)
+        if (m != a) sum += 1.0 / (s - x[m]);
+    return lagrange_at(x, n, a, s) * sum;
+}
+
 void derivative_matrix(const double *x, int n, double D[6][6]) {
     double bw[6];
     for (int a = 0; a < n; ++a) {
@@ -114,6 +122,12 @@ RefData<Real> make_ref(int order) {
         r.xi[a] = (Real)x[a];
         r.w[a] = (Real)w[a];
         for (int i = 0; i < n; ++i) r.dhat[a][i] = (Real)(w[i] / w[a] * D[i][a]);
+        for (int i = 0; i < n; ++i) r.dmat[i][a] = (Real)D[i][a];
+        const double dlm = lagrange_deriv_at(x, n, a, -1.0), dlp = lagrange_deriv_at(x, n, a, 1.0);
+        r.dlm[a] = (Real)dlm;
+        r.dlp[a] = (Real)dlp;
+        r.dliftm[a] = (Real)(dlm / w[a]);
+        r.dliftp[a] = (Real)(dlp / w[a]);
     }
     return r;
 }
@@ -203,6 +217,8 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     A.rvs_tab = c->rvs_tab;
     A.bsplit = c->bsplit;
     A.fbuf = (Real *)c->fbuf;
+    A.alphaK = (Real *)c->alphaK;
+    A.alphaV = (const Real *)c->alphaV;
     A.flags = c->flags;
     return A;
 }
@@ -212,7 +228,8 @@ int do_prepare(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, co
     KArgs<Real> A = base_args<Real>(c, ref);
     A.Uin = (const Real *)U;
     A.trace_out = (Real *)c->trace[tb];
-    return cuda_status(L->prepare(A, c->stream));
+    A.dtrace_out = (Real *)c->dtrace[tb];
+    return cuda_status(L->prepare(A, c->diff, c->stream));
 }
 
 int prepare(dg_ctx *c, const void *U, int tb) {
@@ -220,38 +237,71 @@ int prepare(dg_ctx *c, const void *U, int tb) {
                    : do_prepare<double>(c, c->L64, c->ref64, U, tb);
 }
 
+// last: the stage that ends a time step (the sponge layer acts there)
 template <typename Real>
 int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int mode, const void *Uin,
-             const void *Un, void *Uout, int tin, double alpha, double beta, double gdt) {
+             const void *Un, void *Uout, int tin, double alpha, double beta, double gdt, bool last) {
     KArgs<Real> A = base_args<Real>(c, ref);
     A.Uin = (const Real *)Uin;
     A.Un = (const Real *)Un;
     A.Uout = (Real *)Uout;
     A.trace_in = (const Real *)c->trace[tin];
     A.trace_out = (Real *)c->trace[1 - tin];
+    A.dtrace_in = (const Real *)c->dtrace[tin];
+    A.dtrace_out = (Real *)c->dtrace[1 - tin];
     A.alpha = (Real)alpha;
     A.beta = (Real)beta;
     A.gdt = (Real)gdt;
-    if (c->face_pass) {
-        const int st = cuda_status(L->face(A, c->stream));
+    A.sponge = (last && mode == MODE_STAGE) ? (const Real *)c->sponge : nullptr;
+    if (c->diff) {
+        const int st = cuda_status(L->alpha_vertex(A, c->stream));
         if (st != DG_OK) return st;
     }
-    return cuda_status(L->stage(A, mode, c->face_pass, c->stream));
+    if (c->face_pass) {
+        const int st = cuda_status(L->face(A, c->diff, c->stream));
+        if (st != DG_OK) return st;
+    }
+    return cuda_status(L->stage(A, mode, c->face_pass, c->diff, c->stream));
 }
 
 int stage(dg_ctx *c, int mode, const void *Uin, const void *Un, void *Uout, int tin, double alpha,
-          double beta, double gdt) {
-    return c->fp32 ? do_stage<float>(c, c->L32, c->ref32, mode, Uin, Un, Uout, tin, alpha, beta, gdt)
-                   : do_stage<double>(c, c->L64, c->ref64, mode, Uin, Un, Uout, tin, alpha, beta, gdt);
+          double beta, double gdt, bool last = false) {
+    return c->fp32 ? do_stage<float>(c, c->L32, c->ref32, mode, Uin, Un, Uout, tin, alpha, beta, gdt,
+                                     last)
+                   : do_stage<double>(c, c->L64, c->ref64, mode, Uin, Un, Uout, tin, alpha, beta, gdt,
+                                      last);
 }
 
 void release(dg_ctx *c) {
     void *ptrs[] = {c->U[0], c->U[1], c->derived, c->trace[0], c->trace[1], c->bnode_d,
                     c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab,
                     c->adjX[0], c->adjX[1], c->adjX[2], c->adjL[0], c->adjL[1], c->adjL[2],
-                    c->ubar_part, c->tadj, c->bsplit, c->fbuf};
+                    c->ubar_part, c->tadj, c->bsplit, c->fbuf, c->alphaK, c->alphaV,
+                    c->dtrace[0], c->dtrace[1], c->sponge};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+}
+
+// face grid and the face-pass buffer layout for per_point values per face
+// point; returns the buffer's length in elements
+long long set_face_layout(dg_ctx *c, int per_point) {
+    MeshData &M = c->M;
+    const dg_config &g = c->cfg;
+    long long fofs = 0;
+    for (int j = 0; j < 3; ++j) {
+        M.nfn[j] = (j < g.dim) ? M.n[j] + (M.periodic[j] ? 0 : 1) : 1;
+        M.nv[j] = M.nfn[j];
+        long long nfj = 0;
+        if (j < g.dim) {
+            nfj = 1;
+            for (int i = 0; i < g.dim; ++i) nfj *= (i == j) ? M.nfn[i] : M.n[i];
+        }
+        M.nfaces[j] = (int)nfj;
+        M.fblk[j] = (int)((nfj * c->nfp1 + kFaceThreads - 1) / kFaceThreads);
+        M.fofs[j] = fofs;
+        fofs += nfj * c->nfp1 * per_point;
+    }
+    return fofs;
 }
 
 int alloc(dg_ctx *c, void **p, size_t bytes) {
@@ -438,19 +488,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     // the face pass is the faster schedule for every precision on GB300
     // (measured: float64 -21 %, float32 forms -8 to -11 % per step)
     c->face_pass = g.faces != DG_FACES_INLINE;
-    long long fofs = 0;
-    for (int j = 0; j < 3; ++j) {
-        M.nfn[j] = (j < g.dim) ? M.n[j] + (M.periodic[j] ? 0 : 1) : 1;
-        long long nfj = 0;
-        if (j < g.dim) {
-            nfj = 1;
-            for (int i = 0; i < g.dim; ++i) nfj *= (i == j) ? M.nfn[i] : M.n[i];
-        }
-        M.nfaces[j] = (int)nfj;
-        M.fblk[j] = (int)((nfj * c->nfp1 + kFaceThreads - 1) / kFaceThreads);
-        M.fofs[j] = fofs;
-        fofs += nfj * c->nfp1 * nf;
-    }
+    const long long fofs = set_face_layout(c, nf);
     c->ref64 = make_ref<double>(g.order);
     c->ref32 = make_ref<float>(g.order);
 
@@ -725,7 +763,7 @@ int dg_step_async(dg_ctx *c, double dt, int nsteps) {
         p ^= 1;
         if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Un, Uw, p, 2.0 / 3.0, 1.0 / 3.0, dt / 6.0);
         p ^= 1;
-        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Un, p, 0.0, 1.0, 0.5 * dt);
+        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Un, p, 0.0, 1.0, 0.5 * dt, true);
         p ^= 1;
         c->parity = p;
     }
@@ -775,7 +813,7 @@ int dg_reduce(dg_ctx *c, double out[DG_NREDUCE]) {
 
 int dg_rhs_adjoint(dg_ctx *c, const void *U, const double *w, double *ubar) {
     if (!c || !U || !w || !ubar || (const void *)ubar == U || ubar == w) return DG_EINVAL;
-    if (c->fp32 || !c->LA) return DG_ENOTIMPL;
+    if (c->fp32 || !c->LA || c->diff || c->sponge) return DG_ENOTIMPL;
     if (!c->base_set) return DG_ESTATE;
     DeviceGuard dg(c->device);
     int st = ensure_adjoint(c);
@@ -786,7 +824,7 @@ int dg_rhs_adjoint(dg_ctx *c, const void *U, const double *w, double *ubar) {
 int dg_adjoint_step(dg_ctx *c, double dt, const void *U_n, const double *lam_np1, double *lam_n) {
     if (!c || !U_n || !lam_np1 || !lam_n || !std::isfinite(dt)) return DG_EINVAL;
     if ((const void *)lam_n == U_n || lam_n == lam_np1) return DG_EINVAL;
-    if (c->fp32 || !c->LA) return DG_ENOTIMPL;
+    if (c->fp32 || !c->LA || c->diff || c->sponge) return DG_ENOTIMPL;
     if (!c->base_set) return DG_ESTATE;
     DeviceGuard dg(c->device);
     int st = ensure_adjoint(c);
@@ -831,6 +869,83 @@ int dg_cloud_functional(dg_ctx *c, const void *U, double *J, double *dJdU) {
     double sum = 0.0;
     for (int b = 0; b < c->nred; ++b) sum += h[b];
     *J = sum;
+    return DG_OK;
+}
+
+int dg_set_stabilisation(dg_ctx *c, const dg_stabilisation *sp) {
+    if (!c || !sp) return DG_EINVAL;
+    const dg_stabilisation p = *sp;
+    const dg_config &g = c->cfg;
+    if (!std::isfinite(p.gamma) || p.gamma < 0.0) return DG_EINVAL;
+    if (p.gamma > 0.0 && !(std::isfinite(p.sigma) && p.sigma > 0.0)) return DG_EINVAL;
+    if (!(p.sponge_alpha >= 0.0 && p.sponge_alpha <= 1.0)) return DG_EINVAL;
+    const double top = g.L[g.dim - 1];
+    if (p.sponge_alpha > 0.0 && !(p.sponge_zd >= 0.0 && p.sponge_zd < top)) return DG_EINVAL;
+    const bool diff = p.gamma > 0.0, sponge = p.sponge_alpha > 0.0;
+    if (diff && !c->face_pass) return DG_ENOTIMPL;
+    if (c->in_ensemble && (diff || sponge)) return DG_ENOTIMPL;
+    DeviceGuard dg(c->device);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
+    MeshData &M = c->M;
+    int st = DG_OK;
+    if (diff && !c->alphaK) {
+        // buffers of the diffusion: alpha per element and vertex, derivative
+        // traces, a face-pass buffer with the symmetry terms
+        const long long nvt = (long long)M.nv[0] * M.nv[1] * (g.dim == 3 ? M.nv[2] : 1);
+        const size_t dtr = (size_t)2 * g.dim * c->nf * c->ne * c->nfp1 * c->rsz;
+        st = alloc(c, &c->alphaK, (size_t)2 * c->ne * c->rsz);
+        if (st == DG_OK) st = alloc(c, &c->alphaV, (size_t)2 * nvt * c->rsz);
+        if (st == DG_OK) st = alloc(c, &c->dtrace[0], dtr);
+        if (st == DG_OK) st = alloc(c, &c->dtrace[1], dtr);
+        if (st == DG_OK) {
+            const long long len = set_face_layout(c, 2 * c->nf);
+            void *nb = nullptr;
+            st = alloc(c, &nb, (size_t)len * c->rsz);
+            if (st == DG_OK) {
+                cudaFree(c->fbuf);
+                c->device_bytes -= (size_t)(len / 2) * c->rsz;
+                c->fbuf = nb;
+            } else {
+                set_face_layout(c, c->nf);
+            }
+        }
+        if (st != DG_OK) return st;
+    }
+    if (diff) {
+        const double h = std::pow(M.h[0] * M.h[1] * (g.dim == 3 ? M.h[2] : 1.0), 1.0 / g.dim);
+        M.alpha_pre = p.gamma * 0.5 * std::pow(h, 1.0 - 0.5 * g.dim);
+        for (int j = 0; j < 3; ++j)
+            M.sigma_pen[j] = j < g.dim ? p.sigma * g.order * g.order / M.h[j] : 0.0;
+    }
+    if (c->alphaK) set_face_layout(c, diff ? 2 * c->nf : c->nf);
+    // sponge profile delta_R at the node levels (Section 3.6)
+    if (sponge) {
+        if (!c->sponge) st = alloc(c, &c->sponge, (size_t)M.nzlev_node * c->rsz);
+        if (st != DG_OK) return st;
+        std::vector<double> d(M.nzlev_node);
+        for (int l = 0; l < M.nzlev_node; ++l) {
+            const double z = c->z_node[l];
+            d[l] = z >= p.sponge_zd
+                       ? 0.5 * p.sponge_alpha * (1.0 - std::cos(M_PI * (z - p.sponge_zd) / (top - p.sponge_zd)))
+                       : 0.0;
+        }
+        cudaError_t e;
+        if (c->fp32) {
+            std::vector<float> f(d.begin(), d.end());
+            e = cudaMemcpy(c->sponge, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(c->sponge, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return DG_ECUDA;
+    } else if (c->sponge) {
+        cudaFree(c->sponge);
+        c->device_bytes -= (size_t)M.nzlev_node * c->rsz;
+        c->sponge = nullptr;
+    }
+    c->stab = p;
+    c->diff = diff;
+    // alpha_K and the derivative traces come with the next split
+    c->derived_valid = false;
     return DG_OK;
 }
 

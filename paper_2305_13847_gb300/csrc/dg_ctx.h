@@ -34,6 +34,13 @@ struct dg_ctx {
     float *bsplit = nullptr;     // DG_FP32_PERT: base-state split tables
     bool face_pass = false;      // faces in k_face (DG_FACES_PASS) instead of in the stage kernel
     void *fbuf = nullptr;        // face pass: fluxes per face point
+    // artificial diffusion and sponge layer (dg_set_stabilisation)
+    dg_stabilisation stab{};
+    bool diff = false;           // gamma > 0
+    bool in_ensemble = false;    // stepped by dg_ensemble_step (no stabilisation there)
+    void *alphaK = nullptr, *alphaV = nullptr;
+    void *dtrace[2] = {nullptr, nullptr};
+    void *sponge = nullptr;      // delta_R at the node levels, storage type
     // adjoint scratch (allocated on first use): stage states, adjoint vectors,
     // partial node adjoints, neighbour trace adjoints
     const AdjLaunchers *LA = nullptr;

@@ -89,6 +89,13 @@ struct MeshData {
     int nfaces[3];
     int fblk[3];
     long long fofs[3];
+    // artificial diffusion (Section 3.5): vertex grid of the continuous Q1
+    // coefficient (n_j vertices per row if periodic, n_j + 1 with walls),
+    // alpha_K = alpha_pre ||w||_{0,K} with alpha_pre = gamma 0.5 h^(1 - d/2),
+    // interior-penalty factor sigma k^2 / h_j per direction
+    int nv[3];
+    double alpha_pre;
+    double sigma_pen[3];
 };
 
 template <typename Real>
@@ -97,6 +104,11 @@ struct RefData {
     Real lm[6], lp[6];       // l_a(-1), l_a(+1)
     Real liftm[6], liftp[6]; // l_a(-1)/w_a, l_a(+1)/w_a
     Real xi[6], w[6];
+    // artificial diffusion: nodal derivative matrix dmat[i][a] = l_a'(xi_i),
+    // l_a'(-1), l_a'(+1) and their lifts l_a'(+-1)/w_a
+    Real dmat[6][6];
+    Real dlm[6], dlp[6];
+    Real dliftm[6], dliftp[6];
 };
 
 template <typename Real>
@@ -114,7 +126,13 @@ struct KArgs {
     const double *bnode_d; // float64 copy for the split
     const double *rvs_tab; // rho_vs table: [kTabN][2] = (rho_vs(T_i), 1/T_i)
     const float *bsplit;   // DG_FP32_PERT: split of the base state per node level [kBsN][nzlev_node]
-    Real *fbuf;            // face pass: Lax-Friedrichs flux along +e_j per face point (MeshData.fofs)
+    Real *fbuf;            // face pass: Lax-Friedrichs flux along +e_j per face point (MeshData.fofs);
+                           // with diffusion [2 NF]: flux, then S = alpha [[u]] / 2
+    Real *alphaK;          // diffusion: [2][ne] alpha_u, alpha_r per element (of the state produced)
+    const Real *alphaV;    // diffusion: [2][nv] continuous coefficient at the vertices
+    const Real *dtrace_in; // diffusion: d/dx_j traces of Uin  [2D][NF][ne][NFP1]
+    Real *dtrace_out;      // diffusion: d/dx_j traces of Uout
+    const Real *sponge;    // sponge delta_R at the node levels (last stage of a step) or null
     Real alpha, beta, gdt; // Uout = alpha Un + beta Uin + gdt dU/dt
     unsigned long long *flags;  // [0] Newton failures, [1] non-physical nodes
 };
@@ -139,6 +157,7 @@ struct Shape {
     static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;   // elements per CTA
     static constexpr int NT = ((EPB * NP + 31) / 32) * 32;          // threads per CTA
     static constexpr int VERT = D - 1;
+    static constexpr int NCORNER = 1 << D;                          // element vertices
 };
 
 template <int D, int P1>
@@ -749,7 +768,9 @@ __device__ __forceinline__ Real interp_face(const Real *v, const Real *ls, int j
 // ---------------------------------------------------------------------------
 // k_prepare: split at every node and traces of every face
 // ---------------------------------------------------------------------------
-template <class S, typename Real>
+// DIFF: also the traces of d/dx_j U on the faces normal to e_j,
+// (2/h_j) sum_i l_i'(s) U(line node i), for the interior-penalty terms
+template <class S, typename Real, bool DIFF = false>
 __device__ __forceinline__ void write_traces(const KArgs<Real> &A, const RefData<Real> &ref,
                                              const Real *s_tr, Real *trace_out, int bidx) {
     const int ne = A.M.ne;
@@ -768,6 +789,128 @@ __device__ __forceinline__ void write_traces(const KArgs<Real> &A, const RefData
             trace_out[(((size_t)face * S::NTR + fld) * ne + e) * S::NFP1 + q] =
                 interp_face<S, Real>(v, ls, j, q);
         }
+        if (DIFF) {
+            const Real *dls = (face & 1) ? ref.dlp : ref.dlm;
+            const Real sc = Real(A.M.two_over_h[j]);
+#pragma unroll
+            for (int fld = 0; fld < S::NF; ++fld) {
+                const Real *v = s_tr + (size_t)fld * S::EPB * S::NP + el * S::NP;
+                A.dtrace_out[(((size_t)face * S::NF + fld) * ne + e) * S::NFP1 + q] =
+                    sc * interp_face<S, Real>(v, dls, j, q);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Artificial diffusion helpers (Section 3.5)
+// ---------------------------------------------------------------------------
+// weight W_a |K|/2^d of node a times |u|^2 and |u - v_r e_z|^2, added to the
+// element's sums s_red[0..1] (shared memory)
+template <class S, typename Real>
+__device__ __forceinline__ void alpha_accumulate(const KArgs<Real> &A, const RefData<Real> &ref,
+                                                 const Real *u, Real vr, int a, int lev,
+                                                 Real *s_red) {
+    const int nl = A.M.nzlev_node;
+    const Real rho = (A.bnode[lev] + u[0]) + (A.bnode[nl + lev] + u[1]) + (S::RAIN ? u[2] : Real(0));
+    const Real inv = recip(rho);
+    Real wq = Real(A.M.jac);
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) wq *= ref.w[digit<S::D, S::P1>(a, j)];
+    Real w2u = Real(0), w2r = Real(0);
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) {
+        const Real uj = u[S::IM + j] * inv;
+        w2u = fma(uj, uj, w2u);
+        const Real ur = (j == S::VERT) ? uj - vr : uj;
+        w2r = fma(ur, ur, w2r);
+    }
+    atomicAdd(&s_red[0], wq * w2u);
+    if (S::RAIN) atomicAdd(&s_red[1], wq * w2r);
+}
+
+// alpha_K = alpha_pre ||w||_{0,K} from the element sums (threads t < EPB)
+template <class S, typename Real>
+__device__ __forceinline__ void alpha_store(const KArgs<Real> &A, const Real *s_red, int bidx) {
+    const int t = threadIdx.x;
+    if (t < S::EPB) {
+        const int e = bidx * S::EPB + t;
+        if (e < A.M.ne) {
+            const Real pre = Real(A.M.alpha_pre);
+            A.alphaK[e] = pre * sqrt(s_red[2 * t]);
+            A.alphaK[A.M.ne + e] = S::RAIN ? pre * sqrt(s_red[2 * t + 1]) : Real(0);
+        }
+    }
+}
+
+// the element's 2^d vertex values of the continuous coefficient (alpha_u, then
+// alpha_r), corner c = sum_j b_j 2^j at vertex im + b
+template <class S, typename Real>
+__device__ __forceinline__ void alpha_corners(const KArgs<Real> &A, const int *im, Real *out) {
+    const MeshData &M = A.M;
+    const int nvt = M.nv[0] * M.nv[1] * (S::D == 3 ? M.nv[2] : 1);
+#pragma unroll
+    for (int c = 0; c < S::NCORNER; ++c) {
+        int v[3] = {0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            v[j] = im[j] + ((c >> j) & 1);
+            if (v[j] >= M.nv[j]) v[j] -= M.n[j];     // periodic wrap (nv = n)
+        }
+        const int flat = v[0] + M.nv[0] * (v[1] + M.nv[1] * v[2]);
+        out[c] = A.alphaV[flat];
+        out[S::NCORNER + c] = A.alphaV[nvt + flat];
+    }
+}
+
+// Q1 interpolant at reference point xi[0..D) of corner values cv[NCORNER]
+template <class S, typename Real>
+__device__ __forceinline__ Real q1_interp(const Real *cv, const Real *xi) {
+    Real acc = Real(0);
+#pragma unroll
+    for (int c = 0; c < S::NCORNER; ++c) {
+        Real wgt = Real(1);
+#pragma unroll
+        for (int j = 0; j < S::D; ++j)
+            wgt *= ((c >> j) & 1) ? Real(0.5) * (Real(1) + xi[j]) : Real(0.5) * (Real(1) - xi[j]);
+        acc = fma(wgt, cv[c], acc);
+    }
+    return acc;
+}
+
+// vertex values of the continuous coefficient: mean of alpha_K over the
+// elements sharing the vertex (lumped L2 projection onto continuous Q1)
+template <int D, typename Real>
+__global__ void k_alpha_vertex(MeshData M, const Real *alphaK, Real *alphaV) {
+    const int nvt = M.nv[0] * M.nv[1] * (D == 3 ? M.nv[2] : 1);
+    for (int gid = blockIdx.x * blockDim.x + threadIdx.x; gid < nvt; gid += gridDim.x * blockDim.x) {
+        int v[3];
+        v[0] = gid % M.nv[0];
+        const int r = gid / M.nv[0];
+        v[1] = D == 3 ? r % M.nv[1] : r;
+        v[2] = D == 3 ? r / M.nv[1] : 0;
+        Real su = Real(0), sr = Real(0);
+        int cnt = 0;
+        for (int c = 0; c < (1 << D); ++c) {
+            int ei[3] = {0, 0, 0};
+            bool ok = true;
+            for (int j = 0; j < D; ++j) {
+                int x = v[j] - 1 + ((c >> j) & 1);
+                if (M.periodic[j]) {
+                    if (x < 0) x += M.n[j];
+                } else if (x < 0 || x >= M.n[j]) {
+                    ok = false;
+                }
+                ei[j] = x;
+            }
+            if (!ok) continue;
+            const int e = ei[0] + M.n[0] * (ei[1] + M.n[1] * ei[2]);
+            su += alphaK[e];
+            sr += alphaK[M.ne + e];
+            ++cnt;
+        }
+        alphaV[gid] = su / Real(cnt);
+        alphaV[nvt + gid] = sr / Real(cnt);
     }
 }
 
@@ -793,9 +936,9 @@ __device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<f
                                       A.bnode[lev], A.bnode[nl + lev], A.M, A.rvs_tab);
 }
 
-template <class S, typename Real>
+template <class S, typename Real, bool DIFF = false>
 __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real *u, int e, int a,
-                                                int iz, Real *s_tr, int t) {
+                                                int iz, Real *s_tr, int t, Real *s_red = nullptr) {
     const size_t nodes = (size_t)A.M.ne * S::NP;
     const size_t gi = (size_t)e * S::NP + a;
     const int lev = iz * S::P1 + digit<S::D, S::P1>(a, S::VERT);
@@ -823,6 +966,7 @@ __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real
         A.derived[3 * nodes + gi] = gm;
         A.derived[4 * nodes + gi] = vr;
     }
+    if (DIFF) alpha_accumulate<S, Real>(A, A.ref, u, vr, a, lev, s_red + 2 * (t / S::NP));
     const int str = S::EPB * S::NP;
 #pragma unroll
     for (int f = 0; f < S::NF; ++f) s_tr[f * str + t] = u[f];
@@ -831,24 +975,31 @@ __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real
     s_tr[(S::NF + 2) * str + t] = pp;
 }
 
-template <class S, typename Real>
+// DIFF: also the element coefficients alpha_K and the derivative traces
+template <class S, typename Real, bool DIFF>
 __global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *s_tr = reinterpret_cast<Real *>(smem_raw);  // [NTR][EPB*NP]
+    Real *s_red = s_tr + S::NTR * S::EPB * S::NP;    // [EPB][2]
     const int t = threadIdx.x;
     const int el = t / S::NP, a = t - el * S::NP;
     const int e = blockIdx.x * S::EPB + el;
     const bool valid = (t < S::EPB * S::NP) && (e < A.M.ne);
+    if (DIFF) {
+        if (t < 2 * S::EPB) s_red[t] = Real(0);
+        __syncthreads();
+    }
     if (valid) {
         const size_t nodes = (size_t)A.M.ne * S::NP;
         const size_t gi = (size_t)e * S::NP + a;
         Real u[S::NF];
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
-        split_and_store<S, Real>(A, u, e, a, vert_index<S::D>(A.M, e), s_tr, t);
+        split_and_store<S, Real, DIFF>(A, u, e, a, vert_index<S::D>(A.M, e), s_tr, t, s_red);
     }
     __syncthreads();
-    write_traces<S, Real>(A, A.ref, s_tr, A.trace_out, blockIdx.x);
+    if (DIFF) alpha_store<S, Real>(A, s_red, blockIdx.x);
+    write_traces<S, Real, DIFF>(A, A.ref, s_tr, A.trace_out, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -859,21 +1010,27 @@ constexpr int MODE_STAGE = 1;
 
 // Shared memory of a stage tile: nodal fluxes s_fl [D][NF][EPB NP], node
 // values for the traces s_tr [NTR][EPB NP], face fluxes s_fh
-// [EPB][2D][NF][NFP1] and per-element indices.  s_tr is needed during the
-// face phase only when the float32 inline form interpolates its own traces
-// there; otherwise it is filled after the volume phase and shares s_fl.
-template <class S, typename Real, bool PF>
+// [EPB][2D][NF][NFP1] (with diffusion also the symmetry terms s_fs of the
+// same shape), per-element indices and, with diffusion, the element's
+// vertex coefficients [EPB][2][2^D] and its alpha sums [EPB][2].  s_tr is
+// needed before the volume phase only when the float32 inline form
+// interpolates its own traces in the face phase, or with diffusion (the
+// derivatives of the node values); otherwise it is filled after the volume
+// phase and shares s_fl.
+template <class S, typename Real, bool PF, bool DIFF = false>
 __host__ __device__ constexpr bool tr_shares_fl() {
-    return PF || sizeof(Real) == sizeof(double);
+    return (PF || sizeof(Real) == sizeof(double)) && !DIFF;
 }
 
-template <class S, typename Real, bool PF = false>
+template <class S, typename Real, bool PF = false, bool DIFF = false>
 constexpr size_t stage_smem_bytes() {
     constexpr size_t str = (size_t)S::EPB * S::NP;
     constexpr size_t fl = (size_t)S::D * S::NF * str, tr = (size_t)S::NTR * str;
-    return sizeof(Real) * ((tr_shares_fl<S, Real, PF>() ? (fl > tr ? fl : tr) : fl + tr) +
-                           (size_t)S::EPB * S::NFACE * S::NF * S::NFP1) +
-           sizeof(int) * 16 * (size_t)S::EPB;  // per element: 2D neighbours, vertical index, 2D faces
+    constexpr size_t fh = (size_t)S::EPB * S::NFACE * S::NF * S::NFP1;
+    return sizeof(Real) * ((tr_shares_fl<S, Real, PF, DIFF>() ? (fl > tr ? fl : tr) : fl + tr) +
+                           (DIFF ? 2 * fh : fh)) +
+           sizeof(int) * 16 * (size_t)S::EPB +  // per element: 2D neighbours, vertical index, 2D faces
+           (DIFF ? sizeof(Real) * (size_t)S::EPB * (2 * S::NCORNER + 2) : 0);
 }
 
 // neighbour element across face (j, s) from the element's multi-index, or -1 (wall)
@@ -984,7 +1141,7 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
 // missing element with the ghost state m -> m - 2 (m.n) n.  The element on
 // the lo side lifts +G, the one on the hi side -G, so the two contributions
 // cancel exactly in the sums of the conserved quantities.
-template <class S, typename Real, int J>
+template <class S, typename Real, int J, bool DIFF>
 __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     const MeshData &M = A.M;
     const int ne = M.ne;
@@ -1048,14 +1205,77 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     const size_t fs = (size_t)M.nfaces[J] * S::NFP1;
     const Real hl = Real(0.5) * lam;
     // one explicit fma, as in face_point: both schedules round identically
+    Real G[S::NF];
 #pragma unroll
     for (int fld = 0; fld < S::NF; ++fld)
-        out[fld * fs] = fma(Real(0.5), add_rn(Fl[fld], Fh[fld]), hl * (tl[fld] - th[fld]));
+        G[fld] = fma(Real(0.5), add_rn(Fl[fld], Fh[fld]), hl * (tl[fld] - th[fld]));
+    if (DIFF) {
+        // interior penalty (Eq. (3.7)) on interior faces: viscous flux along +e_j
+        //   V = -alpha {{du/dx_j}} + sigma k^2/h_j alpha [[u]],  [[u]] = u_lo - u_hi,
+        // added to G, and S = alpha [[u]] / 2 for the symmetry term, lifted by
+        // both elements with l_a'(+-1)/w_a; walls carry no diffusive flux
+        Real Sx[S::NF];
+#pragma unroll
+        for (int fld = 0; fld < S::NF; ++fld) Sx[fld] = Real(0);
+        if (e_lo >= 0 && e_hi >= 0) {
+            // continuous coefficient at the face point: Q1 over the face's vertices
+            const int nvt = M.nv[0] * M.nv[1] * (S::D == 3 ? M.nv[2] : 1);
+            Real au = Real(0), ar = Real(0);
+            int qd[3] = {0, 0, 0};
+            {
+                int r = q, o = 0;
+#pragma unroll
+                for (int i = 0; i < S::D; ++i) {
+                    if (i == J) continue;
+                    qd[i] = (o + 1 < S::D - 1) ? r % S::P1 : r;
+                    r /= S::P1;
+                    ++o;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < (1 << (S::D - 1)); ++c) {
+                int v[3] = {0, 0, 0};
+                Real wgt = Real(1);
+                int o = 0;
+#pragma unroll
+                for (int i = 0; i < S::D; ++i) {
+                    if (i == J) {
+                        v[i] = im[J];          // the face coordinate c
+                        continue;
+                    }
+                    const int b = (c >> o) & 1;
+                    ++o;
+                    v[i] = im[i] + b;
+                    if (v[i] >= M.nv[i]) v[i] -= M.n[i];
+                    const Real x = A.ref.xi[qd[i]];
+                    wgt *= b ? Real(0.5) * (Real(1) + x) : Real(0.5) * (Real(1) - x);
+                }
+                const int flat = v[0] + M.nv[0] * (v[1] + M.nv[1] * v[2]);
+                au = fma(wgt, A.alphaV[flat], au);
+                ar = fma(wgt, A.alphaV[nvt + flat], ar);
+            }
+            const Real sig = Real(M.sigma_pen[J]);
+#pragma unroll
+            for (int fld = 0; fld < S::NF; ++fld) {
+                const Real al = (S::RAIN && fld == 2) ? ar : au;
+                const Real dl =
+                    A.dtrace_in[(((size_t)(2 * J + 1) * S::NF + fld) * ne + e_lo) * S::NFP1 + q];
+                const Real dh = A.dtrace_in[(((size_t)(2 * J) * S::NF + fld) * ne + e_hi) * S::NFP1 + q];
+                const Real jump = tl[fld] - th[fld];
+                G[fld] += al * (sig * jump - Real(0.5) * (dl + dh));
+                Sx[fld] = Real(0.5) * al * jump;
+            }
+        }
+#pragma unroll
+        for (int fld = 0; fld < S::NF; ++fld) out[(S::NF + fld) * fs] = Sx[fld];
+    }
+#pragma unroll
+    for (int fld = 0; fld < S::NF; ++fld) out[fld * fs] = G[fld];
 }
 
 constexpr int kFaceThreads = 128;
 
-template <class S, typename Real>
+template <class S, typename Real, bool DIFF>
 __global__ void __launch_bounds__(kFaceThreads) k_face(KArgs<Real> A) {
     int b = blockIdx.x, J = 0;
     if (b >= A.M.fblk[0]) {
@@ -1070,9 +1290,9 @@ __global__ void __launch_bounds__(kFaceThreads) k_face(KArgs<Real> A) {
     const int f = (int)(gid / S::NFP1), q = (int)(gid - (long long)f * S::NFP1);
     if (f >= A.M.nfaces[J]) return;
     switch (J) {
-        case 0: face_flux<S, Real, 0>(A, f, q); break;
-        case 1: face_flux<S, Real, 1>(A, f, q); break;
-        default: face_flux<S, Real, (S::D == 3 ? 2 : 1)>(A, f, q); break;
+        case 0: face_flux<S, Real, 0, DIFF>(A, f, q); break;
+        case 1: face_flux<S, Real, 1, DIFF>(A, f, q); break;
+        default: face_flux<S, Real, (S::D == 3 ? 2 : 1), DIFF>(A, f, q); break;
     }
 }
 
@@ -1080,17 +1300,22 @@ __global__ void __launch_bounds__(kFaceThreads) k_face(KArgs<Real> A) {
 // kernel; every thread of the CTA takes part (the body has barriers).
 // PF: the face fluxes come from the face pass (k_face) instead of being
 // evaluated here on both sides of every face.
-template <class S, typename Real, int MODE, bool PF = false>
+template <class S, typename Real, int MODE, bool PF = false, bool DIFF = false>
 __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<Real> &ref, int bidx,
                                             unsigned char *smem_raw) {
+    static_assert(!DIFF || PF, "artificial diffusion runs with the face pass");
     constexpr int STR = S::EPB * S::NP;
-    constexpr bool SHARE = tr_shares_fl<S, Real, PF>();
+    constexpr bool SHARE = tr_shares_fl<S, Real, PF, DIFF>();
     constexpr int FLTR = SHARE ? (S::D * S::NF > S::NTR ? S::D * S::NF : S::NTR) * STR
                                : (S::D * S::NF + S::NTR) * STR;
+    constexpr int FH = S::EPB * S::NFACE * S::NF * S::NFP1;
     Real *s_fl = reinterpret_cast<Real *>(smem_raw);          // [D][NF][STR]
     Real *s_tr = SHARE ? s_fl : s_fl + S::D * S::NF * STR;    // [NTR][STR]
     Real *s_fh = s_fl + FLTR;                                 // [EPB][NFACE][NF][NFP1]
-    int *s_info = reinterpret_cast<int *>(s_fh + S::EPB * S::NFACE * S::NF * S::NFP1);  // [EPB][16]
+    Real *s_fs = s_fh + FH;                                   // DIFF: symmetry terms, same shape
+    int *s_info = reinterpret_cast<int *>(s_fh + (DIFF ? 2 * FH : FH));  // [EPB][16]
+    Real *s_al = reinterpret_cast<Real *>(s_info + 16 * S::EPB);        // DIFF: [EPB][2][NCORNER]
+    Real *s_red = s_al + S::EPB * 2 * S::NCORNER;                       // DIFF: [EPB][2]
     const MeshData &M = A.M;
     const int ne = M.ne;
     const size_t nodes = (size_t)ne * S::NP;
@@ -1117,6 +1342,11 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 }
             }
             s_info[t * 16 + 6] = im[S::VERT];
+            if (DIFF) alpha_corners<S, Real>(A, im, s_al + t * 2 * S::NCORNER);
+        }
+        if (DIFF) {
+            s_red[2 * t] = Real(0);
+            s_red[2 * t + 1] = Real(0);
         }
     }
     __syncthreads();
@@ -1144,8 +1374,11 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) R[f] = Real(0);
         // node values for the own traces (the float64 form reads them back
-        // from the trace buffer)
-        if (!PF && sizeof(Real) == sizeof(float)) {
+        // from the trace buffer) or for the derivatives of the diffusion
+        if (DIFF) {
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) s_tr[f * STR + t] = u[f];
+        } else if (!PF && sizeof(Real) == sizeof(float)) {
 #pragma unroll
             for (int f = 0; f < S::NF; ++f) s_tr[f * STR + t] = u[f];
             s_tr[S::NF * STR + t] = T;
@@ -1163,6 +1396,35 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         R[S::IE] = -g * u[S::IM + S::VERT];
     }
     __syncthreads();
+
+    // ---- phase 1b (diffusion): F_j -= alpha du/dx_j at the node, so that the
+    // volume term below also carries (alpha grad u, grad phi_a) of Eq. (3.7)
+    if (DIFF) {
+        if (valid) {
+            Real xi[3];
+#pragma unroll
+            for (int j = 0; j < S::D; ++j) xi[j] = ref.xi[digit<S::D, S::P1>(a, j)];
+            const Real *cv = s_al + el * 2 * S::NCORNER;
+            const Real au = q1_interp<S, Real>(cv, xi), ar = q1_interp<S, Real>(cv + S::NCORNER, xi);
+#pragma unroll
+            for (int j = 0; j < S::D; ++j) {
+                const int aj = digit<S::D, S::P1>(a, j);
+                const int st = stride_of<S::P1>(j);
+                const int b0 = el * S::NP + a - aj * st;
+                const Real sc = Real(M.two_over_h[j]);
+#pragma unroll
+                for (int f = 0; f < S::NF; ++f) {
+                    const Real *v = s_tr + f * STR + b0;
+                    Real du = Real(0);
+#pragma unroll
+                    for (int i = 0; i < S::P1; ++i) du = fma(ref.dmat[aj][i], v[i * st], du);
+                    const Real al = (S::RAIN && f == 2) ? ar : au;
+                    s_fl[(j * S::NF + f) * STR + t] -= al * (sc * du);
+                }
+            }
+        }
+        __syncthreads();
+    }
 
     // ---- phase 2a: volume term, sum factorised: R_a += (2/h_j) sum_i dhat[a_j][i] F_j(i)
     if (valid) {
@@ -1196,9 +1458,10 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             const int q = r2 - fld * S::NFP1;
             if (bidx * S::EPB + el2 >= ne) continue;
             const int j = face >> 1;
-            const Real g = A.fbuf[M.fofs[j] +
-                                  ((size_t)fld * M.nfaces[j] + s_info[el2 * 16 + 8 + face]) * S::NFP1 + q];
+            const size_t fb = M.fofs[j] + ((size_t)fld * M.nfaces[j] + s_info[el2 * 16 + 8 + face]) * S::NFP1 + q;
+            const Real g = A.fbuf[fb];
             s_fh[item] = (face & 1) ? g : -g;
+            if (DIFF) s_fs[item] = A.fbuf[fb + (size_t)S::NF * M.nfaces[j] * S::NFP1];
         }
     } else {
         for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
@@ -1234,6 +1497,14 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 #pragma unroll
             for (int f = 0; f < S::NF; ++f)
                 R[f] -= cp * fp[f * S::NFP1] + cm * fm[f * S::NFP1];
+            if (DIFF) {
+                // symmetry term of Eq. (3.7): + (2/h_j)^2 l_a'(s)/w_a S on both faces
+                const Real *sm = s_fs + ((el * S::NFACE + 2 * j) * S::NF) * S::NFP1 + q;
+                const Real *sp = s_fs + ((el * S::NFACE + 2 * j + 1) * S::NF) * S::NFP1 + q;
+                const Real dm = sc * sc * ref.dliftm[aj], dp = sc * sc * ref.dliftp[aj];
+#pragma unroll
+                for (int f = 0; f < S::NF; ++f) R[f] += dp * sp[f * S::NFP1] + dm * sm[f * S::NFP1];
+            }
         }
         const size_t gi = (size_t)e * S::NP + a;
         if (MODE == MODE_RHS) {
@@ -1246,21 +1517,36 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 Real v = A.beta * u[f] + A.gdt * R[f];
                 if (A.alpha != Real(0)) v += A.alpha * A.Un[f * nodes + gi];
                 un[f] = v;
-                A.Uout[f * nodes + gi] = v;
             }
-            split_and_store<S, Real>(A, un, e, a, s_info[el * 16 + 6], s_tr, t);
+            if (A.sponge) {
+                // Eq. (3.8) at the end of the step: relax rho_m', rho_r', m, E'
+                // towards 0 and add the moisture removed to rho_d' (Section 3.6)
+                const Real dl = A.sponge[s_info[el * 16 + 6] * S::P1 + digit<S::D, S::P1>(a, S::VERT)];
+                if (dl != Real(0)) {
+                    const Real om = Real(1) - dl;
+                    Real removed = dl * un[1];
+                    if (S::RAIN) removed = add_rn(removed, dl * un[2]);
+                    un[0] = un[0] + removed;
+#pragma unroll
+                    for (int f = 1; f < S::NF; ++f) un[f] = om * un[f];
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) A.Uout[f * nodes + gi] = un[f];
+            split_and_store<S, Real, DIFF>(A, un, e, a, s_info[el * 16 + 6], s_tr, t, s_red);
         }
     }
     if (MODE == MODE_STAGE) {
         __syncthreads();
-        write_traces<S, Real>(A, ref, s_tr, A.trace_out, bidx);
+        if (DIFF) alpha_store<S, Real>(A, s_red, bidx);
+        write_traces<S, Real, DIFF>(A, ref, s_tr, A.trace_out, bidx);
     }
 }
 
-template <class S, typename Real, int MODE, bool PF>
+template <class S, typename Real, int MODE, bool PF, bool DIFF>
 __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_block<S, Real, MODE, PF>(A, A.ref, blockIdx.x, smem_raw);
+    stage_block<S, Real, MODE, PF, DIFF>(A, A.ref, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -296,6 +296,7 @@ int dg_ensemble_create(dg_ensemble **out, int n, const dg_config *cfgs, const dg
         dg_ctx *c = nullptr;
         st = dg_init_mesh(&c, &cfgs[i], E->stream);
         if (st == DG_OK) {
+            c->in_ensemble = true;
             E->members.push_back(c);
             st = dg_init_bubble(c, &bubbles[i], nullptr, DG_HOST);
         }

@@ -11,10 +11,12 @@ template <typename Real>
 struct Launchers {
     int nf, np, nfp1, nd, ntr, epb, nt;
     size_t prep_smem, stage_smem;
-    cudaError_t (*prepare)(const KArgs<Real> &, cudaStream_t);
+    // diff: with the artificial diffusion of Eq. (3.7) (face pass only)
+    cudaError_t (*prepare)(const KArgs<Real> &, bool diff, cudaStream_t);
     // pf: the stage kernel takes its face fluxes from the face pass
-    cudaError_t (*stage)(const KArgs<Real> &, int mode, bool pf, cudaStream_t);
-    cudaError_t (*face)(const KArgs<Real> &, cudaStream_t);
+    cudaError_t (*stage)(const KArgs<Real> &, int mode, bool pf, bool diff, cudaStream_t);
+    cudaError_t (*face)(const KArgs<Real> &, bool diff, cudaStream_t);
+    cudaError_t (*alpha_vertex)(const KArgs<Real> &, cudaStream_t);
     cudaError_t (*split)(const KArgs<Real> &, double *, double *, double *, double *, cudaStream_t);
     cudaError_t (*init_bubble)(const KArgs<Real> &, const BubbleArgs &, cudaStream_t);
     cudaError_t (*reduce)(const KArgs<Real> &, double *partials, int nblocks, cudaStream_t);
@@ -30,48 +32,72 @@ inline int grid_for(size_t n, int threads) {
 
 template <class S, typename Real>
 struct Impl {
-    static constexpr size_t prep_smem = sizeof(Real) * (size_t)S::NTR * S::EPB * S::NP;
+    static constexpr size_t prep_smem = sizeof(Real) * ((size_t)S::NTR * S::EPB * S::NP + 2 * S::EPB);
     static constexpr size_t stage_smem = stage_smem_bytes<S, Real, false>();
     static constexpr size_t stage_smem_pf = stage_smem_bytes<S, Real, true>();
+    static constexpr size_t stage_smem_diff = stage_smem_bytes<S, Real, true, true>();
 
     static int blocks(const KArgs<Real> &A) { return (A.M.ne + S::EPB - 1) / S::EPB; }
 
-    static cudaError_t prepare(const KArgs<Real> &A, cudaStream_t st) {
+    template <bool DIFF>
+    static cudaError_t launch_prepare(const KArgs<Real> &A, cudaStream_t st) {
         static bool attr = false;
         if (!attr) {
-            cudaError_t err = cudaFuncSetAttribute(k_prepare<S, Real>,
+            cudaError_t err = cudaFuncSetAttribute(k_prepare<S, Real, DIFF>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)prep_smem);
             if (err != cudaSuccess) return err;
             attr = true;
         }
-        k_prepare<S, Real><<<blocks(A), S::NT, prep_smem, st>>>(A);
+        k_prepare<S, Real, DIFF><<<blocks(A), S::NT, prep_smem, st>>>(A);
         return cudaGetLastError();
     }
 
-    template <int MODE, bool PF>
+    static cudaError_t prepare(const KArgs<Real> &A, bool diff, cudaStream_t st) {
+        return diff ? launch_prepare<true>(A, st) : launch_prepare<false>(A, st);
+    }
+
+    template <int MODE, bool PF, bool DIFF>
     static cudaError_t launch_stage(const KArgs<Real> &A, cudaStream_t st) {
+        constexpr size_t smem = DIFF ? stage_smem_diff : (PF ? stage_smem_pf : stage_smem);
         static bool attr = false;
         if (!attr) {
-            cudaError_t err = cudaFuncSetAttribute(k_stage<S, Real, MODE, PF>,
+            cudaError_t err = cudaFuncSetAttribute(k_stage<S, Real, MODE, PF, DIFF>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(PF ? stage_smem_pf : stage_smem));
+                                                   (int)smem);
             if (err != cudaSuccess) return err;
             attr = true;
         }
-        k_stage<S, Real, MODE, PF><<<blocks(A), S::NT, PF ? stage_smem_pf : stage_smem, st>>>(A);
+        k_stage<S, Real, MODE, PF, DIFF><<<blocks(A), S::NT, smem, st>>>(A);
         return cudaGetLastError();
     }
 
-    static cudaError_t stage(const KArgs<Real> &A, int mode, bool pf, cudaStream_t st) {
+    static cudaError_t stage(const KArgs<Real> &A, int mode, bool pf, bool diff, cudaStream_t st) {
+        if (diff) {
+            if (!pf) return cudaErrorInvalidValue;
+            return mode == MODE_RHS ? launch_stage<MODE_RHS, true, true>(A, st)
+                                    : launch_stage<MODE_STAGE, true, true>(A, st);
+        }
         if (mode == MODE_RHS)
-            return pf ? launch_stage<MODE_RHS, true>(A, st) : launch_stage<MODE_RHS, false>(A, st);
-        return pf ? launch_stage<MODE_STAGE, true>(A, st) : launch_stage<MODE_STAGE, false>(A, st);
+            return pf ? launch_stage<MODE_RHS, true, false>(A, st)
+                      : launch_stage<MODE_RHS, false, false>(A, st);
+        return pf ? launch_stage<MODE_STAGE, true, false>(A, st)
+                  : launch_stage<MODE_STAGE, false, false>(A, st);
     }
 
-    static cudaError_t face(const KArgs<Real> &A, cudaStream_t st) {
+    static cudaError_t face(const KArgs<Real> &A, bool diff, cudaStream_t st) {
         const int nb = A.M.fblk[0] + A.M.fblk[1] + A.M.fblk[2];
-        k_face<S, Real><<<nb, kFaceThreads, 0, st>>>(A);
+        if (diff)
+            k_face<S, Real, true><<<nb, kFaceThreads, 0, st>>>(A);
+        else
+            k_face<S, Real, false><<<nb, kFaceThreads, 0, st>>>(A);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t alpha_vertex(const KArgs<Real> &A, cudaStream_t st) {
+        const size_t nvt = (size_t)A.M.nv[0] * A.M.nv[1] * (S::D == 3 ? A.M.nv[2] : 1);
+        k_alpha_vertex<S::D, Real><<<grid_for(nvt, 256), 256, 0, st>>>(A.M, A.alphaK,
+                                                                        const_cast<Real *>(A.alphaV));
         return cudaGetLastError();
     }
 
@@ -107,6 +133,7 @@ struct Impl {
         L.prepare = &prepare;
         L.stage = &stage;
         L.face = &face;
+        L.alpha_vertex = &alpha_vertex;
         L.split = &split;
         L.init_bubble = &init_bubble;
         L.reduce = &reduce;

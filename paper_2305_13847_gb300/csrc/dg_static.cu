@@ -166,7 +166,7 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     if (cudaGetLastError() != cudaSuccess) return DG_ECUDA;
     A.Uin = static_cast<const double *>(U);
     A.trace_out = trace;
-    if (L->prepare(A, stream) != cudaSuccess) return DG_ECUDA;
+    if (L->prepare(A, false, stream) != cudaSuccess) return DG_ECUDA;
     A.Un = A.Uin;
     A.Uout = static_cast<double *>(dUdt);
     A.trace_in = trace;
@@ -174,6 +174,6 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     A.alpha = 0.0;
     A.beta = 1.0;
     A.gdt = 1.0;
-    if (L->stage(A, MODE_RHS, false, stream) != cudaSuccess) return DG_ECUDA;
+    if (L->stage(A, MODE_RHS, false, false, stream) != cudaSuccess) return DG_ECUDA;
     return DG_OK;
 }

@@ -56,6 +56,11 @@ class dg_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t), ("launches_per_stage", ctypes.c_int)]
 
 
+class dg_stabilisation(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("sponge_zd", ctypes.c_double), ("sponge_alpha", ctypes.c_double)]
+
+
 class dg_bubble(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("p_s", ctypes.c_double), ("qt0", ctypes.c_double),
                 ("H", ctypes.c_double), ("amplitude", ctypes.c_double),
@@ -88,6 +93,7 @@ SIGNATURES = [
     ("dg_rhs_noalloc", _I, [ctypes.POINTER(dg_config), _VP, _VP, _VP, _VP, _VP]),
     ("dg_rhs_adjoint", _I, [_VP, _VP, _VP, _VP]),
     ("dg_cloud_functional", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
+    ("dg_set_stabilisation", _I, [_VP, ctypes.POINTER(dg_stabilisation)]),
     ("dg_ensemble_create", _I, [ctypes.POINTER(_VP), _I, _VP, _VP, _VP]),
     ("dg_ensemble_member", _I, [_VP, _I, ctypes.POINTER(_VP)]),
     ("dg_ensemble_dofs", ctypes.c_longlong, [_VP]),
@@ -274,6 +280,24 @@ def dg_cloud_functional(ctx, U, dJdU):
     _check(lib().dg_cloud_functional(ctx, _addr(U), ctypes.byref(J), _addr(dJdU)),
            "dg_cloud_functional")
     return J.value
+
+
+def make_stabilisation(gamma=0.0, sigma=10.0, sponge_zd=0.0, sponge_alpha=0.0):
+    s = dg_stabilisation()
+    s.gamma, s.sigma, s.sponge_zd, s.sponge_alpha = gamma, sigma, sponge_zd, sponge_alpha
+    return s
+
+
+def dg_set_stabilisation(ctx, gamma=0.0, sigma=10.0, sponge_zd=0.0, sponge_alpha=0.0):
+    """Artificial diffusion (gamma, sigma) and sponge layer (z_D, alpha) of ctx."""
+    s = make_stabilisation(gamma, sigma, sponge_zd, sponge_alpha)
+    _check(lib().dg_set_stabilisation(ctx, ctypes.byref(s)), "dg_set_stabilisation")
+
+
+def dg_set_stabilisation_status(ctx, gamma=0.0, sigma=10.0, sponge_zd=0.0, sponge_alpha=0.0):
+    """Raw status of dg_set_stabilisation (for argument-validation tests)."""
+    s = make_stabilisation(gamma, sigma, sponge_zd, sponge_alpha)
+    return lib().dg_set_stabilisation(ctx, ctypes.byref(s))
 
 
 def dg_rhs_noalloc(cfg, base_node, base_face, U, dUdt, stream=None):
