@@ -241,7 +241,7 @@ int dg_reduce(dg_ctx *ctx, double out[DG_NREDUCE]);
  * the GPU (different streams, different host threads) race; serialise them.
  * Errors: DG_EINVAL for a bad argument, a non-float64 precision, or a mesh
  * whose scratch (derived fields + face traces) exceeds
- * DG_STATIC_SCRATCH_BYTES (e.g. about 1,900 elements of 3-D Q4 with rain);
+ * DG_STATIC_SCRATCH_BYTES (e.g. about 1,800 elements of 3-D Q4 with rain);
  * DG_ECUDA. */
 int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, const double *base_face,
                    const void *U, void *dUdt, void *cuda_stream);

@@ -522,7 +522,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     }
     if (st == DG_OK) st = alloc(c, (void **)&c->flags, sizeof(unsigned long long) * 2);
     if (st == DG_OK) st = alloc(c, (void **)&c->partials, sizeof(double) * kNRed * c->nred);
-    if (st == DG_OK) st = alloc(c, (void **)&c->rvs_tab, sizeof(double) * 2 * kTabN);
+    if (st == DG_OK) st = alloc(c, (void **)&c->rvs_tab, sizeof(double) * kTabStride * kTabN);
     if (st == DG_OK && M.pert_split)
         st = alloc(c, (void **)&c->bsplit, sizeof(float) * kBsN * M.nzlev_node);
     if (st == DG_OK && c->face_pass) st = alloc(c, &c->fbuf, (size_t)fofs * c->rsz);

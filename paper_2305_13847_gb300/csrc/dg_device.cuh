@@ -124,7 +124,7 @@ struct KArgs {
     const Real *bnode;     // base at node levels [4][nzlev_node]: rho_d, rho_m, E, p
     const Real *bface;     // base at face levels [4][nzlev_face]
     const double *bnode_d; // float64 copy for the split
-    const double *rvs_tab; // rho_vs table: [kTabN][2] = (rho_vs(T_i), 1/T_i)
+    const double *rvs_tab; // rho_vs Taylor table: [kTabN][kTabStride] (dg_math.cuh)
     const float *bsplit;   // DG_FP32_PERT: split of the base state per node level [kBsN][nzlev_node]
     Real *fbuf;            // face pass: Lax-Friedrichs flux along +e_j per face point (MeshData.fofs);
                            // with diffusion [2 NF]: flux, then S = alpha [[u]] / 2
@@ -239,26 +239,21 @@ __device__ __forceinline__ float rho_vs_f32(float T) {
                                 (float)kEsB * l2e * ((float)kInvTref - __frcp_rn(T)));
 }
 
-// float64 rho_vs(T) from the table (see dg_math.cuh); also returns 1/T.
+// float64 rho_vs(T) and d rho_vs / dT from the Taylor table (dg_math.cuh).
 // Outside the table range the closed form is evaluated directly.
-__device__ __forceinline__ double rho_vs_tab(double T, const double *__restrict__ tab, double &invT) {
+__device__ __forceinline__ double rho_vs_tab(double T, const double *__restrict__ tab, double &d1) {
     if (!(T >= kTabT0 && T <= kTabT1 - 1.0)) {
-        invT = 1.0 / T;
-        return rho_vs(T, invT);
+        const double invT = 1.0 / T;
+        const double v = rho_vs(T, invT);
+        d1 = v * invT * fma(kEsB, invT, kEsA - 1.0);
+        return v;
     }
-    const int i = __double2int_rn((T - kTabT0) * kTabInvStep);
-    const double2 ent = __ldg(reinterpret_cast<const double2 *>(tab) + i);
-    const double Ti = kTabT0 + (double)i * (1.0 / kTabInvStep);
-    const double s = (T - Ti) * ent.y;
-    // ln(1+s) and s/(1+s) to s^5 (truncation < 1e-20 for |s| <= 4.2e-4)
-    const double l1 = s * fma(s, fma(s, fma(s, fma(s, 0.2, -0.25), 1.0 / 3.0), -0.5), 1.0);
-    const double q = s * fma(s, fma(s, fma(s, fma(s, 1.0, -1.0), 1.0), -1.0), 1.0);
-    invT = fma(-ent.y, q, ent.y);                       // 1/T = (1/T_i)(1 - s/(1+s))
-    const double z = fma(kEsA - 1.0, l1, kEsB * ent.y * q);
-    // exp(z) for |z| <= 0.024 to z^7 (truncation < 3e-18)
-    const double ez = fma(z, fma(z, fma(z, fma(z, fma(z, fma(z, fma(z, 1.0 / 5040.0, 1.0 / 720.0),
-        1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0), 1.0);
-    return ent.x * ez;
+    const int i = __double2int_rn(fma(T, kTabInvStep, -kTabT0 * kTabInvStep));
+    const double d = T - fma((double)i, 1.0 / kTabInvStep, kTabT0);
+    const double2 *e = reinterpret_cast<const double2 *>(tab + (size_t)kTabStride * i);
+    const double2 c01 = __ldg(e), c23 = __ldg(e + 1), c45 = __ldg(e + 2), c67 = __ldg(e + 3);
+    d1 = fma(d, fma(d, c67.y, c67.x), c01.y);
+    return fma(d, fma(d, fma(d, fma(d, fma(d, c45.y, c45.x), c23.y), c23.x), c01.y), c01.x);
 }
 
 struct SplitResult {
@@ -290,10 +285,11 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     const double tu = kTref + (re - rm * kLprime) * recip(cu);
     const float rvs32 = rho_vs_f32((float)tu);
     bool sat;
-    double rvs_u = 0.0, invt;
+    double rvs_u = 0.0;
     const bool close = fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tu > 0.0);
     if (close || (NEED_DEFICIT && !(rm > (double)rvs32))) {
-        rvs_u = rho_vs_tab(tu, tab, invt);
+        double d1u;
+        rvs_u = rho_vs_tab(tu, tab, d1u);
         sat = rm > rvs_u;
     } else {
         sat = rm > (double)rvs32;
@@ -328,9 +324,8 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     // one float64 third-order step from T0
     {
         const double t0 = ((double)t > tu) ? (double)t : tu;
-        const double rvs = rho_vs_tab(t0, tab, invt);
-        const double phi1 = invt * fma(kEsB, invt, kEsA - 1.0);     // (ln rho_vs)'
-        const double drvs = rvs * phi1;
+        double drvs;
+        const double rvs = rho_vs_tab(t0, tab, drvs);
         const double heat = fma(kCvv - kCl, rvs, cdry);
         const double lat = fma(kCvv - kCl, t0 - kTref, kLprime);
         const double h = fma(heat, t0 - kTref, fma(rvs, kLprime, -re));
@@ -339,7 +334,8 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
         if (fabs(d) <= 3e-4) {
             // H'' = 2 (c_vv - c_l) rho_vs' + (c_vv - c_l)(T - T_ref) + L') rho_vs'',
             // rho_vs'' = rho_vs (phi1^2 + phi1'), phi1' = -(a-1)/T^2 - 2b/T^3
-            const float itf = (float)invt, p1f = (float)phi1, rvf = (float)rvs;
+            const float itf = __frcp_rn((float)t0), rvf = (float)rvs;
+            const float p1f = itf * (am1 + bb * itf);               // (ln rho_vs)
             const float d2rvs = rvf * (p1f * p1f - itf * itf * (am1 + 2.0f * bb * itf));
             const float d2h = 2.0f * clv * (rvf * p1f) + (float)lat * d2rvs;
             const float df = (float)d;
@@ -356,8 +352,7 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     double lo = tu, hi = INFINITY, rvs = 0.0, drvs = 0.0, step = INFINITY;
     bool done = false;
     for (int it = 0; it < kMaxNewton; ++it) {
-        rvs = rho_vs_tab(tn0, tab, invt);
-        drvs = rvs * invt * fma(kEsB, invt, kEsA - 1.0);
+        rvs = rho_vs_tab(tn0, tab, drvs);
         const double heat = fma(kCvv - kCl, rvs, cdry);
         const double h = fma(heat, tn0 - kTref, fma(rvs, kLprime, -re));
         const double dh = fma(fma(kCvv - kCl, tn0 - kTref, kLprime), drvs, heat);
@@ -472,8 +467,8 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
     const float rvs32 = rho_vs_f32(tuf);
     bool sat;
     if (fabsf(rmf - rvs32) <= 1e-5f * rmf || !(tuf > 0.0f)) {
-        double it_;
-        sat = rm > rho_vs_tab(tu, tab, it_);      // close call: decide in float64
+        double d1u;
+        sat = rm > rho_vs_tab(tu, tab, d1u);      // close call: decide in float64
     } else {
         sat = rmf > rvs32;
     }
@@ -506,9 +501,9 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
             }
         }
         // one float64 Newton correction of T with the float64 rho_vs
-        double invt;
+        double drvs64;
         const double T32 = (double)t;
-        const double rvs = rho_vs_tab(T32, tab, invt);
+        const double rvs = rho_vs_tab(T32, tab, drvs64);
         const double cdry = fma(kCvd, rd, kCl * (rm + rr));
         const double h = fma(fma(kCvv - kCl, rvs, cdry), T32 - kTref, fma(rvs, kLprime, -re));
         const float rvsf = (float)rvs, itf = __frcp_rn(t);
@@ -516,7 +511,7 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
         const float dh = cdf + clv * rvsf + (clv * (t - tref) + lp) * drvs;
         const float dT = (float)h / dh;
         o.T = T32 - (double)dT;
-        o.rv = fma(-(double)drvs, (double)dT, rvs);
+        o.rv = fma(-drvs64, (double)dT, rvs);
         Tf = (float)o.T;
         rvf = (float)o.rv;
         o.conv = conv && fabsf(dT) <= 1e-4f * t;
@@ -1700,13 +1695,32 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(KArgs<Real> A, d
     }
 }
 
-// rho_vs table entries (rho_vs(T_i), 1/T_i), T_i = 150 K + i/8 K, float64 closed form
+// Taylor-table entries of rho_vs (dg_math.cuh): at T_i = 150 K + i/128 K,
+// c_0 = rho_vs(T_i) from the float64 closed form; phi = (a-1) ln T - b/T has
+// the Taylor coefficients p_k = (-1)^(k+1) ((a-1)/(k T_i^k) + b/T_i^(k+1)),
+// and exp gives c_n = (1/n) sum_{k=1..n} k p_k c_{n-k}.
 static __global__ void k_fill_rvs_table(double *tab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kTabN) {
         const double T = kTabT0 + (double)i / kTabInvStep;
-        tab[2 * i] = rho_vs(T, 1.0 / T);
-        tab[2 * i + 1] = 1.0 / T;
+        const double it = 1.0 / T;
+        double p[6], c[6];
+        double itk = 1.0, sgn = 1.0;
+        for (int k = 1; k <= 5; ++k) {
+            itk *= it;
+            p[k] = sgn * ((kEsA - 1.0) * itk / k + kEsB * itk * it);
+            sgn = -sgn;
+        }
+        c[0] = rho_vs(T, it);
+        for (int n = 1; n <= 5; ++n) {
+            double acc = 0.0;
+            for (int k = 1; k <= n; ++k) acc += k * p[k] * c[n - k];
+            c[n] = acc / n;
+        }
+        double *e = tab + (size_t)kTabStride * i;
+        for (int n = 0; n < 6; ++n) e[n] = c[n];
+        e[6] = 2.0 * c[2];
+        e[7] = 3.0 * c[3];
     }
 }
 

@@ -1,12 +1,14 @@
 // Float64 elementary functions of the split and the rain terms, built to use
 // few float64 instructions (GB300 runs float64 at ~1/70 of the float32 rate).
 //
-// * rho_vs(T): table-driven evaluation in the manner of Tang's table-driven
-//   exponential (Tang 1989): rho_vs is tabulated in float64 on a 1/8 K grid
-//   (host, libm), and between grid points
-//       rho_vs(T) = rho_vs(T_i) exp((a-1) ln(1+s) + b s / (T_i (1+s))),
-//   s = (T - T_i)/T_i, |s| <= 4.2e-4, with the two logarithmic terms and the
-//   exponential evaluated by truncated Taylor series (truncation < 1e-17).
+// * rho_vs(T): table of Taylor coefficients.  On a 1/128 K grid T_i the
+//   table holds rho_vs(T_i + d) = sum_{n<=5} c_n d^n (and c_1, 2 c_2, 3 c_3
+//   for the derivative), so that one 64-byte entry and five fmas give
+//   rho_vs to float64 rounding for |d| <= 1/256 K (the first omitted term is
+//   below 1e-20 relative down to 150 K).  The coefficients follow from
+//   rho_vs = R_i exp(phi(T) - phi(T_i)), phi = (a-1) ln T - b/T (Eq. (2.6)),
+//   with the Taylor coefficients p_k of phi and the series recurrence of the
+//   exponential, c_n = (1/n) sum_{k=1..n} k p_k c_{n-k}.
 // * r^(-1/n) by the Newton iteration y <- y + y (1 - r y^n) / n, which needs no
 //   division, seeded from a float32 estimate (error ~1e-7, so two iterations
 //   reach float64 rounding).
@@ -19,10 +21,12 @@
 
 namespace dgm {
 
-// rho_vs table: T_i = kTabT0 + i / kTabInvStep, i = 0 .. kTabN - 1
+// rho_vs table: T_i = kTabT0 + i / kTabInvStep, i = 0 .. kTabN - 1, entries
+// of kTabStride doubles: c_0 .. c_5, 2 c_2, 3 c_3
 constexpr double kTabT0 = 150.0;
-constexpr double kTabInvStep = 8.0;
-constexpr int kTabN = 2001;          // 150 K .. 400 K
+constexpr double kTabInvStep = 128.0;
+constexpr int kTabN = 32001;         // 150 K .. 400 K
+constexpr int kTabStride = 8;
 constexpr double kTabT1 = kTabT0 + (kTabN - 1) / kTabInvStep;
 
 // 1/x: float32 seed, two Newton-Raphson steps r <- r + r (1 - x r)

@@ -120,7 +120,7 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     const size_t nodes = (size_t)ne * L->np;
     const size_t derived_bytes = round_up(sizeof(double) * L->nd * nodes);
     const size_t trace_bytes = round_up(sizeof(double) * 2 * g.dim * L->ntr * (size_t)ne * L->nfp1);
-    const size_t table_bytes = round_up(sizeof(double) * 2 * kTabN);
+    const size_t table_bytes = round_up(sizeof(double) * kTabStride * kTabN);
     const size_t flag_bytes = 2 * sizeof(unsigned long long);
     if (table_bytes + derived_bytes + trace_bytes + flag_bytes > (size_t)DG_STATIC_SCRATCH_BYTES)
         return DG_EINVAL;
