@@ -282,12 +282,11 @@ void release(dg_ctx *c) {
         if (p) cudaFree(p);
 }
 
-// face grid and the face-pass buffer layout for per_point values per face
-// point; returns the buffer's length in elements
+// face grid of the face pass; returns the length (in elements) of its
+// per-element buffer [ne][2D][per_point][NFP1]
 long long set_face_layout(dg_ctx *c, int per_point) {
     MeshData &M = c->M;
     const dg_config &g = c->cfg;
-    long long fofs = 0;
     for (int j = 0; j < 3; ++j) {
         M.nfn[j] = (j < g.dim) ? M.n[j] + (M.periodic[j] ? 0 : 1) : 1;
         M.nv[j] = M.nfn[j];
@@ -298,10 +297,8 @@ long long set_face_layout(dg_ctx *c, int per_point) {
         }
         M.nfaces[j] = (int)nfj;
         M.fblk[j] = (int)((nfj * c->nfp1 + kFaceThreads - 1) / kFaceThreads);
-        M.fofs[j] = fofs;
-        fofs += nfj * c->nfp1 * per_point;
     }
-    return fofs;
+    return c->ne * 2 * g.dim * per_point * c->nfp1;
 }
 
 int alloc(dg_ctx *c, void **p, size_t bytes) {
@@ -488,7 +485,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     // the face pass is the faster schedule for every precision on GB300
     // (measured: float64 -21 %, float32 forms -8 to -11 % per step)
     c->face_pass = g.faces != DG_FACES_INLINE;
-    const long long fofs = set_face_layout(c, nf);
+    const long long fbuf_len = set_face_layout(c, nf);
     c->ref64 = make_ref<double>(g.order);
     c->ref32 = make_ref<float>(g.order);
 
@@ -525,7 +522,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     if (st == DG_OK) st = alloc(c, (void **)&c->rvs_tab, sizeof(double) * kTabStride * kTabN);
     if (st == DG_OK && M.pert_split)
         st = alloc(c, (void **)&c->bsplit, sizeof(float) * kBsN * M.nzlev_node);
-    if (st == DG_OK && c->face_pass) st = alloc(c, &c->fbuf, (size_t)fofs * c->rsz);
+    if (st == DG_OK && c->face_pass) st = alloc(c, &c->fbuf, (size_t)fbuf_len * c->rsz);
     if (st == DG_OK && cudaMemsetAsync(c->flags, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = DG_ECUDA;
     if (st == DG_OK) {

@@ -82,13 +82,13 @@ struct MeshData {
     int pert_split;        // float32 state: 1 = split in perturbation variables (DG_FP32_PERT)
     // faces normal to e_j: a grid of nfn[j] (= n_j, + 1 with walls) x the other n,
     // nfaces[j] of them; face c lies between the elements at coordinates c - 1
-    // and c along e_j.  The face pass stores its fluxes per direction at
-    // fofs[j]: [NF][nfaces[j]][NFP1]; the face kernel covers direction j with
-    // fblk[j] CTAs.
+    // and c along e_j.  The face kernel covers direction j with fblk[j] CTAs
+    // and stores, per element, the outward flux of each of its faces
+    // (fbuf [ne][2D][NFP][NFP1], NFP = NF, or 2 NF with the diffusion's
+    // symmetry terms), so that a stage tile reads one contiguous block.
     int nfn[3];
     int nfaces[3];
     int fblk[3];
-    long long fofs[3];
     // artificial diffusion (Section 3.5): vertex grid of the continuous Q1
     // coefficient (n_j vertices per row if periodic, n_j + 1 with walls),
     // alpha_K = alpha_pre ||w||_{0,K} with alpha_pre = gamma 0.5 h^(1 - d/2),
@@ -126,8 +126,8 @@ struct KArgs {
     const double *bnode_d; // float64 copy for the split
     const double *rvs_tab; // rho_vs Taylor table: [kTabN][kTabStride] (dg_math.cuh)
     const float *bsplit;   // DG_FP32_PERT: split of the base state per node level [kBsN][nzlev_node]
-    Real *fbuf;            // face pass: Lax-Friedrichs flux along +e_j per face point (MeshData.fofs);
-                           // with diffusion [2 NF]: flux, then S = alpha [[u]] / 2
+    Real *fbuf;            // face pass: outward flux of every element face [ne][2D][NFP][NFP1];
+                           // with diffusion NFP = 2 NF: flux, then S = alpha [[u]] / 2
     Real *alphaK;          // diffusion: [2][ne] alpha_u, alpha_r per element (of the state produced)
     const Real *alphaV;    // diffusion: [2][nv] continuous coefficient at the vertices
     const Real *dtrace_in; // diffusion: d/dx_j traces of Uin  [2D][NF][ne][NFP1]
@@ -1004,9 +1004,9 @@ constexpr int MODE_RHS = 0;
 constexpr int MODE_STAGE = 1;
 
 // Shared memory of a stage tile: nodal fluxes s_fl [D][NF][EPB NP], node
-// values for the traces s_tr [NTR][EPB NP], face fluxes s_fh
-// [EPB][2D][NF][NFP1] (with diffusion also the symmetry terms s_fs of the
-// same shape), per-element indices and, with diffusion, the element's
+// values for the traces s_tr [NTR][EPB NP], outward face fluxes s_fh
+// [EPB][2D][NFP][NFP1] (with diffusion NFP = 2 NF: the fluxes, then the
+// symmetry terms), per-element indices and, with diffusion, the element's
 // vertex coefficients [EPB][2][2^D] and its alpha sums [EPB][2].  s_tr is
 // needed before the volume phase only when the float32 inline form
 // interpolates its own traces in the face phase, or with diffusion (the
@@ -1017,16 +1017,46 @@ __host__ __device__ constexpr bool tr_shares_fl() {
     return (PF || sizeof(Real) == sizeof(double)) && !DIFF;
 }
 
+// byte offset of s_fh (16-byte aligned for the asynchronous copy of the face fluxes)
+template <class S, typename Real, bool PF, bool DIFF>
+__host__ __device__ constexpr size_t stage_fh_offset() {
+    return ((sizeof(Real) * (tr_shares_fl<S, Real, PF, DIFF>()
+                                 ? ((size_t)S::D * S::NF > (size_t)S::NTR ? (size_t)S::D * S::NF
+                                                                          : (size_t)S::NTR)
+                                 : (size_t)S::D * S::NF + S::NTR) *
+             S::EPB * S::NP) + 15) / 16 * 16;
+}
+
 template <class S, typename Real, bool PF = false, bool DIFF = false>
 constexpr size_t stage_smem_bytes() {
-    constexpr size_t str = (size_t)S::EPB * S::NP;
-    constexpr size_t fl = (size_t)S::D * S::NF * str, tr = (size_t)S::NTR * str;
-    constexpr size_t fh = (size_t)S::EPB * S::NFACE * S::NF * S::NFP1;
-    return sizeof(Real) * ((tr_shares_fl<S, Real, PF, DIFF>() ? (fl > tr ? fl : tr) : fl + tr) +
-                           (DIFF ? 2 * fh : fh)) +
-           sizeof(int) * 16 * (size_t)S::EPB +  // per element: 2D neighbours, vertical index, 2D faces
+    constexpr size_t fh = (size_t)S::EPB * S::NFACE * (DIFF ? 2 * S::NF : S::NF) * S::NFP1;
+    return stage_fh_offset<S, Real, PF, DIFF>() + sizeof(Real) * fh +
+           sizeof(int) * 16 * (size_t)S::EPB +  // per element: 2D neighbours, vertical index
            (DIFF ? sizeof(Real) * (size_t)S::EPB * (2 * S::NCORNER + 2) : 0);
 }
+
+// Asynchronous global -> shared copy of n bytes in CHUNK-byte pieces (4, 8 or
+// 16; both addresses CHUNK-aligned), spread over the CTA's threads; completed
+// by cp_async_wait_all.
+template <int CHUNK>
+__device__ __forceinline__ void cp_async_block(void *dst, const void *src, size_t n) {
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(dst);
+    const char *g = static_cast<const char *>(src);
+    for (size_t i = (size_t)threadIdx.x * CHUNK; i < n; i += (size_t)blockDim.x * CHUNK) {
+        if (CHUNK == 16)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + (unsigned)i),
+                         "l"(g + i));
+        else if (CHUNK == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sbase + (unsigned)i),
+                         "l"(g + i));
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sbase + (unsigned)i),
+                         "l"(g + i));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // neighbour element across face (j, s) from the element's multi-index, or -1 (wall)
 template <int D>
@@ -1038,23 +1068,6 @@ __device__ __forceinline__ int neighbour_of(const MeshData &M, const int *im, in
     }
     const int i0 = j == 0 ? v : im[0], i1 = j == 1 ? v : im[1], i2 = j == 2 ? v : im[2];
     return i0 + M.n[0] * (i1 + M.n[1] * (D == 3 ? i2 : 0));
-}
-
-// index of face c (0 <= c < nfn[j]) normal to e_j through the element row of im
-template <int D>
-__device__ __forceinline__ int face_index(const MeshData &M, const int *im, int j, int c) {
-    const int i0 = j == 0 ? c : im[0], i1 = j == 1 ? c : im[1], i2 = j == 2 ? c : im[2];
-    const int n0 = j == 0 ? M.nfn[0] : M.n[0], n1 = j == 1 ? M.nfn[1] : M.n[1];
-    return i0 + n0 * (i1 + n1 * (D == 3 ? i2 : 0));
-}
-
-// face of element im on side s of direction j (the high face of the last
-// element of a periodic row is face 0)
-template <int D>
-__device__ __forceinline__ int element_face(const MeshData &M, const int *im, int j, int s) {
-    int c = im[j] + (s > 0 ? 1 : 0);
-    if (c >= M.nfn[j]) c -= M.n[j];
-    return face_index<D>(M, im, j, c);
 }
 
 template <class S, typename Real>
@@ -1196,8 +1209,13 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     flux_dir<S, Real>(Ph, J, Fh);
     const Real ll = wave_speed<S, J, Real>(Pl), lh = wave_speed<S, J, Real>(Ph);
     const Real lam = ll > lh ? ll : lh;
-    Real *out = A.fbuf + M.fofs[J] + (size_t)f * S::NFP1 + q;
-    const size_t fs = (size_t)M.nfaces[J] * S::NFP1;
+    // per element: [2D faces][NFP fields][NFP1 points]
+    constexpr int NFP = DIFF ? 2 * S::NF : S::NF;
+    constexpr size_t EB = (size_t)S::NFACE * NFP * S::NFP1;
+    Real *out_lo = e_lo >= 0 ? A.fbuf + (size_t)e_lo * EB + (size_t)(2 * J + 1) * NFP * S::NFP1 + q
+                             : nullptr;
+    Real *out_hi = e_hi >= 0 ? A.fbuf + (size_t)e_hi * EB + (size_t)(2 * J) * NFP * S::NFP1 + q
+                             : nullptr;
     const Real hl = Real(0.5) * lam;
     // one explicit fma, as in face_point: both schedules round identically
     Real G[S::NF];
@@ -1262,10 +1280,17 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
             }
         }
 #pragma unroll
-        for (int fld = 0; fld < S::NF; ++fld) out[(S::NF + fld) * fs] = Sx[fld];
+        for (int fld = 0; fld < S::NF; ++fld) {
+            if (out_lo) out_lo[(S::NF + fld) * S::NFP1] = Sx[fld];
+            if (out_hi) out_hi[(S::NF + fld) * S::NFP1] = Sx[fld];
+        }
     }
+    // outward fluxes: +G for the element below the face, -G for the one above
 #pragma unroll
-    for (int fld = 0; fld < S::NF; ++fld) out[fld * fs] = G[fld];
+    for (int fld = 0; fld < S::NF; ++fld) {
+        if (out_lo) out_lo[fld * S::NFP1] = G[fld];
+        if (out_hi) out_hi[fld * S::NFP1] = -G[fld];
+    }
 }
 
 constexpr int kFaceThreads = 128;
@@ -1303,12 +1328,12 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     constexpr bool SHARE = tr_shares_fl<S, Real, PF, DIFF>();
     constexpr int FLTR = SHARE ? (S::D * S::NF > S::NTR ? S::D * S::NF : S::NTR) * STR
                                : (S::D * S::NF + S::NTR) * STR;
-    constexpr int FH = S::EPB * S::NFACE * S::NF * S::NFP1;
+    constexpr int NFP = DIFF ? 2 * S::NF : S::NF;             // per face: fluxes [, symmetry terms]
+    constexpr int EB = S::NFACE * NFP * S::NFP1;              // face values of one element
     Real *s_fl = reinterpret_cast<Real *>(smem_raw);          // [D][NF][STR]
     Real *s_tr = SHARE ? s_fl : s_fl + S::D * S::NF * STR;    // [NTR][STR]
-    Real *s_fh = s_fl + FLTR;                                 // [EPB][NFACE][NF][NFP1]
-    Real *s_fs = s_fh + FH;                                   // DIFF: symmetry terms, same shape
-    int *s_info = reinterpret_cast<int *>(s_fh + (DIFF ? 2 * FH : FH));  // [EPB][16]
+    Real *s_fh = reinterpret_cast<Real *>(smem_raw + stage_fh_offset<S, Real, PF, DIFF>());  // [EPB][EB]
+    int *s_info = reinterpret_cast<int *>(s_fh + S::EPB * EB);                            // [EPB][16]
     Real *s_al = reinterpret_cast<Real *>(s_info + 16 * S::EPB);        // DIFF: [EPB][2][NCORNER]
     Real *s_red = s_al + S::EPB * 2 * S::NCORNER;                       // DIFF: [EPB][2]
     const MeshData &M = A.M;
@@ -1319,19 +1344,25 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     const int e = bidx * S::EPB + el;
     const bool valid = (t < STR) && (e < ne);
 
-    // per element: neighbours across the 2D faces (or, with the face pass,
-    // the faces themselves) and the vertical index
+    // face pass: the tile's outward face fluxes are one contiguous block of
+    // fbuf; copy it to shared memory while the nodal phases run
+    if (PF) {
+        constexpr size_t EBB = sizeof(Real) * (size_t)EB;
+        constexpr int CHUNK = EBB % 16 == 0 ? 16 : (EBB % 8 == 0 ? 8 : 4);
+        const int nel = min(S::EPB, ne - bidx * S::EPB);
+        cp_async_block<CHUNK>(s_fh, A.fbuf + (size_t)bidx * S::EPB * EB, EBB * (size_t)nel);
+    }
+
+    // per element: neighbours across the 2D faces (inline faces) and the
+    // vertical index
     if (t < S::EPB) {
         const int e0 = bidx * S::EPB + t;
         if (e0 < ne) {
             int im[3];
             elem_multi(M, e0, im[0], im[1], im[2]);
+            if (!PF) {
 #pragma unroll
-            for (int j = 0; j < S::D; ++j) {
-                if (PF) {
-                    s_info[t * 16 + 8 + 2 * j] = element_face<S::D>(M, im, j, -1);
-                    s_info[t * 16 + 8 + 2 * j + 1] = element_face<S::D>(M, im, j, 1);
-                } else {
+                for (int j = 0; j < S::D; ++j) {
                     s_info[t * 16 + 2 * j] = neighbour_of<S::D>(M, im, j, -1);
                     s_info[t * 16 + 2 * j + 1] = neighbour_of<S::D>(M, im, j, 1);
                 }
@@ -1442,22 +1473,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 
     // ---- phase 2b: Lax-Friedrichs flux at every face point of the CTA's elements
     if (PF) {
-        // outward fluxes from the face pass: +G on the high face, -G on the low
-        // face; s_fh[el][face][f][q] in the order of the item index
-        for (int item = t; item < S::EPB * S::NFACE * S::NF * S::NFP1; item += S::NT) {
-            const int el2 = item / (S::NFACE * S::NF * S::NFP1);
-            const int rem = item - el2 * (S::NFACE * S::NF * S::NFP1);
-            const int face = rem / (S::NF * S::NFP1);
-            const int r2 = rem - face * (S::NF * S::NFP1);
-            const int fld = r2 / S::NFP1;
-            const int q = r2 - fld * S::NFP1;
-            if (bidx * S::EPB + el2 >= ne) continue;
-            const int j = face >> 1;
-            const size_t fb = M.fofs[j] + ((size_t)fld * M.nfaces[j] + s_info[el2 * 16 + 8 + face]) * S::NFP1 + q;
-            const Real g = A.fbuf[fb];
-            s_fh[item] = (face & 1) ? g : -g;
-            if (DIFF) s_fs[item] = A.fbuf[fb + (size_t)S::NF * M.nfaces[j] * S::NFP1];
-        }
+        // outward fluxes of the face pass, copied asynchronously since the start
+        cp_async_wait_all();
     } else {
         for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
             const int el2 = item / (S::NFACE * S::NFP1);
@@ -1486,16 +1503,16 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             const int aj = digit<S::D, S::P1>(a, j);
             const int q = face_q<S::D, S::P1>(a, j);
             const Real sc = Real(M.two_over_h[j]);
-            const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * S::NF) * S::NFP1 + q;
-            const Real *fp = s_fh + ((el * S::NFACE + 2 * j + 1) * S::NF) * S::NFP1 + q;
+            const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * NFP) * S::NFP1 + q;
+            const Real *fp = s_fh + ((el * S::NFACE + 2 * j + 1) * NFP) * S::NFP1 + q;
             const Real cm = sc * ref.liftm[aj], cp = sc * ref.liftp[aj];
 #pragma unroll
             for (int f = 0; f < S::NF; ++f)
                 R[f] -= cp * fp[f * S::NFP1] + cm * fm[f * S::NFP1];
             if (DIFF) {
                 // symmetry term of Eq. (3.7): + (2/h_j)^2 l_a'(s)/w_a S on both faces
-                const Real *sm = s_fs + ((el * S::NFACE + 2 * j) * S::NF) * S::NFP1 + q;
-                const Real *sp = s_fs + ((el * S::NFACE + 2 * j + 1) * S::NF) * S::NFP1 + q;
+                const Real *sm = fm + S::NF * S::NFP1;
+                const Real *sp = fp + S::NF * S::NFP1;
                 const Real dm = sc * sc * ref.dliftm[aj], dp = sc * sc * ref.dliftp[aj];
 #pragma unroll
                 for (int f = 0; f < S::NF; ++f) R[f] += dp * sp[f * S::NFP1] + dm * sm[f * S::NFP1];
