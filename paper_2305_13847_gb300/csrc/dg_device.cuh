@@ -763,11 +763,53 @@ __device__ __forceinline__ Real interp_face(const Real *v, const Real *ls, int j
 // ---------------------------------------------------------------------------
 // k_prepare: split at every node and traces of every face
 // ---------------------------------------------------------------------------
-// DIFF: also the traces of d/dx_j U on the faces normal to e_j,
-// (2/h_j) sum_i l_i'(s) U(line node i), for the interior-penalty terms
-template <class S, typename Real, bool DIFF = false>
-__device__ __forceinline__ void write_traces(const KArgs<Real> &A, const RefData<Real> &ref,
-                                             const Real *s_tr, Real *trace_out, int bidx) {
+// Traces on the two faces normal to e_J through face point q of element el:
+// the k+1 node values of the line are read once and interpolated to both
+// ends (same fma chain as interp_face).  DIFF: also the traces of
+// d/dx_J U, (2/h_J) sum_i l_i'(+-1) U(line node i), for the interior-penalty
+// terms.
+template <class S, typename Real, bool DIFF, int J>
+__device__ __forceinline__ void write_line(const KArgs<Real> &A, const RefData<Real> &ref,
+                                           const Real *s_tr, Real *trace_out, int el, int e, int q) {
+    constexpr int STR = S::EPB * S::NP;
+    const int ne = A.M.ne;
+    const int b0 = el * S::NP + line_node<S::D, S::P1>(J, q, 0);
+    constexpr int st = J == 0 ? 1 : (J == 1 ? S::P1 : S::P1 * S::P1);
+    Real *om = trace_out + ((size_t)(2 * J) * S::NTR * ne + e) * S::NFP1 + q;
+    Real *op = trace_out + ((size_t)(2 * J + 1) * S::NTR * ne + e) * S::NFP1 + q;
+    const size_t fs = (size_t)ne * S::NFP1;
+#pragma unroll
+    for (int fld = 0; fld < S::NTR; ++fld) {
+        Real v[S::P1];
+#pragma unroll
+        for (int i = 0; i < S::P1; ++i) v[i] = s_tr[fld * STR + b0 + i * st];
+        Real am = Real(0), ap = Real(0);
+#pragma unroll
+        for (int i = 0; i < S::P1; ++i) {
+            am = fma(ref.lm[i], v[i], am);
+            ap = fma(ref.lp[i], v[i], ap);
+        }
+        om[fld * fs] = am;
+        op[fld * fs] = ap;
+        if (DIFF && fld < S::NF) {
+            Real dm = Real(0), dp = Real(0);
+#pragma unroll
+            for (int i = 0; i < S::P1; ++i) {
+                dm = fma(ref.dlm[i], v[i], dm);
+                dp = fma(ref.dlp[i], v[i], dp);
+            }
+            const Real sc = Real(A.M.two_over_h[J]);
+            A.dtrace_out[(((size_t)(2 * J) * S::NF + fld) * ne + e) * S::NFP1 + q] = sc * dm;
+            A.dtrace_out[(((size_t)(2 * J + 1) * S::NF + fld) * ne + e) * S::NFP1 + q] = sc * dp;
+        }
+    }
+}
+
+// One thread per face point: the float64 form, whose FP64 pipe is the bound,
+// runs faster with the trace work spread over more threads (measured).
+template <class S, typename Real, bool DIFF>
+__device__ __forceinline__ void write_traces_points(const KArgs<Real> &A, const RefData<Real> &ref,
+                                                    const Real *s_tr, Real *trace_out, int bidx) {
     const int ne = A.M.ne;
     for (int item = threadIdx.x; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
         const int el = item / (S::NFACE * S::NFP1);
@@ -793,6 +835,35 @@ __device__ __forceinline__ void write_traces(const KArgs<Real> &A, const RefData
                 A.dtrace_out[(((size_t)face * S::NF + fld) * ne + e) * S::NFP1 + q] =
                     sc * interp_face<S, Real>(v, dls, j, q);
             }
+        }
+    }
+}
+
+// Traces of the tile's state on all 2D faces.  float32: one thread per line
+// (both ends; the float32 tile is bound by instruction issue, and this halves
+// the shared-memory reads and index work, measured -22 % per step);
+// float64: one thread per face point (write_traces_points).
+template <class S, typename Real, bool DIFF = false>
+__device__ __forceinline__ void write_traces(const KArgs<Real> &A, const RefData<Real> &ref,
+                                             const Real *s_tr, Real *trace_out, int bidx) {
+    if (sizeof(Real) == sizeof(double)) {
+        write_traces_points<S, Real, DIFF>(A, ref, s_tr, trace_out, bidx);
+        return;
+    }
+    const int ne = A.M.ne;
+    for (int item = threadIdx.x; item < S::EPB * S::D * S::NFP1; item += S::NT) {
+        const int el = item / (S::D * S::NFP1);
+        const int rem = item - el * (S::D * S::NFP1);
+        const int j = rem / S::NFP1;
+        const int q = rem - j * S::NFP1;
+        const int e = bidx * S::EPB + el;
+        if (e >= ne) continue;
+        switch (j) {
+            case 0: write_line<S, Real, DIFF, 0>(A, ref, s_tr, trace_out, el, e, q); break;
+            case 1: write_line<S, Real, DIFF, 1>(A, ref, s_tr, trace_out, el, e, q); break;
+            default:
+                write_line<S, Real, DIFF, (S::D == 3 ? 2 : 1)>(A, ref, s_tr, trace_out, el, e, q);
+                break;
         }
     }
 }
