@@ -282,6 +282,19 @@ void release(dg_ctx *c) {
         if (p) cudaFree(p);
 }
 
+// float32 copies of the mesh constants (used by the float32 forms)
+void mesh_float_copies(MeshData &M) {
+    for (int j = 0; j < 3; ++j) {
+        M.two_over_h_f[j] = (float)M.two_over_h[j];
+        M.sigma_pen_f[j] = (float)M.sigma_pen[j];
+    }
+    M.g_f = (float)M.g;
+    M.kvr_f = (float)M.kvr;
+    M.rho_w_f = (float)M.rho_w;
+    M.jac_f = (float)M.jac;
+    M.alpha_pre_f = (float)M.alpha_pre;
+}
+
 // face grid of the face pass; returns the length (in elements) of its
 // per-element buffer [ne][2D][per_point][NFP1]
 long long set_face_layout(dg_ctx *c, int per_point) {
@@ -486,6 +499,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     // (measured: float64 -21 %, float32 forms -8 to -11 % per step)
     c->face_pass = g.faces != DG_FACES_INLINE;
     const long long fbuf_len = set_face_layout(c, nf);
+    mesh_float_copies(M);
     c->ref64 = make_ref<double>(g.order);
     c->ref32 = make_ref<float>(g.order);
 
@@ -913,6 +927,7 @@ int dg_set_stabilisation(dg_ctx *c, const dg_stabilisation *sp) {
         M.alpha_pre = p.gamma * 0.5 * std::pow(h, 1.0 - 0.5 * g.dim);
         for (int j = 0; j < 3; ++j)
             M.sigma_pen[j] = j < g.dim ? p.sigma * g.order * g.order / M.h[j] : 0.0;
+        mesh_float_copies(M);
     }
     if (c->alphaK) set_face_layout(c, diff ? 2 * c->nf : c->nf);
     // sponge profile delta_R at the node levels (Section 3.6)

@@ -96,7 +96,18 @@ struct MeshData {
     int nv[3];
     double alpha_pre;
     double sigma_pen[3];
+    // float32 copies of the constants the float32 forms use in their hot
+    // loops (a float64 -> float32 conversion occupies the FP64 pipe)
+    float two_over_h_f[3];
+    float g_f, kvr_f, rho_w_f, jac_f, alpha_pre_f;
+    float sigma_pen_f[3];
 };
+
+// a mesh constant in the storage type: the float64 value, or its float32 copy
+template <typename Real>
+__device__ __forceinline__ Real mconst(double d, float f) {
+    return sizeof(Real) == sizeof(double) ? (Real)d : (Real)f;
+}
 
 template <typename Real>
 struct RefData {
@@ -388,9 +399,9 @@ __device__ __forceinline__ double rain_velocity(double rr, double rm, const Mesh
 
 __device__ __forceinline__ float rain_velocity(float rr, float rm, const MeshData &M) {
     const float rrp = rr > 0.0f ? rr : 0.0f;
-    const float rw = M.rho_w > 0.0 ? (float)M.rho_w : rm + rr;
+    const float rw = M.rho_w_f > 0.0f ? M.rho_w_f : rm + rr;
     if (!(rrp > 0.0f) || !(rw > 0.0f)) return 0.0f;
-    return (float)M.kvr * exp2f(0.125f * __log2f(rrp * __frcp_rn(rw)));
+    return M.kvr_f * exp2f(0.125f * __log2f(rrp * __frcp_rn(rw)));
 }
 
 // Per-node split plus the node-local quantities the next operator needs.
@@ -798,7 +809,7 @@ __device__ __forceinline__ void write_line(const KArgs<Real> &A, const RefData<R
                 dm = fma(ref.dlm[i], v[i], dm);
                 dp = fma(ref.dlp[i], v[i], dp);
             }
-            const Real sc = Real(A.M.two_over_h[J]);
+            const Real sc = mconst<Real>(A.M.two_over_h[J], A.M.two_over_h_f[J]);
             A.dtrace_out[(((size_t)(2 * J) * S::NF + fld) * ne + e) * S::NFP1 + q] = sc * dm;
             A.dtrace_out[(((size_t)(2 * J + 1) * S::NF + fld) * ne + e) * S::NFP1 + q] = sc * dp;
         }
@@ -828,7 +839,7 @@ __device__ __forceinline__ void write_traces_points(const KArgs<Real> &A, const 
         }
         if (DIFF) {
             const Real *dls = (face & 1) ? ref.dlp : ref.dlm;
-            const Real sc = Real(A.M.two_over_h[j]);
+            const Real sc = mconst<Real>(A.M.two_over_h[j], A.M.two_over_h_f[j]);
 #pragma unroll
             for (int fld = 0; fld < S::NF; ++fld) {
                 const Real *v = s_tr + (size_t)fld * S::EPB * S::NP + el * S::NP;
@@ -880,7 +891,7 @@ __device__ __forceinline__ void alpha_accumulate(const KArgs<Real> &A, const Ref
     const int nl = A.M.nzlev_node;
     const Real rho = (A.bnode[lev] + u[0]) + (A.bnode[nl + lev] + u[1]) + (S::RAIN ? u[2] : Real(0));
     const Real inv = recip(rho);
-    Real wq = Real(A.M.jac);
+    Real wq = mconst<Real>(A.M.jac, A.M.jac_f);
 #pragma unroll
     for (int j = 0; j < S::D; ++j) wq *= ref.w[digit<S::D, S::P1>(a, j)];
     Real w2u = Real(0), w2r = Real(0);
@@ -902,7 +913,7 @@ __device__ __forceinline__ void alpha_store(const KArgs<Real> &A, const Real *s_
     if (t < S::EPB) {
         const int e = bidx * S::EPB + t;
         if (e < A.M.ne) {
-            const Real pre = Real(A.M.alpha_pre);
+            const Real pre = mconst<Real>(A.M.alpha_pre, A.M.alpha_pre_f);
             A.alphaK[e] = pre * sqrt(s_red[2 * t]);
             A.alphaK[A.M.ne + e] = S::RAIN ? pre * sqrt(s_red[2 * t + 1]) : Real(0);
         }
@@ -1338,7 +1349,7 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
                 au = fma(wgt, A.alphaV[flat], au);
                 ar = fma(wgt, A.alphaV[nvt + flat], ar);
             }
-            const Real sig = Real(M.sigma_pen[J]);
+            const Real sig = mconst<Real>(M.sigma_pen[J], M.sigma_pen_f[J]);
 #pragma unroll
             for (int fld = 0; fld < S::NF; ++fld) {
                 const Real al = (S::RAIN && fld == 2) ? ar : au;
@@ -1488,7 +1499,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             R[1] = gm;
             R[2] = -gm;
         }
-        const Real g = Real(M.g);
+        const Real g = mconst<Real>(M.g, M.g_f);
         R[S::IM + S::VERT] = -g * (u[0] + u[1] + (S::RAIN ? u[2] : Real(0)));
         R[S::IE] = -g * u[S::IM + S::VERT];
     }
@@ -1508,7 +1519,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 const int aj = digit<S::D, S::P1>(a, j);
                 const int st = stride_of<S::P1>(j);
                 const int b0 = el * S::NP + a - aj * st;
-                const Real sc = Real(M.two_over_h[j]);
+                const Real sc = mconst<Real>(M.two_over_h[j], M.two_over_h_f[j]);
 #pragma unroll
                 for (int f = 0; f < S::NF; ++f) {
                     const Real *v = s_tr + f * STR + b0;
@@ -1530,7 +1541,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             const int aj = digit<S::D, S::P1>(a, j);
             const int st = stride_of<S::P1>(j);
             const int b0 = el * S::NP + a - aj * st;
-            const Real sc = Real(M.two_over_h[j]);
+            const Real sc = mconst<Real>(M.two_over_h[j], M.two_over_h_f[j]);
 #pragma unroll
             for (int f = 0; f < S::NF; ++f) {
                 const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
@@ -1573,7 +1584,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         for (int j = 0; j < S::D; ++j) {
             const int aj = digit<S::D, S::P1>(a, j);
             const int q = face_q<S::D, S::P1>(a, j);
-            const Real sc = Real(M.two_over_h[j]);
+            const Real sc = mconst<Real>(M.two_over_h[j], M.two_over_h_f[j]);
             const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * NFP) * S::NFP1 + q;
             const Real *fp = s_fh + ((el * S::NFACE + 2 * j + 1) * NFP) * S::NFP1 + q;
             const Real cm = sc * ref.liftm[aj], cp = sc * ref.liftp[aj];
