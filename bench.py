@@ -22,7 +22,8 @@ import time
 
 # The reference arm and the cpu baseline time the oracle single-threaded:
 # pin the BLAS thread pools before numpy loads.
-if "reference" in sys.argv and os.environ.get("DG_ORACLE_THREADS") != "1":
+if (__name__ == "__main__" and "reference" in sys.argv
+        and os.environ.get("DG_ORACLE_THREADS") != "1"):
     os.execve(sys.executable, [sys.executable] + sys.argv,
               dict(os.environ, DG_ORACLE_THREADS="1", OMP_NUM_THREADS="1",
                    OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1"))
