@@ -267,6 +267,21 @@ __device__ __forceinline__ double rho_vs_tab(double T, const double *__restrict_
     return fma(d, fma(d, fma(d, fma(d, fma(d, c45.y, c45.x), c23.y), c23.x), c01.y), c01.x);
 }
 
+// The same at a float32 temperature t (T = (double)t exactly): the index,
+// the range check and the offset d = t - T_i are exact in float32 (T_i =
+// 150 + i/128 has 16 significant bits, and t - T_i is exact by Sterbenz's
+// lemma), so only the two polynomials run in float64.
+__device__ __forceinline__ double rho_vs_tab(float t, const double *__restrict__ tab, double &d1) {
+    if (!(t >= (float)kTabT0 && t <= (float)(kTabT1 - 1.0))) return rho_vs_tab((double)t, tab, d1);
+    const int i = __float2int_rn((t - (float)kTabT0) * (float)kTabInvStep);
+    const float Ti = (float)kTabT0 + (float)i * (float)(1.0 / kTabInvStep);
+    const double d = (double)(t - Ti);
+    const double2 *e = reinterpret_cast<const double2 *>(tab + (size_t)kTabStride * i);
+    const double2 c01 = __ldg(e), c23 = __ldg(e + 1), c45 = __ldg(e + 2), c67 = __ldg(e + 3);
+    d1 = fma(d, fma(d, c67.y, c67.x), c01.y);
+    return fma(d, fma(d, fma(d, fma(d, fma(d, c45.y, c45.x), c23.y), c23.x), c01.y), c01.x);
+}
+
 struct SplitResult {
     double T, rv, deficit;  // deficit = rho_vs(T) - rho_v (0 at saturation)
     bool converged;
@@ -334,9 +349,10 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     r.deficit = 0.0;
     // one float64 third-order step from T0
     {
-        const double t0 = ((double)t > tu) ? (double)t : tu;
+        const bool tf = (double)t > tu;
+        const double t0 = tf ? (double)t : tu;
         double drvs;
-        const double rvs = rho_vs_tab(t0, tab, drvs);
+        const double rvs = tf ? rho_vs_tab(t, tab, drvs) : rho_vs_tab(t0, tab, drvs);
         const double heat = fma(kCvv - kCl, rvs, cdry);
         const double lat = fma(kCvv - kCl, t0 - kTref, kLprime);
         const double h = fma(heat, t0 - kTref, fma(rvs, kLprime, -re));
@@ -514,7 +530,7 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
         // one float64 Newton correction of T with the float64 rho_vs
         double drvs64;
         const double T32 = (double)t;
-        const double rvs = rho_vs_tab(T32, tab, drvs64);
+        const double rvs = rho_vs_tab(t, tab, drvs64);
         const double cdry = fma(kCvd, rd, kCl * (rm + rr));
         const double h = fma(fma(kCvv - kCl, rvs, cdry), T32 - kTref, fma(rvs, kLprime, -re));
         const float rvsf = (float)rvs, itf = __frcp_rn(t);
