@@ -341,7 +341,7 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
             const float heat = cdf + clv * rvs;
             const float h = heat * (t - tref) + rvs * lp - ref;
             const float dh = heat + (clv * (t - tref) + lp) * drvs;
-            const float dt = h / dh;
+            const float dt = h * __frcp_rn(dh);
             t -= dt;
             if (fabsf(dt) <= 2e-6f * t) break;
         }
@@ -520,7 +520,7 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
             const float heat = cdf + clv * rvs;
             const float h = heat * (t - tref) + rvs * lp - ref;
             const float dh = heat + (clv * (t - tref) + lp) * drvs;
-            const float dt = h / dh;
+            const float dt = h * __frcp_rn(dh);
             t -= dt;
             if (fabsf(dt) <= 1e-6f * t) {
                 conv = true;
@@ -585,14 +585,16 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
 // The float32-rounded base split (T_bar, rho_v_bar) is taken as the exact
 // reference; the float64 residuals of its identities are tabulated, so the
 // rounding of the reference enters no result.
-constexpr int kBsN = 10;  // 0 T_bar, 1 rho_v_bar, 2 R_bar = rho_vs(T_bar), 3 rho_m_bar - R_bar,
+constexpr int kBsN = 12;  // 0 T_bar, 1 rho_v_bar, 2 R_bar = rho_vs(T_bar), 3 rho_m_bar - R_bar,
                           // 4 R_bar - rho_v_bar, 5 p residual (rho_d R_d + rho_v R_v) T - p, 6 C_bar,
                           // 7 T_bar - T_ref, 8 energy residual E_bar - C_bar (T_bar - T_ref) - rho_v_bar L',
-                          // 9 rho_m_bar - rho_v_bar
+                          // 9 rho_m_bar - rho_v_bar, 10 1/T_bar, 11 b/T_bar
 
-__device__ __forceinline__ float phi_of(float tau, float Tb) {
-    const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
-    return am1 * log1pf(tau / Tb) + (bb / Tb) * (tau / (Tb + tau));
+// phi(tau) = (a-1) log1p(tau/T_bar) + (b/T_bar) tau/T with T = T_bar + tau;
+// iTb = 1/T_bar and bTb = b/T_bar from the table, iT = 1/T (no divisions)
+__device__ __forceinline__ float phi_of(float tau, float iTb, float bTb, float iT) {
+    const float am1 = (float)(kEsA - 1.0);
+    return am1 * log1pf(tau * iTb) + bTb * (tau * iT);
 }
 
 template <bool RAIN>
@@ -602,21 +604,21 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
     NodeDerived o;
     const float Tb = bs[0], rvb = bs[nl], Rb = bs[2 * nl], Qb = bs[3 * nl], Db = bs[4 * nl];
     const float pres = bs[5 * nl], Cb = bs[6 * nl], dTb = bs[7 * nl], eres = bs[8 * nl];
-    const float cqb = bs[9 * nl];
+    const float cqb = bs[9 * nl], iTb = bs[10 * nl], bTb = bs[11 * nl];
     const float cvd = (float)kCvd, cvv = (float)kCvv, cl = (float)kCl, lp = (float)kLprime;
     const float rdp = u[0], rmp = u[1], rrp = RAIN ? u[2] : 0.0f;
     const float rho = brd + brm + rdp + rmp + rrp;
     float msq = 0.0f;
     for (int j = 0; j < d; ++j) msq = fmaf(u[im + j], u[im + j], msq);
     // rho e - (base identity) = E' - |m|^2/(2 rho) + energy residual
-    const float de = (u[ie] - 0.5f * msq / rho) + eres;
+    const float de = (u[ie] - 0.5f * msq * __frcp_rn(rho)) + eres;
     const float c0 = cvd * rdp + cl * (rmp + rrp);            // C - C_bar without the nu part
     // unsaturated candidate: rho_v = rho_m, nu_u = rho_m' + (rho_m_bar - rho_v_bar)
     const float nu_u = rmp + cqb;
     const float Cu = Cb + c0 + (cvv - cl) * nu_u;
-    const float tau_u = (de - (c0 + (cvv - cl) * nu_u) * dTb - nu_u * lp) / Cu;
+    const float tau_u = (de - (c0 + (cvv - cl) * nu_u) * dTb - nu_u * lp) * __frcp_rn(Cu);
     // saturated iff rho_m > rho_vs(T_u) <=> rho_m' + Q_bar - R_bar expm1(phi(tau_u)) > 0
-    const float em_u = expm1f(phi_of(tau_u, Tb));
+    const float em_u = expm1f(phi_of(tau_u, iTb, bTb, __frcp_rn(Tb + tau_u)));
     const bool sat = rmp + Qb - Rb * em_u > 0.0f;
     float tau, nu, deficit = 0.0f;
     bool conv = true;
@@ -631,13 +633,14 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
         float prev = 3.0e38f;
         for (int it = 0; it < 40; ++it) {
             const float T = Tb + tau;
-            const float em = expm1f(phi_of(tau, Tb));
+            const float iT = __frcp_rn(T);
+            const float em = expm1f(phi_of(tau, iTb, bTb, iT));
             const float nus = Db + Rb * em;                     // rho_vs(T) - rho_v_bar
-            const float dnu = Rb * (1.0f + em) * (am1 / T + bb / (T * T));
+            const float dnu = Rb * (1.0f + em) * iT * (am1 + bb * iT);
             const float C = Cb + c0 + (cvv - cl) * nus;
             const float h = C * tau + (c0 + (cvv - cl) * nus) * dTb + nus * lp - de;
             const float dh = C + ((cvv - cl) * (tau + dTb) + lp) * dnu;
-            const float step = h / dh;
+            const float step = h * __frcp_rn(dh);
             tau -= step;
             // done once the step is at rounding level (2 ulp of T, or 2e-6 K),
             // or once it stops shrinking below 1e-4 K (float32 rounding of h
@@ -649,7 +652,7 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
             }
             prev = as;
         }
-        nu = Db + Rb * expm1f(phi_of(tau, Tb));
+        nu = Db + Rb * expm1f(phi_of(tau, iTb, bTb, __frcp_rn(Tb + tau)));
     }
     const float T = Tb + tau;
     o.Tf = T;
@@ -698,6 +701,8 @@ static __global__ void k_base_split(const double *bnode, int nl, float *bs, cons
     bs[5 * nl + l] = (float)((rd * kRd + rv * kRv) * T - p);
     bs[6 * nl + l] = (float)C;
     bs[7 * nl + l] = (float)(T - kTref);
+    bs[10 * nl + l] = (float)(1.0 / T);
+    bs[11 * nl + l] = (float)(kEsB / T);
     bs[8 * nl + l] = (float)(E - C * (T - kTref) - rv * kLprime);
     bs[9 * nl + l] = (float)(rm - rv);
 }
@@ -1442,6 +1447,22 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     const int e = bidx * S::EPB + el;
     const bool valid = (t < STR) && (e < ne);
 
+    // the node's state and derived fields: loads issued first, so that their
+    // latency overlaps the set-up below
+    Real u[S::NF], R[S::NF], dT = Real(0), drv = Real(0), dpp = Real(0), dgm = Real(0), dvr = Real(0);
+    if (valid) {
+        const size_t gi = (size_t)e * S::NP + a;
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
+        dT = A.derived[gi];
+        drv = A.derived[nodes + gi];
+        dpp = A.derived[2 * nodes + gi];
+        if (S::RAIN) {
+            dgm = A.derived[3 * nodes + gi];
+            dvr = A.derived[4 * nodes + gi];
+        }
+    }
+
     // face pass: the tile's outward face fluxes are one contiguous block of
     // fbuf; copy it to shared memory while the nodal phases run
     if (PF) {
@@ -1475,19 +1496,15 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     }
     __syncthreads();
 
-    Real u[S::NF], R[S::NF];
     // ---- phase 1: nodal fluxes, sources, node values for own traces
     if (valid) {
-        const size_t gi = (size_t)e * S::NP + a;
-#pragma unroll
-        for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
-        const Real T = A.derived[gi], rv = A.derived[nodes + gi], pp = A.derived[2 * nodes + gi];
+        const Real T = dT, rv = drv, pp = dpp;
         const int lev = s_info[el * 16 + 6] * S::P1 + digit<S::D, S::P1>(a, S::VERT);
         Real brd, brm, bE, bp;
         load_base<S, Real>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
         Prim<S::D, S::RAIN, Real> P;
         make_prim<S, Real>(P, u, brd, brm, bE, bp, T, rv, pp);
-        if (S::RAIN) P.vr = A.derived[4 * nodes + gi];
+        if (S::RAIN) P.vr = dvr;
 #pragma unroll
         for (int j = 0; j < S::D; ++j) {
             Real F[S::NF];
@@ -1511,9 +1528,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         }
         // sources G (Eq. (2.11)): microphysics and gravity
         if (S::RAIN) {
-            const Real gm = A.derived[3 * nodes + gi];
-            R[1] = gm;
-            R[2] = -gm;
+            R[1] = dgm;
+            R[2] = -dgm;
         }
         const Real g = mconst<Real>(M.g, M.g_f);
         R[S::IM + S::VERT] = -g * (u[0] + u[1] + (S::RAIN ? u[2] : Real(0)));
