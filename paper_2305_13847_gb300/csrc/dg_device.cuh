@@ -627,7 +627,11 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
         nu = nu_u;
         deficit = (Db + Rb * em_u) - nu_u;                     // rho_vs(T) - rho_v
     } else {
-        tau = tau_u;
+        // start at the base temperature unless T_u is warmer: where the base
+        // state is cloudy T_u lies ~ rho_c L'/C (a few K) below the root,
+        // while the root is usually within a fraction of a K of T_bar.  H is
+        // increasing and convex, so Newton converges from either side.
+        tau = tau_u > 0.0f ? tau_u : 0.0f;
         conv = false;
         const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
         float prev = 3.0e38f;
