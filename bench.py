@@ -235,9 +235,9 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto
 # named below; they scale with the node count for the same dimension, order
 # and form.  None (-> traffic null) for any other configuration.
 PROFILED_TRAFFIC = {
-    (3, 4, "fp64"): 481.6,        # 32x32x32 Q4 capture: k_face 147.8 + k_stage 333.8
-    (3, 3, "fp32_bulk"): 281.1,   # 64x64x32 Q3 capture: k_face 93.3 + k_stage 187.8
-    (3, 3, "fp32_pert"): 281.2,   # 64x64x32 Q3 capture: k_face 93.4 + k_stage 187.8
+    (3, 4, "fp64"): 481.4,        # 32x32x32 Q4 capture: k_face 147.7 + k_stage 333.7
+    (3, 3, "fp32_bulk"): 281.2,   # 64x64x32 Q3 capture: k_face 93.3 + k_stage 187.9
+    (3, 3, "fp32_pert"): 281.1,   # 64x64x32 Q3 capture: k_face 93.4 + k_stage 187.7
 }
 
 
@@ -346,7 +346,7 @@ def run_gb300(args):
     if args.precision == "fp64":
         # the float64 form is bound by the FP64 pipe, not by HBM: ncu's pipe
         # utilisation of the two kernels of a stage (32x32x32 Q4 capture)
-        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.878, "k_face": 0.850,
+        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.879, "k_face": 0.850,
                              "source": "ncu sm__inst_executed_pipe_fp64, 32x32x32 Q4 capture"}
     dm.dg_free(ctx)
     del host
