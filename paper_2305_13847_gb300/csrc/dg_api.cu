@@ -502,6 +502,16 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     mesh_float_copies(M);
     c->ref64 = make_ref<double>(g.order);
     c->ref32 = make_ref<float>(g.order);
+    // the volume derivative tables pre-scaled by 2/h_j of this mesh
+    for (int j = 0; j < 3; ++j)
+        for (int a = 0; a < 6; ++a)
+            for (int i = 0; i < 6; ++i) {
+                const double v = M.two_over_h[j] * c->ref64.dhat[a][i];
+                c->ref64.dhat_s[j][a][i] = v;
+                c->ref32.dhat_s[j][a][i] = (float)v;
+            }
+    c->ref64.scaled = 1;
+    c->ref32.scaled = 1;
 
     // z-levels
     c->z_node.resize(M.nzlev_node);

@@ -120,6 +120,11 @@ struct RefData {
     Real dmat[6][6];
     Real dlm[6], dlp[6];
     Real dliftm[6], dliftp[6];
+    // scaled != 0: dhat_s[j] = (2/h_j) dhat of this mesh, so that the volume
+    // contraction needs no separate scaling (read from the mesh's own kernel
+    // arguments, also where the other tables are shared between meshes)
+    Real dhat_s[3][6][6];
+    int scaled;
 };
 
 template <typename Real>
@@ -1571,7 +1576,22 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     }
 
     // ---- phase 2a: volume term, sum factorised: R_a += (2/h_j) sum_i dhat[a_j][i] F_j(i)
-    if (valid) {
+    if (valid && A.ref.scaled) {
+#pragma unroll
+        for (int j = 0; j < S::D; ++j) {
+            const int aj = digit<S::D, S::P1>(a, j);
+            const int st = stride_of<S::P1>(j);
+            const int b0 = el * S::NP + a - aj * st;
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) {
+                const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
+                Real acc = R[f];
+#pragma unroll
+                for (int i = 0; i < S::P1; ++i) acc = fma(A.ref.dhat_s[j][aj][i], fl[i * st], acc);
+                R[f] = acc;
+            }
+        }
+    } else if (valid) {
 #pragma unroll
         for (int j = 0; j < S::D; ++j) {
             const int aj = digit<S::D, S::P1>(a, j);
