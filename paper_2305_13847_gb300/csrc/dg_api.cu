@@ -510,6 +510,20 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
                 c->ref64.dhat_s[j][a][i] = v;
                 c->ref32.dhat_s[j][a][i] = (float)v;
             }
+    for (int j = 0; j < 3; ++j)
+        for (int a = 0; a < 6; ++a) {
+            const double sc = M.two_over_h[j];
+            const double v[4] = {sc * c->ref64.liftm[a], sc * c->ref64.liftp[a],
+                                 sc * sc * c->ref64.dliftm[a], sc * sc * c->ref64.dliftp[a]};
+            c->ref64.liftm_s[j][a] = v[0];
+            c->ref64.liftp_s[j][a] = v[1];
+            c->ref64.dliftm_s[j][a] = v[2];
+            c->ref64.dliftp_s[j][a] = v[3];
+            c->ref32.liftm_s[j][a] = (float)v[0];
+            c->ref32.liftp_s[j][a] = (float)v[1];
+            c->ref32.dliftm_s[j][a] = (float)v[2];
+            c->ref32.dliftp_s[j][a] = (float)v[3];
+        }
     c->ref64.scaled = 1;
     c->ref32.scaled = 1;
 

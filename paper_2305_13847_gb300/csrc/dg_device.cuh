@@ -124,6 +124,8 @@ struct RefData {
     // contraction needs no separate scaling (read from the mesh's own kernel
     // arguments, also where the other tables are shared between meshes)
     Real dhat_s[3][6][6];
+    Real liftm_s[3][6], liftp_s[3][6];    // (2/h_j) l_a(-+1)/w_a
+    Real dliftm_s[3][6], dliftp_s[3][6];  // (2/h_j)^2 l_a'(-+1)/w_a
     int scaled;
 };
 
@@ -463,7 +465,9 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
         const double s_au = kSau * (rc > 0.0 ? rc : 0.0);
         const double s_ac = kSac * rc * x14;
         o.gm = s_ev - s_au - s_ac;
-        o.vr = rain_velocity(rr, rm, M);
+        // v_r = kvr (rho_r / rho_w)^(1/8) = kvr x^2 rho_w^(-1/8) (Section 2.1)
+        const double rw = M.rho_w > 0.0 ? M.rho_w : rm + rr;
+        o.vr = (rrp > 0.0 && rw > 0.0) ? M.kvr * x2 * inv_root8(rw) : 0.0;
     }
     return o;
 }
@@ -1643,7 +1647,9 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             const Real sc = mconst<Real>(M.two_over_h[j], M.two_over_h_f[j]);
             const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * NFP) * S::NFP1 + q;
             const Real *fp = s_fh + ((el * S::NFACE + 2 * j + 1) * NFP) * S::NFP1 + q;
-            const Real cm = sc * ref.liftm[aj], cp = sc * ref.liftp[aj];
+            const bool scl = A.ref.scaled != 0;
+            const Real cm = scl ? A.ref.liftm_s[j][aj] : sc * ref.liftm[aj];
+            const Real cp = scl ? A.ref.liftp_s[j][aj] : sc * ref.liftp[aj];
 #pragma unroll
             for (int f = 0; f < S::NF; ++f)
                 R[f] -= cp * fp[f * S::NFP1] + cm * fm[f * S::NFP1];
@@ -1651,7 +1657,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 // symmetry term of Eq. (3.7): + (2/h_j)^2 l_a'(s)/w_a S on both faces
                 const Real *sm = fm + S::NF * S::NFP1;
                 const Real *sp = fp + S::NF * S::NFP1;
-                const Real dm = sc * sc * ref.dliftm[aj], dp = sc * sc * ref.dliftp[aj];
+                const Real dm = scl ? A.ref.dliftm_s[j][aj] : sc * sc * ref.dliftm[aj];
+                const Real dp = scl ? A.ref.dliftp_s[j][aj] : sc * sc * ref.dliftp[aj];
 #pragma unroll
                 for (int f = 0; f < S::NF; ++f) R[f] += dp * sp[f * S::NFP1] + dm * sm[f * S::NFP1];
             }
