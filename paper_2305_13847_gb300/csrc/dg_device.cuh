@@ -314,18 +314,26 @@ template <bool NEED_DEFICIT>
 __device__ __forceinline__ SplitResult split_point(double rd, double rm, double rr, double re,
                                                    const double *__restrict__ tab) {
     SplitResult r;
-    const double cu = kCvd * rd + kCvv * rm + kCl * rr;
-    const double tu = kTref + (re - rm * kLprime) * recip(cu);
-    const float rvs32 = rho_vs_f32((float)tu);
+    // T_u = T_ref + X / C_u.  X (a difference of large terms) is float64; the
+    // float32 T_u decides saturation (with a 1e-5 margin) and starts the
+    // pre-solve, and the float64 T_u is formed only where it is the answer or
+    // the decision is close (saturated nodes need only the float32 value: their
+    // root lies above T_u, and the pre-solve ends there)
+    const double X = fma(-rm, kLprime, re);
+    const float cuf = (float)kCvd * (float)rd + (float)kCvv * (float)rm + (float)kCl * (float)rr;
+    const float tuf = fmaf((float)X, __frcp_rn(cuf), (float)kTref);
+    const float rvs32 = rho_vs_f32(tuf);
     bool sat;
-    double rvs_u = 0.0;
-    const bool close = fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tu > 0.0);
+    double rvs_u = 0.0, tu = 0.0;
+    const bool close = fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tuf > 0.0f);
     if (close || (NEED_DEFICIT && !(rm > (double)rvs32))) {
+        tu = fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
         double d1u;
         rvs_u = rho_vs_tab(tu, tab, d1u);
         sat = rm > rvs_u;
     } else {
         sat = rm > (double)rvs32;
+        if (!sat) tu = fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
     }
     if (!sat) {
         r.T = tu;
@@ -338,7 +346,7 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
     const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
     // float32 pre-solve
-    float t = (float)tu;
+    float t = tuf;
     {
         const float cdf = (float)cdry, ref = (float)re, tref = (float)kTref;
         for (int it = 0; it < 30; ++it) {
@@ -356,8 +364,10 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     r.deficit = 0.0;
     // one float64 third-order step from T0
     {
-        const bool tf = (double)t > tu;
-        const double t0 = tf ? (double)t : tu;
+        // t > T_u after a pre-solve from the left of the root; otherwise
+        // (pre-solve cut short) start from the float64 T_u
+        const bool tf = t > tuf;
+        const double t0 = tf ? (double)t : fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
         double drvs;
         const double rvs = tf ? rho_vs_tab(t, tab, drvs) : rho_vs_tab(t0, tab, drvs);
         const double heat = fma(kCvv - kCl, rvs, cdry);
@@ -382,6 +392,7 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
         }
     }
     // fallback: bracketed float64 Newton iteration
+    tu = fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
     double tn0 = ((double)t > tu) ? (double)t : tu;
     double lo = tu, hi = INFINITY, rvs = 0.0, drvs = 0.0, step = INFINITY;
     bool done = false;
@@ -497,12 +508,18 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
     const double rm = brm + (double)u[1];
     const double rr = RAIN ? (double)u[2] : 0.0;
     const double re = (bE + (double)u[ie]) - (double)(0.5f * msq * __frcp_rn(rhof));
-    const double cu = fma(kCvd, rd, fma(kCvv, rm, kCl * rr));
-    const double tu = fma(fma(-rm, kLprime, re), recip(cu), kTref);
-    const float tuf = (float)tu;
+    // T_u = T_ref + X / C_u with X in float64; the float32 T_u decides
+    // saturation and starts the pre-solve, the float64 one is formed only
+    // where T = T_u (unsaturated) or the decision is close
+    const double X = fma(-rm, kLprime, re);
+    const float cuf = (float)kCvd * rdf + (float)kCvv * rmf + (float)kCl * rrf;
+    const float tuf = fmaf((float)X, __frcp_rn(cuf), (float)kTref);
     const float rvs32 = rho_vs_f32(tuf);
     bool sat;
-    if (fabsf(rmf - rvs32) <= 1e-5f * rmf || !(tuf > 0.0f)) {
+    double tu = 0.0;
+    const bool close = fabsf(rmf - rvs32) <= 1e-5f * rmf || !(tuf > 0.0f);
+    if (close) {
+        tu = fma(X, recip(fma(kCvd, rd, fma(kCvv, rm, kCl * rr))), kTref);
         double d1u;
         sat = rm > rho_vs_tab(tu, tab, d1u);      // close call: decide in float64
     } else {
@@ -511,11 +528,12 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
     float deficit = 0.0f, rvf, Tf;
     o.conv = true;
     if (!sat) {
+        if (!close) tu = fma(X, recip(fma(kCvd, rd, fma(kCvv, rm, kCl * rr))), kTref);
         o.T = tu;
         o.rv = rm;
-        Tf = tuf;
+        Tf = (float)tu;
         rvf = rmf;
-        deficit = rvs32 - rmf;
+        deficit = rho_vs_f32(Tf) - rmf;
     } else {
         const float cdf = kCvd * rdf + kCl * (rmf + rrf), ref = (float)re, tref = (float)kTref;
         const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
