@@ -57,6 +57,11 @@ __device__ __forceinline__ Dual sqrt_nr(Dual a) {
     const double s = sqrt(a.v);
     return Dual(s, 0.5 * a.d / s);
 }
+// 1/sqrt(x) and its derivative -1/2 x^(-3/2) x'
+__device__ __forceinline__ Dual rsqrt_nr(Dual a) {
+    const double r = 1.0 / sqrt(a.v);
+    return Dual(r, -0.5 * a.d * r * r * r);
+}
 // |x| with the symmetric derivative 0 at x = 0 (the velocity is exactly 0 in
 // a resting initial state; central differences see 0 there)
 __device__ __forceinline__ Dual fabs(Dual a) {

@@ -802,8 +802,10 @@ template <class S, int J, typename Real>
 __device__ __forceinline__ Real wave_speed(const Prim<S::D, S::RAIN, Real> &P) {
     const Real rc = P.rm - P.rv;
     const Real cv = Real(kCvd) * P.rd + Real(kCvv) * P.rv + Real(kCl) * (rc + P.rr);
-    const Real cm2 = (cv + Real(kRd) * P.rd + Real(kRv) * P.rv) * P.p * P.irho * recip(cv);
-    Real lam = fabs(P.u[J]) + sqrt_nr(cm2);
+    // c_m = sqrt(num / den) = num / sqrt(num den): one reciprocal square root
+    const Real num = (cv + Real(kRd) * P.rd + Real(kRv) * P.rv) * P.p;
+    const Real nd = num * (cv * P.rho);
+    Real lam = fabs(P.u[J]) + (nd > Real(0) ? num * rsqrt_nr(nd) : Real(0));
     if (S::RAIN && J == S::VERT) lam += fabs(P.vr);
     return lam;
 }

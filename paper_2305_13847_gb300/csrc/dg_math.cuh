@@ -76,6 +76,7 @@ __device__ __forceinline__ double inv_root8(double r) {
 // float32 versions for the FP32-bulk arithmetic
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ float sqrt_nr(float x) { return x > 0.0f ? sqrtf(x) : 0.0f; }
+__device__ __forceinline__ float rsqrt_nr(float x) { return 1.0f / sqrtf(x); }
 __device__ __forceinline__ float inv_root8(float r) { return exp2f(-0.125f * __log2f(r)); }
 
 }  // namespace dgm
