@@ -995,18 +995,20 @@ __device__ __forceinline__ void alpha_corners(const KArgs<Real> &A, const int *i
 }
 
 // Q1 interpolant at reference point xi[0..D) of corner values cv[NCORNER]
+// (corner c = sum_j b_j 2^j): D rounds of linear interpolation, first along
+// x (2^(D-1) pairs), then y, then z
 template <class S, typename Real>
 __device__ __forceinline__ Real q1_interp(const Real *cv, const Real *xi) {
-    Real acc = Real(0);
+    Real v[S::NCORNER];
 #pragma unroll
-    for (int c = 0; c < S::NCORNER; ++c) {
-        Real wgt = Real(1);
+    for (int c = 0; c < S::NCORNER; ++c) v[c] = cv[c];
 #pragma unroll
-        for (int j = 0; j < S::D; ++j)
-            wgt *= ((c >> j) & 1) ? Real(0.5) * (Real(1) + xi[j]) : Real(0.5) * (Real(1) - xi[j]);
-        acc = fma(wgt, cv[c], acc);
+    for (int j = 0; j < S::D; ++j) {
+        const Real t = Real(0.5) * (Real(1) + xi[j]);
+#pragma unroll
+        for (int k = 0; k < (S::NCORNER >> (j + 1)); ++k) v[k] = fma(t, v[2 * k + 1] - v[2 * k], v[2 * k]);
     }
-    return acc;
+    return v[0];
 }
 
 // vertex values of the continuous coefficient: mean of alpha_K over the
