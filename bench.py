@@ -293,6 +293,48 @@ def measure_ensemble(torch, dm, inputs, args, world, dist):
             dm.dg_ensemble_free(ens)
 
 
+def measure_adjoint(torch, dm, inputs, workloads, stream, steps):
+    """The adjoint workload (128 x 64 Q4, warm rain, float64): one forward step
+    and one step adjoint (dg_adjoint_step) timed with CUDA events, and the
+    gradient of the final cloud water through 500 steps with at most 32
+    stored states (binomial checkpointing), wall clock."""
+    from paper_2305_13847_gb300.adjoint import cloud_water_gradient
+    w = inputs.workload("adjoint2d_q4")
+    ctx = workloads.open_workload(w, stream=stream)
+    try:
+        info = dm.dg_get_info(ctx)
+        red = dm.dg_reduce(ctx)
+        dt = w["cfl"] * min(L / n for L, n in zip(w["L"], w["n"])) / red[5]
+        shape = (info.n_fields, info.n_elem, info.nodes_per_elem)
+        U0 = torch.empty(shape, dtype=torch.float64, device="cuda")
+        dm.dg_get_state(ctx, U0, dm.DG_DEVICE)
+        lam = torch.ones_like(U0)
+        out = torch.empty_like(U0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        dm.dg_step(ctx, dt, 2)
+        dm.dg_adjoint_step(ctx, dt, U0, lam, out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dm.dg_step_async(ctx, dt, steps)
+        e1.record(stream)
+        for _ in range(steps):
+            dm.dg_adjoint_step(ctx, dt, U0, lam, out)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fwd = e0.elapsed_time(e1) / steps
+        adj = e1.elapsed_time(e2) / steps
+        t0 = time.perf_counter()
+        J, grad, st = cloud_water_gradient(ctx, U0, dt, w["steps"], snapshots=32)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return {"workload": "adjoint2d_q4: 128x64 quads, Q4, warm rain, float64, %d DOFs" % info.n_dofs,
+                "forward_ms_per_step": fwd, "adjoint_ms_per_step": adj, "adjoint_over_forward": adj / fwd,
+                "gradient_%d_steps_s" % w["steps"]: wall, "forward_steps_done": st.forward_steps,
+                "max_stored_states": st.max_held}
+    finally:
+        dm.dg_free(ctx)
+
+
 def run_gb300(args):
     import torch
     from paper_2305_13847_gb300 import dgmoist as dm
@@ -395,6 +437,10 @@ def run_gb300(args):
                 "ms_per_step": 1000.0 * t3 / args.steps}
         dm.dg_free(ctx3)
 
+    # the adjoint workload: step adjoint and the 500-step gradient
+    if args.precision == "fp64" and args.workload == WORKLOAD and not args.no_adjoint:
+        extra["adjoint"] = measure_adjoint(torch, dm, inputs, workloads, stream, args.steps)
+
     # the batched ensemble: 256 uneven 2-D warm-rain bubbles, orders 2-5, FP32-bulk
     if not args.no_ensemble:
         extra["ensemble"] = measure_ensemble(torch, dm, inputs, args, world, dist)
@@ -438,6 +484,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurements")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint measurement")
     ap.add_argument("--no-stab", action="store_true",
                     help="skip the measurement with artificial diffusion and sponge")
     ap.add_argument("--faces", default="auto", choices=sorted(FACES),

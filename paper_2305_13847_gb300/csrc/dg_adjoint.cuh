@@ -90,6 +90,32 @@ __device__ __forceinline__ Dual rain_velocity(Dual rr, Dual rm, const MeshData &
     return Dual(M.kvr) * rain_pow(rrp, 0.125, M.rain_floor) * pow(rw, -0.125);
 }
 
+// v_r(rho_r, rho_m) and its partial derivatives, by the rules of
+// rain_velocity(Dual) (derivative of rho_r^(1/8) at max(rho_r, floor)): the
+// dual-number passes below seed these instead of re-evaluating the powers
+struct RainVel {
+    double v, d_rm, d_rr;
+};
+__device__ __forceinline__ RainVel rain_velocity_partials(double rr, double rm, const MeshData &M) {
+    RainVel o = {0.0, 0.0, 0.0};
+    const double rrp = rr > 0.0 ? rr : 0.0;
+    const bool lit = !(M.rho_w > 0.0);
+    const double rw = lit ? rm + rr : M.rho_w;
+    if (!(rrp > 0.0) || !(rw > 0.0)) return o;
+    const double y = ::pow(rrp, 0.125);
+    const double re = rrp > M.rain_floor ? rrp : M.rain_floor;
+    const double dy = 0.125 * ::pow(re, -0.875);
+    const double z = ::pow(rw, -0.125);
+    const double dz = lit ? -0.125 * z / rw : 0.0;     // d z / d rho_w, rho_w = rho_m + rho_r
+    o.v = M.kvr * y * z;
+    o.d_rr = M.kvr * (dy * z + y * dz);
+    o.d_rm = M.kvr * (y * dz);
+    return o;
+}
+__device__ __forceinline__ Dual rain_velocity_seeded(const RainVel &r, double drm, double drr) {
+    return Dual(r.v, r.d_rm * drm + r.d_rr * drr);
+}
+
 // rho_vs(T) with derivative (closed form of Eq. (2.6) / (R_v T))
 __device__ __forceinline__ Dual rho_vs_dual(Dual T) {
     const double r = rho_vs(T.v, 1.0 / T.v);
@@ -118,6 +144,8 @@ template <class S>
 __device__ __forceinline__ void flux_vjp(const double *x, double brd, double brm, double bE,
                                          double bp, const double (*Fbar)[S::NF], const MeshData &M,
                                          double *xbar) {
+    RainVel rvel = {0.0, 0.0, 0.0};
+    if (S::RAIN) rvel = rain_velocity_partials(x[2], brm + x[1], M);
     for (int k = 0; k < S::NTR; ++k) {
         Dual xd[S::NTR];
 #pragma unroll
@@ -125,7 +153,7 @@ __device__ __forceinline__ void flux_vjp(const double *x, double brd, double brm
         Prim<S::D, S::RAIN, Dual> P;
         make_prim<S, Dual>(P, xd, Dual(brd), Dual(brm), Dual(bE), Dual(bp), xd[S::NF],
                            xd[S::NF + 1], xd[S::NF + 2]);
-        if (S::RAIN) P.vr = rain_velocity(P.rr, P.rm, M);
+        if (S::RAIN) P.vr = rain_velocity_seeded(rvel, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0);
         double acc = 0.0;
 #pragma unroll
         for (int j = 0; j < S::D; ++j) {
@@ -156,17 +184,20 @@ __device__ __forceinline__ void source_vjp(const double *x, double brd, double b
     const int ins[4] = {1, 2, S::NF, S::NF + 1};
     const double rm0 = brm + x[1];
     const bool sat = rm0 - x[S::NF + 1] > 0.0;
+    // the pieces that depend on one input only, evaluated once: rho_vs(T) and
+    // x_r = rho_r^(1/16) with their derivatives (rules of rho_vs_dual, rain_pow)
+    const Dual rvs1 = rho_vs_dual(Dual(x[S::NF], 1.0));
+    const bool rpos = x[2] > 0.0;
+    const Dual xr1 = rpos ? rain_pow(Dual(x[2], 1.0), 0.0625, M.rain_floor) : Dual(0.0);
     for (int c = 0; c < 4; ++c) {
         const int k = ins[c];
         const Dual rm = Dual(brm) + Dual(x[1], k == 1 ? 1.0 : 0.0);
-        const Dual rr = Dual(x[2], k == 2 ? 1.0 : 0.0);
         const Dual T = Dual(x[S::NF], k == S::NF ? 1.0 : 0.0);
         const Dual rv = Dual(x[S::NF + 1], k == S::NF + 1 ? 1.0 : 0.0);
         const Dual rc = rm - rv;
-        Dual deficit = rho_vs_dual(T) - rv;
+        Dual deficit = Dual(rvs1.v, k == S::NF ? rvs1.d : 0.0) - rv;
         if (sat) deficit.v = 0.0;            // the forward value is exactly 0 at saturation
-        const Dual rrp = rr.v > 0.0 ? rr : Dual(0.0);
-        const Dual xr = rrp.v > 0.0 ? rain_pow(rrp, 0.0625, M.rain_floor) : Dual(0.0);
+        const Dual xr = Dual(xr1.v, k == 2 ? xr1.d : 0.0);
         const Dual x2 = xr * xr, x3 = x2 * xr, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
         const Dual s_ev = (Dual(kSevA) - Dual(kSevB) * (T - Dual(kTref))) *
                           (Dual(1.0) + Dual(kSevC) * x3) * deficit * x8;
@@ -236,6 +267,8 @@ __device__ __forceinline__ void face_vjp(const AdjArgs &A, const double *s_w, do
         const double *tt = side == 0 ? tm : tp;
         const bool active = side == 0 ? m_active : !m_active;
         const double jsign = side == 0 ? 1.0 : -1.0;   // d[[U]]/dU^- = 1, d[[U]]/dU^+ = -1
+        RainVel rvel = {0.0, 0.0, 0.0};
+        if (S::RAIN && J == S::VERT) rvel = rain_velocity_partials(tt[2], brm + tt[1], M);
         for (int k = 0; k < S::NTR; ++k) {
             Dual td[S::NTR];
 #pragma unroll
@@ -243,7 +276,8 @@ __device__ __forceinline__ void face_vjp(const AdjArgs &A, const double *s_w, do
             Prim<S::D, S::RAIN, Dual> P;
             make_prim<S, Dual>(P, td, Dual(brd), Dual(brm), Dual(bE), Dual(bp), td[S::NF],
                                td[S::NF + 1], td[S::NF + 2]);
-            if (S::RAIN) P.vr = rain_velocity(P.rr, P.rm, M);
+            if (S::RAIN && J == S::VERT)
+                P.vr = rain_velocity_seeded(rvel, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0);
             Dual F[S::NF];
             flux_dir<S, Dual>(P, J, F);
             const double dlam = active ? wave_speed<S, J, Dual>(P).d : 0.0;
