@@ -194,6 +194,21 @@ def cpu_baseline_subprocess(timeout=600):
 # ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
+def max_over_ranks(torch, dist, value, device):
+    """The largest of every rank's `value` (a duration), returned on every rank;
+    `value` itself when there is no process group."""
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units all ranks processed over the slowest rank's time.  Every rank
+    steps its own full replica (weak scaling), so the job did world x units."""
+    return world * units_per_rank / seconds
+
+
 def _measure(torch, dm, ctx, info, dt, steps, warmup, stream, barrier, dist):
     """Time `steps` SSPRK(4,3) steps (after `warmup`) with CUDA events on `stream`."""
     dm.dg_step(ctx, dt, warmup)
@@ -211,10 +226,7 @@ def _measure(torch, dm, ctx, info, dt, steps, warmup, stream, barrier, dist):
         raise RuntimeError("step failed: %s %s" % (dm.dg_strerror(st), counts.tolist()))
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item()) / 1000.0, step_ms
+    return max_over_ranks(torch, dist, total_ms, "cuda") / 1000.0, step_ms
 
 
 FACES = {"auto": 0, "inline": 1, "pass": 2}
@@ -276,10 +288,7 @@ def measure_ensemble(torch, dm, inputs, args, world, dist):
             ms = ensemble.time_steps(ens, args.steps, stream)
             st = dm.dg_ensemble_step(ens, 0)
             dofs = dm.dg_ensemble_dofs(ens)
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            if dist is not None:
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(torch, dist, ms, "cuda")
             ks = sorted(set(m["order"] for m in members))
             return {
                 "workload": "ensemble: %d 2-D warm-rain bubbles, meshes %dx%d..%dx%d, orders %s, "
@@ -287,7 +296,7 @@ def measure_ensemble(torch, dm, inputs, args, world, dist):
                             % (len(members), min(m["n"][0] for m in members),
                                min(m["n"][1] for m in members), max(m["n"][0] for m in members),
                                max(m["n"][1] for m in members), ks),
-                "dofs": dofs, "value": world * dofs * STAGES / (ms / 1000.0), "unit": UNIT,
+                "dofs": dofs, "value": whole_job_rate(world, dofs * STAGES, ms / 1000.0), "unit": UNIT,
                 "ms_per_step": ms, "autotuned": best, "candidates": len(table)}
         finally:
             dm.dg_ensemble_free(ens)
@@ -363,7 +372,7 @@ def run_gb300(args):
     sampler.start()
     t_max, step_ms = _measure(torch, dm, ctx, info, dt, args.steps, args.warmup, stream, barrier, dist)
     clocks = sampler.stop()
-    value = world * info.n_dofs * STAGES * args.steps / t_max
+    value = whole_job_rate(world, info.n_dofs * STAGES * args.steps, t_max)
 
     # end to end through the C interface with host buffers: upload the state
     # from pinned memory, one step, download the state, every step
@@ -379,10 +388,8 @@ def run_gb300(args):
         dm.dg_step(ctx, dt, 1)
         dm.dg_get_state(ctx, host, dm.DG_HOST)
     torch.cuda.synchronize()
-    e2e_local = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
-    e2e_value = world * info.n_dofs * STAGES * e2e_steps / float(e2e_local.item())
+    e2e_s = max_over_ranks(torch, dist, time.perf_counter() - t0, "cuda")
+    e2e_value = whole_job_rate(world, info.n_dofs * STAGES * e2e_steps, e2e_s)
     roof = _roofline(info, word, t_max, args.steps, peak, peak_kind,
                      _traffic(w, args.precision, info))
     if args.precision == "fp64":
@@ -408,7 +415,7 @@ def run_gb300(args):
                 "workload": "%s: %s hex, Q%d, 7 fields, %d DOFs, %s"
                             % (name, "x".join(map(str, w2["n"])), w2["order"], info2.n_dofs,
                                forms[form]),
-                "value": world * info2.n_dofs * STAGES * args.steps / t2, "unit": UNIT,
+                "value": whole_job_rate(world, info2.n_dofs * STAGES * args.steps, t2), "unit": UNIT,
                 "ms_per_step": 1000.0 * t2 / args.steps,
                 "roofline": _roofline(info2, 4, t2, args.steps, peak, peak_kind,
                                       _traffic(w2, form, info2))}
@@ -433,7 +440,7 @@ def run_gb300(args):
                 "workload": "%s with artificial diffusion (gamma 0.06, sigma 10) and a sponge "
                             "(z_D = 0.75 H, alpha 0.1): alpha pass + face pass + stage kernel"
                             % WORKLOAD,
-                "value": world * info3.n_dofs * STAGES * args.steps / t3, "unit": UNIT,
+                "value": whole_job_rate(world, info3.n_dofs * STAGES * args.steps, t3), "unit": UNIT,
                 "ms_per_step": 1000.0 * t3 / args.steps}
         dm.dg_free(ctx3)
 
