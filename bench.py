@@ -177,7 +177,7 @@ def run_reference(args):
 def cpu_baseline_subprocess(timeout=600):
     """The oracle as it stands, single-threaded, in a child process."""
     code = ("import json,sys; sys.path.insert(0,%r); import bench; "
-            "r,s,d = bench.oracle_sample_rate(60); print(json.dumps([r,s,d]))" % ROOT)
+            "r,s,d = bench.oracle_sample_rate(120); print(json.dumps([r,s,d]))" % ROOT)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     try:
@@ -247,8 +247,8 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto
 # named below; they scale with the node count for the same dimension, order
 # and form.  None (-> traffic null) for any other configuration.
 PROFILED_TRAFFIC = {
-    (3, 4, "fp64"): 481.4,        # 32x32x32 Q4 capture: k_face 147.7 + k_stage 333.7
-    (3, 3, "fp32_bulk"): 281.2,   # 64x64x32 Q3 capture: k_face 93.3 + k_stage 187.9
+    (3, 4, "fp64"): 482.0,        # 32x32x32 Q4 capture: k_face 147.9 + k_stage 334.1
+    (3, 3, "fp32_bulk"): 281.2,   # 64x64x32 Q3 capture: k_face 93.4 + k_stage 187.8
     (3, 3, "fp32_pert"): 281.1,   # 64x64x32 Q3 capture: k_face 93.4 + k_stage 187.7
 }
 
@@ -395,8 +395,8 @@ def run_gb300(args):
     if args.precision == "fp64":
         # the float64 form is bound by the FP64 pipe, not by HBM: ncu's pipe
         # utilisation of the two kernels of a stage (32x32x32 Q4 capture)
-        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.879, "k_face": 0.850,
-                             "source": "ncu sm__inst_executed_pipe_fp64, 32x32x32 Q4 capture"}
+        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.886, "k_face": 0.847,
+                             "source": "ncu sm__pipe_fp64_cycles_active, 32x32x32 Q4 capture"}
     dm.dg_free(ctx)
     del host
 
