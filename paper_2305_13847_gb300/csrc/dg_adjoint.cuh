@@ -45,6 +45,7 @@ __device__ __forceinline__ Dual &operator-=(Dual &a, Dual b) { return a = a - b;
 __device__ __forceinline__ bool operator>(Dual a, Dual b) { return a.v > b.v; }
 __device__ __forceinline__ bool operator<(Dual a, Dual b) { return a.v < b.v; }
 __device__ __forceinline__ bool operator!=(Dual a, Dual b) { return a.v != b.v; }
+__device__ __forceinline__ bool gt0(Dual a) { return a.v > 0.0; }
 __device__ __forceinline__ Dual fma(Dual a, Dual b, Dual c) {
     return Dual(::fma(a.v, b.v, c.v), a.d * b.v + a.v * b.d + c.d);
 }

@@ -279,10 +279,10 @@ __device__ __forceinline__ double rho_vs_tab(double T, const double *__restrict_
 // 150 + i/128 has 16 significant bits, and t - T_i is exact by Sterbenz's
 // lemma), so only the two polynomials run in float64.
 __device__ __forceinline__ double rho_vs_tab(float t, const double *__restrict__ tab, double &d1) {
-    if (!(t >= (float)kTabT0 && t <= (float)(kTabT1 - 1.0))) return rho_vs_tab((double)t, tab, d1);
+    if (!(t >= (float)kTabT0 && t <= (float)(kTabT1 - 1.0))) return rho_vs_tab(widen(t), tab, d1);
     const int i = __float2int_rn((t - (float)kTabT0) * (float)kTabInvStep);
     const float Ti = (float)kTabT0 + (float)i * (float)(1.0 / kTabInvStep);
-    const double d = (double)(t - Ti);
+    const double d = widen(t - Ti);
     const double2 *e = reinterpret_cast<const double2 *>(tab + (size_t)kTabStride * i);
     const double2 c01 = __ldg(e), c23 = __ldg(e + 1), c45 = __ldg(e + 2), c67 = __ldg(e + 3);
     d1 = fma(d, fma(d, c67.y, c67.x), c01.y);
@@ -319,20 +319,25 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     // pre-solve, and the float64 T_u is formed only where it is the answer or
     // the decision is close (saturated nodes need only the float32 value: their
     // root lies above T_u, and the pre-solve ends there)
+    // (float32 copies by narrow(), float64 ones of float32 values by widen():
+    // integer operations, which keep the FP64 pipe for the arithmetic; the
+    // decisions against the float32 rho_vs are float32 compares of the
+    // float32-rounded rho_m, exact up to the 1e-5 margin)
     const double X = fma(-rm, kLprime, re);
-    const float cuf = (float)kCvd * (float)rd + (float)kCvv * (float)rm + (float)kCl * (float)rr;
-    const float tuf = fmaf((float)X, __frcp_rn(cuf), (float)kTref);
+    const float rmf = narrow(rm);
+    const float cuf = (float)kCvd * narrow(rd) + (float)kCvv * rmf + (float)kCl * narrow(rr);
+    const float tuf = fmaf(narrow(X), __frcp_rn(cuf), (float)kTref);
     const float rvs32 = rho_vs_f32(tuf);
     bool sat;
     double rvs_u = 0.0, tu = 0.0;
-    const bool close = fabs(rm - (double)rvs32) <= 1e-5 * rm || !(tuf > 0.0f);
-    if (close || (NEED_DEFICIT && !(rm > (double)rvs32))) {
+    const bool close = fabsf(rmf - rvs32) <= 1e-5f * rmf || !(tuf > 0.0f);
+    if (close || (NEED_DEFICIT && !(rmf > rvs32))) {
         tu = fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
         double d1u;
         rvs_u = rho_vs_tab(tu, tab, d1u);
         sat = rm > rvs_u;
     } else {
-        sat = rm > (double)rvs32;
+        sat = rmf > rvs32;
         if (!sat) tu = fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
     }
     if (!sat) {
@@ -348,7 +353,7 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     // float32 pre-solve
     float t = tuf;
     {
-        const float cdf = (float)cdry, ref = (float)re, tref = (float)kTref;
+        const float cdf = narrow(cdry), ref = narrow(re), tref = (float)kTref;
         for (int it = 0; it < 30; ++it) {
             const float rvs = rho_vs_f32(t);
             const float it_ = __frcp_rn(t);
@@ -367,7 +372,7 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
         // t > T_u after a pre-solve from the left of the root; otherwise
         // (pre-solve cut short) start from the float64 T_u
         const bool tf = t > tuf;
-        const double t0 = tf ? (double)t : fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
+        const double t0 = tf ? widen(t) : fma(X, recip(kCvd * rd + kCvv * rm + kCl * rr), kTref);
         double drvs;
         const double rvs = tf ? rho_vs_tab(t, tab, drvs) : rho_vs_tab(t0, tab, drvs);
         const double heat = fma(kCvv - kCl, rvs, cdry);
@@ -375,18 +380,19 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
         const double h = fma(heat, t0 - kTref, fma(rvs, kLprime, -re));
         const double dh = fma(lat, drvs, heat);
         const double d = -h * recip(dh);
-        if (fabs(d) <= 3e-4) {
+        if (abs_le(d, 3e-4)) {
             // H'' = 2 (c_vv - c_l) rho_vs' + (c_vv - c_l)(T - T_ref) + L') rho_vs'',
             // rho_vs'' = rho_vs (phi1^2 + phi1'), phi1' = -(a-1)/T^2 - 2b/T^3
-            const float itf = __frcp_rn((float)t0), rvf = (float)rvs;
+            const float itf = __frcp_rn(tf ? t : narrow(t0)), rvf = narrow(rvs);
             const float p1f = itf * (am1 + bb * itf);               // (ln rho_vs)
             const float d2rvs = rvf * (p1f * p1f - itf * itf * (am1 + 2.0f * bb * itf));
-            const float d2h = 2.0f * clv * (rvf * p1f) + (float)lat * d2rvs;
-            const float df = (float)d;
-            const float c2 = -0.5f * d2h / (float)dh * df * df;   // second-order term of the step
-            const double dc = d + (double)c2;
+            const float d2h = 2.0f * clv * (rvf * p1f) + narrow(lat) * d2rvs;
+            const float df = narrow(d);
+            const float c2 = -0.5f * d2h / narrow(dh) * df * df;   // second-order term of the step
+            const double dc = d + widen(c2);
+            const float dcf = narrow(dc);
             r.T = t0 + dc;
-            r.rv = fma(drvs, dc, rvs) + (double)(0.5f * d2rvs * (float)dc * (float)dc);
+            r.rv = fma(drvs, dc, rvs) + widen(0.5f * d2rvs * dcf * dcf);
             r.converged = true;
             return r;
         }
@@ -422,9 +428,9 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
 
 // v_r = v0 Gamma(4.5)/6 (pi rho_w N0)^(-1/8) rho_r^(1/8) = kvr (rho_r / rho_w)^(1/8) (Section 2.1)
 __device__ __forceinline__ double rain_velocity(double rr, double rm, const MeshData &M) {
-    const double rrp = rr > 0.0 ? rr : 0.0;
-    const double rw = M.rho_w > 0.0 ? M.rho_w : rm + rr;
-    if (!(rrp > 0.0) || !(rw > 0.0)) return 0.0;
+    const double rw = gt0(M.rho_w) ? M.rho_w : rm + rr;
+    if (!gt0(rr) || !gt0(rw)) return 0.0;
+    const double rrp = rr;
     const double t = rrp * recip(rw);
     const double y = inv_root8(t);                          // t^(-1/8)
     const double y2 = y * y, y4 = y2 * y2;
@@ -458,14 +464,15 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
     o.rv = s.rv;
     o.conv = s.converged;
     o.pp = (rd * kRd + s.rv * kRv) * s.T - pbar;
-    o.phys = (rd > 0.0) && (rho > 0.0) && (s.T > 50.0) && (s.T < 1000.0) && isfinite(o.pp);
+    o.phys = gt0(rd) && gt0(rho) && gt(s.T, 50.0) && lt(s.T, 1000.0) && finite(o.pp);
     o.gm = 0.0;
     o.vr = 0.0;
     if (RAIN) {
         // Eq. (2.4): the rain powers from x = max(rho_r, 0)^(1/16) = r y^15, y = r^(-1/16)
-        const double rrp = rr > 0.0 ? rr : 0.0;
+        const bool rpos = gt0(rr);
+        const double rrp = rpos ? rr : 0.0;
         double x = 0.0;
-        if (rrp > 0.0) {
+        if (rpos) {
             const double y = inv_root16(rrp);
             const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
             x = rrp * (y8 * y4 * y2 * y);
@@ -473,12 +480,12 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
         const double x2 = x * x, x3 = x2 * x, x4 = x2 * x2, x8 = x4 * x4, x14 = x8 * x4 * x2;
         const double rc = rm - s.rv;
         const double s_ev = (kSevA - kSevB * (s.T - kTref)) * (1.0 + kSevC * x3) * s.deficit * x8;
-        const double s_au = kSau * (rc > 0.0 ? rc : 0.0);
+        const double s_au = kSau * (gt0(rc) ? rc : 0.0);
         const double s_ac = kSac * rc * x14;
         o.gm = s_ev - s_au - s_ac;
         // v_r = kvr (rho_r / rho_w)^(1/8) = kvr x^2 rho_w^(-1/8) (Section 2.1)
-        const double rw = M.rho_w > 0.0 ? M.rho_w : rm + rr;
-        o.vr = (rrp > 0.0 && rw > 0.0) ? M.kvr * x2 * inv_root8(rw) : 0.0;
+        const double rw = gt0(M.rho_w) ? M.rho_w : rm + rr;
+        o.vr = (rpos && gt0(rw)) ? M.kvr * x2 * inv_root8(rw) : 0.0;
     }
     return o;
 }
@@ -504,16 +511,16 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
     float msq = 0.0f;
     for (int j = 0; j < d; ++j) msq = fmaf(u[im + j], u[im + j], msq);
     // float64 temperature recovery: T_u = T_ref + (E - |m|^2/(2 rho) - rho_m L') / C_u
-    const double rd = brd + (double)u[0];
-    const double rm = brm + (double)u[1];
-    const double rr = RAIN ? (double)u[2] : 0.0;
-    const double re = (bE + (double)u[ie]) - (double)(0.5f * msq * __frcp_rn(rhof));
+    const double rd = brd + widen(u[0]);
+    const double rm = brm + widen(u[1]);
+    const double rr = RAIN ? widen(u[2]) : 0.0;
+    const double re = (bE + widen(u[ie])) - widen(0.5f * msq * __frcp_rn(rhof));
     // T_u = T_ref + X / C_u with X in float64; the float32 T_u decides
     // saturation and starts the pre-solve, the float64 one is formed only
     // where T = T_u (unsaturated) or the decision is close
     const double X = fma(-rm, kLprime, re);
     const float cuf = (float)kCvd * rdf + (float)kCvv * rmf + (float)kCl * rrf;
-    const float tuf = fmaf((float)X, __frcp_rn(cuf), (float)kTref);
+    const float tuf = fmaf(narrow(X), __frcp_rn(cuf), (float)kTref);
     const float rvs32 = rho_vs_f32(tuf);
     bool sat;
     double tu = 0.0;
@@ -531,11 +538,14 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
         if (!close) tu = fma(X, recip(fma(kCvd, rd, fma(kCvv, rm, kCl * rr))), kTref);
         o.T = tu;
         o.rv = rm;
-        Tf = (float)tu;
+        Tf = narrow(tu);
         rvf = rmf;
         deficit = rho_vs_f32(Tf) - rmf;
     } else {
-        const float cdf = kCvd * rdf + kCl * (rmf + rrf), ref = (float)re, tref = (float)kTref;
+        // explicit fma: a contraction left to the compiler may differ between
+        // the stage kernel and the ensemble's tile functions
+        const float cdf = fmaf((float)kCvd, rdf, (float)kCl * (rmf + rrf)), ref = narrow(re);
+        const float tref = (float)kTref;
         const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
         const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
         float t = tuf;
@@ -556,23 +566,24 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
         }
         // one float64 Newton correction of T with the float64 rho_vs
         double drvs64;
-        const double T32 = (double)t;
+        const double T32 = widen(t);
         const double rvs = rho_vs_tab(t, tab, drvs64);
         const double cdry = fma(kCvd, rd, kCl * (rm + rr));
         const double h = fma(fma(kCvv - kCl, rvs, cdry), T32 - kTref, fma(rvs, kLprime, -re));
-        const float rvsf = (float)rvs, itf = __frcp_rn(t);
+        const float rvsf = narrow(rvs), itf = __frcp_rn(t);
         const float drvs = rvsf * itf * (am1 + bb * itf);
         const float dh = cdf + clv * rvsf + (clv * (t - tref) + lp) * drvs;
-        const float dT = (float)h / dh;
-        o.T = T32 - (double)dT;
-        o.rv = fma(-drvs64, (double)dT, rvs);
-        Tf = (float)o.T;
-        rvf = (float)o.rv;
+        const float dT = narrow(h) / dh;
+        const double dT64 = widen(dT);
+        o.T = T32 - dT64;
+        o.rv = fma(-drvs64, dT64, rvs);
+        Tf = narrow(o.T);
+        rvf = narrow(o.rv);
         o.conv = conv && fabsf(dT) <= 1e-4f * t;
     }
     // p' = (rho_d R_d + rho_v R_v) T - p_bar in float64 (cancellation against p_bar)
     o.pp = fma(fma(rd, kRd, o.rv * kRv), o.T, -pbar);
-    const float ppf = (float)o.pp;
+    const float ppf = narrow(o.pp);
     o.phys = (rdf > 0.0f) && (rhof > 0.0f) && (Tf > 50.0f) && (Tf < 1000.0f) && isfinite(ppf);
     o.gm = 0.0;
     o.vr = 0.0;
@@ -805,7 +816,7 @@ __device__ __forceinline__ Real wave_speed(const Prim<S::D, S::RAIN, Real> &P) {
     // c_m = sqrt(num / den) = num / sqrt(num den): one reciprocal square root
     const Real num = (cv + Real(kRd) * P.rd + Real(kRv) * P.rv) * P.p;
     const Real nd = num * (cv * P.rho);
-    Real lam = fabs(P.u[J]) + (nd > Real(0) ? num * rsqrt_nr(nd) : Real(0));
+    Real lam = fabs(P.u[J]) + (gt0(nd) ? num * rsqrt_nr(nd) : Real(0));
     if (S::RAIN && J == S::VERT) lam += fabs(P.vr);
     return lam;
 }
@@ -1270,7 +1281,7 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
     flux_dir<S, Real>(Pm, J, Fm);
     flux_dir<S, Real>(Pp, J, Fp);
     const Real lm = wave_speed<S, J, Real>(Pm), lpp = wave_speed<S, J, Real>(Pp);
-    const Real lam = lm > lpp ? lm : lpp;
+    const Real lam = max_nonneg(lm, lpp);
     const Real hs = Real(0.5) * Real(s), hl = Real(0.5) * lam;
     Real *out = s_fh + ((el2 * S::NFACE + face) * S::NF) * S::NFP1 + q;
     // one explicit fma, as in face_flux: both schedules round identically
@@ -1346,7 +1357,7 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     flux_dir<S, Real>(Pl, J, Fl);
     flux_dir<S, Real>(Ph, J, Fh);
     const Real ll = wave_speed<S, J, Real>(Pl), lh = wave_speed<S, J, Real>(Ph);
-    const Real lam = ll > lh ? ll : lh;
+    const Real lam = max_nonneg(ll, lh);
     // per element: [2D faces][NFP fields][NFP1 points]
     constexpr int NFP = DIFF ? 2 * S::NF : S::NF;
     constexpr size_t EB = (size_t)S::NFACE * NFP * S::NFP1;
@@ -1672,9 +1683,11 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             const bool scl = A.ref.scaled != 0;
             const Real cm = scl ? A.ref.liftm_s[j][aj] : sc * ref.liftm[aj];
             const Real cp = scl ? A.ref.liftp_s[j][aj] : sc * ref.liftp[aj];
+            // two fmas per face and field (a sum of the two products first
+            // would cost a multiply and an add more)
 #pragma unroll
             for (int f = 0; f < S::NF; ++f)
-                R[f] -= cp * fp[f * S::NFP1] + cm * fm[f * S::NFP1];
+                R[f] = fma(-cm, fm[f * S::NFP1], fma(-cp, fp[f * S::NFP1], R[f]));
             if (DIFF) {
                 // symmetry term of Eq. (3.7): + (2/h_j)^2 l_a'(s)/w_a S on both faces
                 const Real *sm = fm + S::NF * S::NFP1;
@@ -1682,7 +1695,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 const Real dm = scl ? A.ref.dliftm_s[j][aj] : sc * sc * ref.dliftm[aj];
                 const Real dp = scl ? A.ref.dliftp_s[j][aj] : sc * sc * ref.dliftp[aj];
 #pragma unroll
-                for (int f = 0; f < S::NF; ++f) R[f] += dp * sp[f * S::NFP1] + dm * sm[f * S::NFP1];
+                for (int f = 0; f < S::NF; ++f)
+                    R[f] = fma(dm, sm[f * S::NFP1], fma(dp, sp[f * S::NFP1], R[f]));
             }
         }
         const size_t gi = (size_t)e * S::NP + a;
@@ -1694,7 +1708,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 #pragma unroll
             for (int f = 0; f < S::NF; ++f) {
                 Real v = A.beta * u[f] + A.gdt * R[f];
-                if (A.alpha != Real(0)) v += A.alpha * A.Un[f * nodes + gi];
+                if (nonzero(A.alpha)) v = fma(A.alpha, A.Un[f * nodes + gi], v);
                 un[f] = v;
             }
             if (A.sponge) {

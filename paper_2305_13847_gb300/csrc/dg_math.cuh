@@ -12,8 +12,11 @@
 // * r^(-1/n) by the Newton iteration y <- y + y (1 - r y^n) / n, which needs no
 //   division, seeded from a float32 estimate (error ~1e-7, so two iterations
 //   reach float64 rounding).
-// * Reciprocal and reciprocal square root by Newton-Raphson refinement of a
-//   float32 seed.
+// * Reciprocal and reciprocal square root by Newton-Raphson refinement of the
+//   hardware's approximate float64 reciprocal and reciprocal square root.
+// * float32 <-> float64 conversions by integer operations (narrow, widen).
+//   The hardware conversions issue to the FP64 pipe, which bounds the
+//   float64 kernels on GB300; the integer pipe is nearly idle there.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -29,18 +32,81 @@ constexpr int kTabN = 32001;         // 150 K .. 400 K
 constexpr int kTabStride = 8;
 constexpr double kTabT1 = kTabT0 + (kTabN - 1) / kTabInvStep;
 
-// 1/x: float32 seed, two Newton-Raphson steps r <- r + r (1 - x r)
+// float32 value of x rounded to nearest even, as the hardware conversion
+// gives it, from the bit pattern.  Values outside the float32 normal range
+// (and NaN, infinities) go to the hardware conversion; zero keeps its sign.
+__device__ __forceinline__ float narrow(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned mag = hi & 0x7fffffffu;
+    // float32 biased exponent = float64 biased exponent - 896, in 1 .. 254
+    if ((mag >> 20) - 897u >= 254u) {
+        if ((mag | lo) == 0u) return __uint_as_float(hi);
+        return (float)x;
+    }
+    unsigned bits = ((mag - (896u << 20)) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;           // the 29 bits that are dropped
+    bits += (rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | bits);
+}
+
+// float64 value of a float32 (exact), from the bit pattern; subnormals, NaN
+// and infinities go to the hardware conversion
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f), mag = u & 0x7fffffffu;
+    if (mag - 0x00800000u >= 0x7f000000u) {
+        if (mag == 0u) return __hiloint2double((int)u, 0);
+        return (double)f;
+    }
+    return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(mag << 29));
+}
+
+// float64 comparisons on the bit pattern (integer pipe).  Non-negative
+// doubles order like their bit patterns read as signed 64-bit integers and
+// negative ones read as negative integers, so against a positive constant c
+// these agree with the float64 compare for every x but NaN.  A NaN with its
+// sign bit clear passes gt0() and gt() and fails lt(); with the sign bit set
+// it fails gt0() and gt() and passes lt(); abs_le() fails for every NaN.  So
+// gt(x, a) && lt(x, b) is false for NaN, as the float64 compares are.
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool gt(double x, double c) {
+    return __double_as_longlong(x) > __double_as_longlong(c);
+}
+__device__ __forceinline__ bool lt(double x, double c) {
+    return __double_as_longlong(x) < __double_as_longlong(c);
+}
+__device__ __forceinline__ bool abs_le(double x, double c) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) <= __double_as_longlong(c);
+}
+__device__ __forceinline__ bool finite(double x) {
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
+// the hardware's approximate float64 reciprocal and reciprocal square root
+// (from the upper half of the operand; float32-level accuracy), as seeds
+__device__ __forceinline__ double rcp_seed(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
+__device__ __forceinline__ double rsqrt_seed(double x) {
+    double r;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
+// 1/x: two Newton-Raphson steps r <- r + r (1 - x r) from the seed
 __device__ __forceinline__ double recip(double x) {
-    double r = (double)__frcp_rn((float)x);
+    double r = rcp_seed(x);
     double e = fma(-x, r, 1.0);
     r = fma(r, e, r);
     e = fma(-x, r, 1.0);
     return fma(r, e, r);
 }
 
-// 1/sqrt(x): float32 seed, two Newton steps y <- y (3 - x y^2) / 2
+// 1/sqrt(x): two Newton steps y <- y (3 - x y^2) / 2 from the seed
 __device__ __forceinline__ double rsqrt_nr(double x) {
-    double y = (double)rsqrtf((float)x);
+    double y = rsqrt_seed(x);
     double h = 0.5 * x;
     y = y * fma(-h * y, y, 1.5);
     return y * fma(-h * y, y, 1.5);
@@ -49,10 +115,11 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 __device__ __forceinline__ double sqrt_nr(double x) { return x > 0.0 ? x * rsqrt_nr(x) : 0.0; }
 
 // r^(-1/16) for r > 0 (two iterations from a float32 seed; tiny r, outside the
-// float32 range of the seed, takes the library power function)
+// float32 range of the seed, takes the library power function; r > 0 orders
+// like its bit pattern, so the test needs no float64 compare)
 __device__ __forceinline__ double inv_root16(double r) {
-    if (r < 1e-30) return pow(r, -0.0625);
-    double y = (double)exp2f(-0.0625f * __log2f((float)r));
+    if (__double_as_longlong(r) < __double_as_longlong(1e-30)) return pow(r, -0.0625);
+    double y = widen(exp2f(-0.0625f * __log2f(narrow(r))));
     for (int it = 0; it < 2; ++it) {
         const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4, y16 = y8 * y8;
         const double e = fma(-r, y16, 1.0);
@@ -63,8 +130,8 @@ __device__ __forceinline__ double inv_root16(double r) {
 
 // r^(-1/8) for r > 0
 __device__ __forceinline__ double inv_root8(double r) {
-    if (r < 1e-30) return pow(r, -0.125);
-    double y = (double)exp2f(-0.125f * __log2f((float)r));
+    if (__double_as_longlong(r) < __double_as_longlong(1e-30)) return pow(r, -0.125);
+    double y = widen(exp2f(-0.125f * __log2f(narrow(r))));
     for (int it = 0; it < 2; ++it) {
         const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
         const double e = fma(-r, y8, 1.0);
@@ -73,7 +140,20 @@ __device__ __forceinline__ double inv_root8(double r) {
     return y;
 }
 
+// x != 0 (either sign of zero is zero), for kernel parameters
+__device__ __forceinline__ bool nonzero(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0;
+}
+__device__ __forceinline__ bool nonzero(float x) { return x != 0.0f; }
+
+// the larger of two non-negative values (wave speeds): on the bit pattern
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+    return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
+}
+
 // float32 versions for the FP32-bulk arithmetic
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+__device__ __forceinline__ float max_nonneg(float a, float b) { return a > b ? a : b; }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ float sqrt_nr(float x) { return x > 0.0f ? sqrtf(x) : 0.0f; }
 __device__ __forceinline__ float rsqrt_nr(float x) { return 1.0f / sqrtf(x); }
