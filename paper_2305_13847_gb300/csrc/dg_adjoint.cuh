@@ -220,13 +220,15 @@ __device__ __forceinline__ void face_vjp(const AdjArgs &A, const double *s_w, do
     double tm[S::NTR], tp[S::NTR];
 #pragma unroll
     for (int fld = 0; fld < S::NTR; ++fld)
-        tm[fld] = A.trace[(((size_t)face * S::NTR + fld) * ne + e2) * S::NFP1 + q];
+        tm[fld] = has_trace<S>(fld, J) ? A.trace[(((size_t)face * S::NTR + fld) * ne + e2) * S::NFP1 + q]
+                                       : 0.0;
     const int nb = neighbour<S::D>(M, e2, J, s);
     if (nb >= 0) {
         const int fo = 2 * J + (s > 0 ? 0 : 1);
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld)
-            tp[fld] = A.trace[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q];
+            tp[fld] = has_trace<S>(fld, J) ? A.trace[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q]
+                                           : 0.0;
     } else {
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld) tp[fld] = tm[fld];

@@ -836,6 +836,14 @@ __device__ __forceinline__ Real interp_face(const Real *v, const Real *ls, int j
     return acc;
 }
 
+// Which trace fields a face carries: T enters the face flux only through the
+// rain's energy flux on faces normal to e_z, so the other faces hold no
+// temperature trace (its slot in the trace buffer is neither written nor read)
+template <class S>
+__host__ __device__ constexpr bool has_trace(int fld, int j) {
+    return fld != S::NF || j == S::VERT;
+}
+
 // ---------------------------------------------------------------------------
 // k_prepare: split at every node and traces of every face
 // ---------------------------------------------------------------------------
@@ -856,6 +864,7 @@ __device__ __forceinline__ void write_line(const KArgs<Real> &A, const RefData<R
     const size_t fs = (size_t)ne * S::NFP1;
 #pragma unroll
     for (int fld = 0; fld < S::NTR; ++fld) {
+        if (!has_trace<S>(fld, J)) continue;
         Real v[S::P1];
 #pragma unroll
         for (int i = 0; i < S::P1; ++i) v[i] = s_tr[fld * STR + b0 + i * st];
@@ -898,6 +907,7 @@ __device__ __forceinline__ void write_traces_points(const KArgs<Real> &A, const 
         const Real *ls = (face & 1) ? ref.lp : ref.lm;
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld) {
+            if (!has_trace<S>(fld, j)) continue;
             const Real *v = s_tr + (size_t)fld * S::EPB * S::NP + el * S::NP;
             trace_out[(((size_t)face * S::NTR + fld) * ne + e) * S::NFP1 + q] =
                 interp_face<S, Real>(v, ls, j, q);
@@ -1247,7 +1257,9 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
         // when this state was produced; reading it back saves float64 work
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld)
-            tm[fld] = A.trace_in[(((size_t)face * S::NTR + fld) * ne + e2) * S::NFP1 + q];
+            tm[fld] = has_trace<S>(fld, J)
+                          ? A.trace_in[(((size_t)face * S::NTR + fld) * ne + e2) * S::NFP1 + q]
+                          : Real(0);
     } else {
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld)
@@ -1257,7 +1269,9 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
         const int fo = 2 * J + (s > 0 ? 0 : 1);
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld)
-            tp[fld] = A.trace_in[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q];
+            tp[fld] = has_trace<S>(fld, J)
+                          ? A.trace_in[(((size_t)fo * S::NTR + fld) * ne + nb) * S::NFP1 + q]
+                          : Real(0);
     } else {
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld) tp[fld] = tm[fld];
@@ -1322,12 +1336,16 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     if (e_lo >= 0) {
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld)
-            tl[fld] = A.trace_in[(((size_t)(2 * J + 1) * S::NTR + fld) * ne + e_lo) * S::NFP1 + q];
+            tl[fld] = has_trace<S>(fld, J)
+                          ? A.trace_in[(((size_t)(2 * J + 1) * S::NTR + fld) * ne + e_lo) * S::NFP1 + q]
+                          : Real(0);
     }
     if (e_hi >= 0) {
 #pragma unroll
         for (int fld = 0; fld < S::NTR; ++fld)
-            th[fld] = A.trace_in[(((size_t)(2 * J) * S::NTR + fld) * ne + e_hi) * S::NFP1 + q];
+            th[fld] = has_trace<S>(fld, J)
+                          ? A.trace_in[(((size_t)(2 * J) * S::NTR + fld) * ne + e_hi) * S::NFP1 + q]
+                          : Real(0);
     }
     if (e_lo < 0) {
 #pragma unroll

@@ -9,9 +9,9 @@
 //   rho_vs = R_i exp(phi(T) - phi(T_i)), phi = (a-1) ln T - b/T (Eq. (2.6)),
 //   with the Taylor coefficients p_k of phi and the series recurrence of the
 //   exponential, c_n = (1/n) sum_{k=1..n} k p_k c_{n-k}.
-// * r^(-1/n) by the Newton iteration y <- y + y (1 - r y^n) / n, which needs no
-//   division, seeded from a float32 estimate (error ~1e-7, so two iterations
-//   reach float64 rounding).
+// * r^(-1/n) from a float32 estimate by one third-order step
+//   y <- y (1 + e/n + (n+1) e^2/(2 n^2)), e = 1 - r y^n, which needs no
+//   division and reaches float64 rounding from the estimate's ~3e-7.
 // * Reciprocal and reciprocal square root by Newton-Raphson refinement of the
 //   hardware's approximate float64 reciprocal and reciprocal square root.
 // * float32 <-> float64 conversions by integer operations (narrow, widen).
@@ -114,30 +114,29 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 
 __device__ __forceinline__ double sqrt_nr(double x) { return x > 0.0 ? x * rsqrt_nr(x) : 0.0; }
 
-// r^(-1/16) for r > 0 (two iterations from a float32 seed; tiny r, outside the
-// float32 range of the seed, takes the library power function; r > 0 orders
-// like its bit pattern, so the test needs no float64 compare)
+// r^(-1/n) for r > 0, n = 16 and 8: a float32 seed y (relative error delta
+// ~3e-7), then one third-order step.  With e = 1 - r y^n the exact value is
+// y (1 - e)^(-1/n) = y (1 + e/n + (n+1) e^2/(2 n^2) + O(e^3)); keeping the
+// terms to e^2 leaves ~(n+1)(2n+1) delta^3/6 < 1e-18, float64 rounding.
+// Tiny r, outside the float32 range of the seed, takes the library power
+// function; r > 0 orders like its bit pattern, so that test needs no
+// float64 compare.
 __device__ __forceinline__ double inv_root16(double r) {
     if (__double_as_longlong(r) < __double_as_longlong(1e-30)) return pow(r, -0.0625);
-    double y = widen(exp2f(-0.0625f * __log2f(narrow(r))));
-    for (int it = 0; it < 2; ++it) {
-        const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4, y16 = y8 * y8;
-        const double e = fma(-r, y16, 1.0);
-        y = fma(0.0625 * y, e, y);
-    }
-    return y;
+    const double y = widen(exp2f(-0.0625f * __log2f(narrow(r))));
+    const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    const double e = fma(-r, y8 * y8, 1.0);
+    const double c = fma(17.0 / 512.0, e, 0.0625);
+    return fma(y * c, e, y);
 }
 
-// r^(-1/8) for r > 0
 __device__ __forceinline__ double inv_root8(double r) {
     if (__double_as_longlong(r) < __double_as_longlong(1e-30)) return pow(r, -0.125);
-    double y = widen(exp2f(-0.125f * __log2f(narrow(r))));
-    for (int it = 0; it < 2; ++it) {
-        const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
-        const double e = fma(-r, y8, 1.0);
-        y = fma(0.125 * y, e, y);
-    }
-    return y;
+    const double y = widen(exp2f(-0.125f * __log2f(narrow(r))));
+    const double y2 = y * y, y4 = y2 * y2;
+    const double e = fma(-r, y4 * y4, 1.0);
+    const double c = fma(9.0 / 128.0, e, 0.125);
+    return fma(y * c, e, y);
 }
 
 // x != 0 (either sign of zero is zero), for kernel parameters
