@@ -379,7 +379,11 @@ def run_gb300(args):
     host = torch.empty(info.state_bytes // word, dtype=torch.float64 if word == 8 else torch.float32,
                        pin_memory=True)
     dm.dg_get_state(ctx, host, dm.DG_HOST)
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 10))
+    # one untimed round trip first (first use of the pinned pages by the copies)
+    dm.dg_set_state(ctx, host, dm.DG_HOST)
+    dm.dg_step(ctx, dt, 1)
+    dm.dg_get_state(ctx, host, dm.DG_HOST)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
