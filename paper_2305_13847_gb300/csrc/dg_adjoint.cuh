@@ -138,33 +138,133 @@ struct AdjArgs {
     double alpha, beta, gamma;
 };
 
-// Column-by-column Jacobian-vector products of the nodal flux: for the
-// inputs x = (U, T, rho_v, p') at one node, xbar_k += sum_j sum_f
-// Fbar[j][f] dF_jf / dx_k.
+// Reverse-mode derivatives of the pointwise flux, by hand: the adjoints of
+// the primitive quantities of make_prim accumulate in PrimBar (flux_dir_vjp,
+// wave_speed_vjp) and prim_to_inputs carries them back to the inputs
+// x = (U', T, rho_v, p').  One reverse sweep replaces one forward
+// dual-number pass per input.
+template <int D>
+struct PrimBar {
+    double rd, rm, rr, rho, E, p, T, rv, vr;
+    double m[D], u[D];
+};
+
+template <int D>
+__device__ __forceinline__ void zero_bar(PrimBar<D> &B) {
+    B.rd = B.rm = B.rr = B.rho = B.E = B.p = B.T = B.rv = B.vr = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) B.m[i] = B.u[i] = 0.0;
+}
+
+// sign with the convention of fabs(Dual): derivative 0 at exactly 0
+__device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// Fb . dF_j/dP for the flux of flux_dir (same formulas):
+//   F_j = rho_d u_j, rho_m u_j, rho_r (u_j - v_r d_jz), m_i u_j - rho_r v_r u_i d_jz + p' d_ij,
+//         (E + p) u_j - (c_l (T - T_ref) + |u|^2/2) rho_r v_r d_jz
+template <class S>
+__device__ __forceinline__ void flux_dir_vjp(const Prim<S::D, S::RAIN, double> &P, int j,
+                                             const double *Fb, PrimBar<S::D> &B) {
+    const bool vert = (j == S::VERT);
+    const double uj = P.u[j];
+    double ubj = Fb[0] * P.rd + Fb[1] * P.rm + Fb[S::IE] * (P.E + P.p);
+    B.rd += Fb[0] * uj;
+    B.rm += Fb[1] * uj;
+    if (S::RAIN) {
+        ubj += Fb[2] * P.rr;
+        B.rr += Fb[2] * uj;
+    }
+#pragma unroll
+    for (int i = 0; i < S::D; ++i) {
+        ubj += Fb[S::IM + i] * P.m[i];
+        B.m[i] += Fb[S::IM + i] * uj;
+    }
+    B.p += Fb[S::IM + j] + Fb[S::IE] * uj;     // p' d_ij and (E + p) u_j (p = p_bar + p')
+    B.E += Fb[S::IE] * uj;
+    if (S::RAIN && vert) {
+        const double rvr = P.rr * P.vr;
+        double ke = 0.0;
+#pragma unroll
+        for (int i = 0; i < S::D; ++i) ke += P.u[i] * P.u[i];
+        double rvrb = -Fb[2] - Fb[S::IE] * (kCl * (P.T - kTref) + 0.5 * ke);
+#pragma unroll
+        for (int i = 0; i < S::D; ++i) {
+            rvrb -= Fb[S::IM + i] * P.u[i];
+            B.u[i] -= (Fb[S::IM + i] + Fb[S::IE] * P.u[i]) * rvr;
+        }
+        B.T -= Fb[S::IE] * kCl * rvr;
+        B.rr += rvrb * P.vr;
+        B.vr += rvrb * P.rr;
+    }
+    B.u[j] += ubj;
+}
+
+// lb . dLambda_side/dP for wave_speed: |u_J| + c_m (+ |v_r| on faces normal
+// to e_z), c_m = sqrt(num / (c_v rho)), num = (c_v + R) p, so that
+// dc = c/2 (d(c_v + R)/(c_v + R) + dp/p - dc_v/c_v - drho/rho)
+template <class S, int J>
+__device__ __forceinline__ void wave_speed_vjp(const Prim<S::D, S::RAIN, double> &P, double lb,
+                                               PrimBar<S::D> &B) {
+    B.u[J] += lb * sgn0(P.u[J]);
+    if (S::RAIN && J == S::VERT) B.vr += lb * sgn0(P.vr);
+    const double cv = kCvd * P.rd + kCvv * P.rv + kCl * (P.rm - P.rv + P.rr);
+    const double R = kRd * P.rd + kRv * P.rv;
+    const double num = (cv + R) * P.p;
+    const double nd = num * (cv * P.rho);
+    if (!(nd > 0.0)) return;
+    const double h = 0.5 * lb * num * rsqrt_nr(nd);       // c/2 times lb
+    const double a = h / (cv + R);
+    const double cvb = a - h / cv;
+    B.p += h / P.p;
+    B.rho -= h / P.rho;
+    B.rd += cvb * kCvd + a * kRd;
+    B.rv += cvb * (kCvv - kCl) + a * kRv;
+    B.rm += cvb * kCl;
+    if (S::RAIN) B.rr += cvb * kCl;
+}
+
+// back through make_prim (rho_d = rho_d_bar + x_0, ..., u = m / rho,
+// p = p_bar + p') and v_r(rho_r, rho_m) to the inputs x
+template <class S>
+__device__ __forceinline__ void prim_to_inputs(const Prim<S::D, S::RAIN, double> &P, PrimBar<S::D> &B,
+                                               const RainVel &rvel, double *xb) {
+    if (S::RAIN) {
+        B.rr += B.vr * rvel.d_rr;
+        B.rm += B.vr * rvel.d_rm;
+    }
+    double irb = 0.0;
+#pragma unroll
+    for (int i = 0; i < S::D; ++i) {
+        B.m[i] += B.u[i] * P.irho;
+        irb += B.u[i] * P.m[i];
+    }
+    B.rho -= irb * P.irho * P.irho;
+    xb[0] += B.rd + B.rho;
+    xb[1] += B.rm + B.rho;
+    if (S::RAIN) xb[2] += B.rr + B.rho;
+#pragma unroll
+    for (int i = 0; i < S::D; ++i) xb[S::IM + i] += B.m[i];
+    xb[S::IE] += B.E;
+    xb[S::NF] += B.T;
+    xb[S::NF + 1] += B.rv;
+    xb[S::NF + 2] += B.p;
+}
+
+// Nodal flux: xbar += sum_j sum_f Fbar[j][f] dF_jf / dx
 template <class S>
 __device__ __forceinline__ void flux_vjp(const double *x, double brd, double brm, double bE,
                                          double bp, const double (*Fbar)[S::NF], const MeshData &M,
                                          double *xbar) {
     RainVel rvel = {0.0, 0.0, 0.0};
     if (S::RAIN) rvel = rain_velocity_partials(x[2], brm + x[1], M);
-    for (int k = 0; k < S::NTR; ++k) {
-        Dual xd[S::NTR];
+    Prim<S::D, S::RAIN, double> P;
+    make_prim<S, double>(P, x, brd, brm, bE, bp, x[S::NF], x[S::NF + 1], x[S::NF + 2]);
+    if (S::RAIN) P.vr = rvel.v;
+    PrimBar<S::D> B;
+    zero_bar<S::D>(B);
 #pragma unroll
-        for (int i = 0; i < S::NTR; ++i) xd[i] = Dual(x[i], i == k ? 1.0 : 0.0);
-        Prim<S::D, S::RAIN, Dual> P;
-        make_prim<S, Dual>(P, xd, Dual(brd), Dual(brm), Dual(bE), Dual(bp), xd[S::NF],
-                           xd[S::NF + 1], xd[S::NF + 2]);
-        if (S::RAIN) P.vr = rain_velocity_seeded(rvel, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0);
-        double acc = 0.0;
-#pragma unroll
-        for (int j = 0; j < S::D; ++j) {
-            Dual F[S::NF];
-            flux_dir<S, Dual>(P, j, F);
-#pragma unroll
-            for (int f = 0; f < S::NF; ++f) acc = ::fma(Fbar[j][f], F[f].d, acc);
-        }
-        xbar[k] += acc;
-    }
+    for (int j = 0; j < S::D; ++j) flux_dir_vjp<S>(P, j, Fbar[j], B);
+    prim_to_inputs<S>(P, B, rvel, xbar);
 }
 
 // Sources G (Eq. (2.4), gravity) as functions of x = (U, T, rho_v, p'):
@@ -266,33 +366,33 @@ __device__ __forceinline__ void face_vjp(const AdjArgs &A, const double *s_w, do
     const double lam = m_active ? lmv : lpv;
     const double hs = 0.5 * s;
     double tmb[S::NTR], tpb[S::NTR];
+    // d Fhat / d(side) = hs dF_J/d(side) + [active] (dLambda/d(side)) (tm - tp)/2
+    //                    + jsign lam/2 on the field itself
+    double Fb[S::NF], lb = 0.0;
+#pragma unroll
+    for (int f = 0; f < S::NF; ++f) {
+        Fb[f] = hs * fhb[f];
+        lb = ::fma(fhb[f], 0.5 * (tm[f] - tp[f]), lb);
+    }
     for (int side = 0; side < 2; ++side) {
-        const double *tt = side == 0 ? tm : tp;
+        Prim<S::D, S::RAIN, double> &P = side == 0 ? Pm : Pp;
         const bool active = side == 0 ? m_active : !m_active;
         const double jsign = side == 0 ? 1.0 : -1.0;   // d[[U]]/dU^- = 1, d[[U]]/dU^+ = -1
         RainVel rvel = {0.0, 0.0, 0.0};
-        if (S::RAIN && J == S::VERT) rvel = rain_velocity_partials(tt[2], brm + tt[1], M);
-        for (int k = 0; k < S::NTR; ++k) {
-            Dual td[S::NTR];
-#pragma unroll
-            for (int i = 0; i < S::NTR; ++i) td[i] = Dual(tt[i], i == k ? 1.0 : 0.0);
-            Prim<S::D, S::RAIN, Dual> P;
-            make_prim<S, Dual>(P, td, Dual(brd), Dual(brm), Dual(bE), Dual(bp), td[S::NF],
-                               td[S::NF + 1], td[S::NF + 2]);
-            if (S::RAIN && J == S::VERT)
-                P.vr = rain_velocity_seeded(rvel, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0);
-            Dual F[S::NF];
-            flux_dir<S, Dual>(P, J, F);
-            const double dlam = active ? wave_speed<S, J, Dual>(P).d : 0.0;
-            double acc = 0.0;
-#pragma unroll
-            for (int f = 0; f < S::NF; ++f) {
-                double df = hs * F[f].d + 0.5 * dlam * (tm[f] - tp[f]);
-                if (f == k) df += 0.5 * lam * jsign;
-                acc = ::fma(fhb[f], df, acc);
-            }
-            (side == 0 ? tmb : tpb)[k] = acc;
+        if (S::RAIN && J == S::VERT) {
+            rvel = rain_velocity_partials(P.rr, P.rm, M);
+            P.vr = rvel.v;
         }
+        PrimBar<S::D> B;
+        zero_bar<S::D>(B);
+        flux_dir_vjp<S>(P, J, Fb, B);
+        if (active) wave_speed_vjp<S, J>(P, lb, B);
+        double *tb = side == 0 ? tmb : tpb;
+#pragma unroll
+        for (int k = 0; k < S::NTR; ++k) tb[k] = 0.0;
+        prim_to_inputs<S>(P, B, rvel, tb);
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) tb[f] = ::fma(0.5 * lam * jsign, fhb[f], tb[f]);
     }
     if (nb >= 0) {
         // the + side is the neighbour's trace on its face (J, -s)
