@@ -503,7 +503,8 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
                                                          double brd, double brm, double bE,
                                                          double pbar, float brdf, float brmf,
                                                          const MeshData &M,
-                                                         const double *__restrict__ tab) {
+                                                         const double *__restrict__ tab,
+                                                         float Tprev = -1.0f) {
     NodeDerived o;
     // float32 totals for the saturation test, the pre-solve and the checks
     const float rdf = brdf + u[0], rmf = brmf + u[1], rrf = RAIN ? u[2] : 0.0f;
@@ -548,7 +549,9 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
         const float tref = (float)kTref;
         const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
         const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
-        float t = tuf;
+        // start at this node's temperature of the previous stage when there
+        // is one (not below T_u, which lies below the saturated root)
+        float t = Tprev > tuf ? Tprev : tuf;
         bool conv = false;
         for (int it = 0; it < 40; ++it) {
             const float rvs = rho_vs_f32(t);
@@ -559,7 +562,9 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
             const float dh = heat + (clv * (t - tref) + lp) * drvs;
             const float dt = h * __frcp_rn(dh);
             t -= dt;
-            if (fabsf(dt) <= 1e-6f * t) {
+            // a step of at most 2e-3 K leaves at most (H''/2H') dt^2 < 2e-7 K;
+            // the float64 correction below takes the rest
+            if (fabsf(dt) <= 2e-3f) {
                 conv = true;
                 break;
             }
@@ -638,7 +643,8 @@ __device__ __forceinline__ float phi_of(float tau, float iTb, float bTb, float i
 template <bool RAIN>
 __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im, int ie, int d,
                                                          float brd, float brm, const float *bs,
-                                                         int nl, const MeshData &M) {
+                                                         int nl, const MeshData &M,
+                                                         float Tprev = -1.0f) {
     NodeDerived o;
     const float Tb = bs[0], rvb = bs[nl], Rb = bs[2 * nl], Qb = bs[3 * nl], Db = bs[4 * nl];
     const float pres = bs[5 * nl], Cb = bs[6 * nl], dTb = bs[7 * nl], eres = bs[8 * nl];
@@ -665,11 +671,14 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
         nu = nu_u;
         deficit = (Db + Rb * em_u) - nu_u;                     // rho_vs(T) - rho_v
     } else {
-        // start at the base temperature unless T_u is warmer: where the base
-        // state is cloudy T_u lies ~ rho_c L'/C (a few K) below the root,
-        // while the root is usually within a fraction of a K of T_bar.  H is
-        // increasing and convex, so Newton converges from either side.
-        tau = tau_u > 0.0f ? tau_u : 0.0f;
+        // start at this node's temperature of the previous stage (a stage
+        // moves it by ~1e-3 K), else at the base temperature; not below T_u,
+        // which lies below the saturated root.  Where the base state is
+        // cloudy T_u lies ~ rho_c L'/C (a few K) below the root, while the
+        // root is usually within a fraction of a K of T_bar.  H is increasing
+        // and convex, so Newton converges from either side.
+        const float tau_p = Tprev > 0.0f ? Tprev - Tb : 0.0f;
+        tau = tau_u > tau_p ? tau_u : tau_p;
         conv = false;
         const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
         float prev = 3.0e38f;
@@ -684,11 +693,13 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
             const float dh = C + ((cvv - cl) * (tau + dTb) + lp) * dnu;
             const float step = h * __frcp_rn(dh);
             tau -= step;
-            // done once the step is at rounding level (2 ulp of T, or 2e-6 K),
-            // or once it stops shrinking below 1e-4 K (float32 rounding of h
-            // then decides the last bits and the iteration only dithers)
+            // done once the step s is at most 2e-3 K: Newton leaves an error
+            // of at most (H''/2H') s^2, and H''/2H' < 0.05 /K on the saturated
+            // branch (0.023 /K at 300 K), so at most 2e-7 K remains; or once
+            // the step stops shrinking (float32 rounding of h then decides
+            // the last bits and the iteration only dithers)
             const float as = fabsf(step);
-            if (as <= 2.4e-7f * T + 2e-6f || (as <= 1e-4f && as >= 0.5f * prev)) {
+            if (as <= 2e-3f || (as <= 1e-2f && as >= 0.5f * prev)) {
                 conv = true;
                 break;
             }
@@ -1068,8 +1079,12 @@ __global__ void k_alpha_vertex(MeshData M, const Real *alphaK, Real *alphaV) {
     }
 }
 
+// Tprev: this node's temperature at the previous stage (a start for the
+// float32 Newton iterations), or <= 0 when there is none
 template <class S>
-__device__ __forceinline__ NodeDerived derive_node(const double *u, const KArgs<double> &A, int lev) {
+__device__ __forceinline__ NodeDerived derive_node(const double *u, const KArgs<double> &A, int lev,
+                                                   double Tprev = -1.0) {
+    (void)Tprev;
     const int nl = A.M.nzlev_node;
     double msq = 0.0;
 #pragma unroll
@@ -1080,23 +1095,25 @@ __device__ __forceinline__ NodeDerived derive_node(const double *u, const KArgs<
 }
 
 template <class S>
-__device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<float> &A, int lev) {
+__device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<float> &A, int lev,
+                                                   float Tprev = -1.0f) {
     const int nl = A.M.nzlev_node;
     if (A.M.pert_split)
         return node_derived_pert<S::RAIN>(u, S::IM, S::IE, S::D, A.bnode[lev], A.bnode[nl + lev],
-                                          A.bsplit + lev, nl, A.M);
+                                          A.bsplit + lev, nl, A.M, Tprev);
     return node_derived_bulk<S::RAIN>(u, S::IM, S::IE, S::D, A.bnode_d[lev], A.bnode_d[nl + lev],
                                       A.bnode_d[2 * nl + lev], A.bnode_d[3 * nl + lev],
-                                      A.bnode[lev], A.bnode[nl + lev], A.M, A.rvs_tab);
+                                      A.bnode[lev], A.bnode[nl + lev], A.M, A.rvs_tab, Tprev);
 }
 
 template <class S, typename Real, bool DIFF = false>
 __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real *u, int e, int a,
-                                                int iz, Real *s_tr, int t, Real *s_red = nullptr) {
+                                                int iz, Real *s_tr, int t, Real *s_red = nullptr,
+                                                Real Tprev = Real(-1)) {
     const size_t nodes = (size_t)A.M.ne * S::NP;
     const size_t gi = (size_t)e * S::NP + a;
     const int lev = iz * S::P1 + digit<S::D, S::P1>(a, S::VERT);
-    const NodeDerived nd = derive_node<S>(u, A, lev);
+    const NodeDerived nd = derive_node<S>(u, A, lev, Tprev);
     if (!nd.conv) atomicAdd(&A.flags[0], 1ull);
     if (!nd.phys) atomicAdd(&A.flags[1], 1ull);
     Real T, rv, pp, gm, vr;
@@ -1744,7 +1761,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             }
 #pragma unroll
             for (int f = 0; f < S::NF; ++f) A.Uout[f * nodes + gi] = un[f];
-            split_and_store<S, Real, DIFF>(A, un, e, a, s_info[el * 16 + 6], s_tr, t, s_red);
+            split_and_store<S, Real, DIFF>(A, un, e, a, s_info[el * 16 + 6], s_tr, t, s_red, dT);
         }
     }
     if (MODE == MODE_STAGE) {
