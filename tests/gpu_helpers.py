@@ -61,22 +61,27 @@ def to_device(U, dtype):
     return torch.from_numpy(np.ascontiguousarray(U)).to(device="cuda", dtype=dtype)
 
 
-def flux_scale(prob, U):
+def flux_scale(prob, U, elements=None):
     """Per-field round-off scale of the right-hand side: the largest term of
     the face flux -- physical flux component, Lambda |U_f|, and for the
     momenta the full pressure p (p' = p - p_bar carries the rounding of p) --
     times the largest derivative-matrix factor (k+1)^2 (2/h).
 
     dU/dt is a difference of such terms; float64 rounding on them is of
-    order 1e-16 of this scale per operation."""
+    order 1e-16 of this scale per operation.  ``elements`` restricts the
+    maxima to a subset of the elements (a sampled region of a large mesh)."""
+    from oracle import thermo
     mesh = prob.mesh
-    el = np.arange(mesh.Ne)
+    el = np.arange(mesh.Ne) if elements is None else np.asarray(elements)
     T, rv, pp, _ = dg.nodal_derived(prob, U, el)
-    P = dg.primitives(prob, [U[f] for f in range(prob.nf)], dg.node_base(prob, el), T, rv, pp)
+    Ue = [U[f][el] for f in range(prob.nf)]
+    P = dg.primitives(prob, Ue, dg.node_base(prob, el), T, rv, pp)
     fl = [dg.physical_flux(prob, j, P) for j in range(mesh.dim)]
     fac = (mesh.k + 1) ** 2 * max(2.0 / h for h in mesh.h)
-    lam = dg.max_wave_speed(prob, U)
+    cm = thermo.sound_speed(P["rho_d"], P["rho_v"], P["rho_c"], P["rho_r"], P["p"])
+    speed = np.sqrt(sum(ui * ui for ui in P["u"]))
+    lam = float(np.max(speed + np.abs(P["v_r"]) + cm))
     pmax = np.abs(prob.base_node["p"]).max()
     return np.array([max(max(np.abs(fl[j][f]).max() for j in range(mesh.dim)),
-                         lam * np.abs(U[f]).max(), pmax if f in prob.i_m else 0.0) * fac
+                         lam * np.abs(Ue[f]).max(), pmax if f in prob.i_m else 0.0) * fac
                      for f in range(prob.nf)])
