@@ -217,6 +217,7 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     A.rvs_tab = c->rvs_tab;
     A.bsplit = c->bsplit;
     A.fbuf = (Real *)c->fbuf;
+    A.ftab = c->ftab;
     A.alphaK = (Real *)c->alphaK;
     A.alphaV = (const Real *)c->alphaV;
     A.flags = c->flags;
@@ -276,7 +277,7 @@ void release(dg_ctx *c) {
     void *ptrs[] = {c->U[0], c->U[1], c->derived, c->trace[0], c->trace[1], c->bnode_d,
                     c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab,
                     c->adjX[0], c->adjX[1], c->adjX[2], c->adjL[0], c->adjL[1], c->adjL[2],
-                    c->ubar_part, c->tadj, c->bsplit, c->fbuf, c->alphaK, c->alphaV,
+                    c->ubar_part, c->tadj, c->bsplit, c->fbuf, c->ftab, c->alphaK, c->alphaV,
                     c->dtrace[0], c->dtrace[1], c->sponge};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -296,7 +297,7 @@ void mesh_float_copies(MeshData &M) {
 }
 
 // face grid of the face pass; returns the length (in elements) of its
-// per-element buffer [ne][2D][per_point][NFP1]
+// face-major buffer [faces normal to e_0 | e_1 | e_2][per_point][NFP1]
 long long set_face_layout(dg_ctx *c, int per_point) {
     MeshData &M = c->M;
     const dg_config &g = c->cfg;
@@ -311,7 +312,32 @@ long long set_face_layout(dg_ctx *c, int per_point) {
         M.nfaces[j] = (int)nfj;
         M.fblk[j] = (int)((nfj * c->nfp1 + kFaceThreads - 1) / kFaceThreads);
     }
-    return c->ne * 2 * g.dim * per_point * c->nfp1;
+    return ((long long)M.nfaces[0] + M.nfaces[1] + M.nfaces[2]) * per_point * c->nfp1;
+}
+
+// index in the face-major face buffer of every element's 2D faces, [ne][2D]
+// (face 2j + s: the low (s = 0) or high (s = 1) face normal to e_j; the high
+// face of the last element of a periodic row is the row's face 0)
+std::vector<int> face_table(const dg_ctx *c) {
+    const MeshData &M = c->M;
+    const int d = c->cfg.dim;
+    std::vector<int> tab((size_t)c->ne * 2 * d);
+    for (long long e = 0; e < c->ne; ++e) {
+        const int im[3] = {(int)(e % M.n[0]), (int)((e / M.n[0]) % M.n[1]),
+                           d == 3 ? (int)(e / ((long long)M.n[0] * M.n[1])) : 0};
+        long long off = 0;
+        for (int j = 0; j < d; ++j) {
+            for (int side = 0; side < 2; ++side) {
+                int f[3] = {im[0], im[1], im[2]};
+                f[j] += side;
+                if (f[j] == M.n[j] && M.periodic[j]) f[j] = 0;
+                const long long n0 = j == 0 ? M.nfn[0] : M.n[0], n1 = j == 1 ? M.nfn[1] : M.n[1];
+                tab[(size_t)e * 2 * d + 2 * j + side] = (int)(off + f[0] + n0 * (f[1] + n1 * f[2]));
+            }
+            off += M.nfaces[j];
+        }
+    }
+    return tab;
 }
 
 int alloc(dg_ctx *c, void **p, size_t bytes) {
@@ -561,6 +587,13 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     if (st == DG_OK && M.pert_split)
         st = alloc(c, (void **)&c->bsplit, sizeof(float) * kBsN * M.nzlev_node);
     if (st == DG_OK && c->face_pass) st = alloc(c, &c->fbuf, (size_t)fbuf_len * c->rsz);
+    if (st == DG_OK && c->face_pass) {
+        const std::vector<int> tab = face_table(c);
+        st = alloc(c, (void **)&c->ftab, sizeof(int) * tab.size());
+        if (st == DG_OK && cudaMemcpy(c->ftab, tab.data(), sizeof(int) * tab.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess)
+            st = DG_ECUDA;
+    }
     if (st == DG_OK && cudaMemsetAsync(c->flags, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = DG_ECUDA;
     if (st == DG_OK) {

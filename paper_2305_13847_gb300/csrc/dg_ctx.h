@@ -34,6 +34,7 @@ struct dg_ctx {
     float *bsplit = nullptr;     // DG_FP32_PERT: base-state split tables
     bool face_pass = false;      // faces in k_face (DG_FACES_PASS) instead of in the stage kernel
     void *fbuf = nullptr;        // face pass: fluxes per face point
+    int *ftab = nullptr;         // face pass: index in fbuf of each element's 2D faces [ne][2D]
     // artificial diffusion and sponge layer (dg_set_stabilisation)
     dg_stabilisation stab{};
     bool diff = false;           // gamma > 0

@@ -144,8 +144,10 @@ struct KArgs {
     const double *bnode_d; // float64 copy for the split
     const double *rvs_tab; // rho_vs Taylor table: [kTabN][kTabStride] (dg_math.cuh)
     const float *bsplit;   // DG_FP32_PERT: split of the base state per node level [kBsN][nzlev_node]
-    Real *fbuf;            // face pass: outward flux of every element face [ne][2D][NFP][NFP1];
-                           // with diffusion NFP = 2 NF: flux, then S = alpha [[u]] / 2
+    Real *fbuf;            // face pass: G along +e_j of every face, face-major [faces][NFP][NFP1]
+                           // (faces normal to e_0, then e_1, e_2); with diffusion NFP = 2 NF:
+                           // flux, then S = alpha [[u]] / 2
+    const int *ftab;       // face pass: index in fbuf of each element's 2D faces [ne][2D]
     Real *alphaK;          // diffusion: [2][ne] alpha_u, alpha_r per element (of the state produced)
     const Real *alphaV;    // diffusion: [2][nv] continuous coefficient at the vertices
     const Real *dtrace_in; // diffusion: d/dx_j traces of Uin  [2D][NF][ne][NFP1]
@@ -1211,28 +1213,36 @@ constexpr size_t stage_smem_bytes() {
            (DIFF ? sizeof(Real) * (size_t)S::EPB * (2 * S::NCORNER + 2) : 0);
 }
 
-// Asynchronous global -> shared copy of n bytes in CHUNK-byte pieces (4, 8 or
-// 16; both addresses CHUNK-aligned), spread over the CTA's threads; completed
-// by cp_async_wait_all.
-template <int CHUNK>
-__device__ __forceinline__ void cp_async_block(void *dst, const void *src, size_t n) {
-    const unsigned sbase = (unsigned)__cvta_generic_to_shared(dst);
-    const char *g = static_cast<const char *>(src);
-    for (size_t i = (size_t)threadIdx.x * CHUNK; i < n; i += (size_t)blockDim.x * CHUNK) {
+// completes the asynchronous copies issued by this thread
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The tile's face values from the face pass's face-major buffer
+// (fbuf [faces][NFP][NFP1]; ftab [ne][2D] gives each element's faces) to
+// s_fh [EPB][2D][NFP][NFP1]: one contiguous block per face, copied
+// asynchronously in CHUNK-byte pieces by all threads; completed by
+// cp_async_wait_all.
+template <class S, typename Real, int NFP>
+__device__ __forceinline__ void cp_async_faces(const Real *fbuf, const int *ftab, Real *s_fh,
+                                               int bidx, int nel) {
+    constexpr size_t FB = sizeof(Real) * (size_t)NFP * S::NFP1;   // bytes per face
+    constexpr int CHUNK = FB % 16 == 0 ? 16 : (FB % 8 == 0 ? 8 : 4);
+    constexpr int NCH = (int)(FB / CHUNK);
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(s_fh);
+    const char *g = reinterpret_cast<const char *>(fbuf);
+    for (int item = threadIdx.x; item < nel * S::NFACE * NCH; item += blockDim.x) {
+        const int ef = item / NCH, ch = item - ef * NCH;            // (element, face), piece
+        const int fidx = __ldg(ftab + (size_t)bidx * S::EPB * S::NFACE + ef);
+        const char *src = g + (size_t)fidx * FB + (size_t)ch * CHUNK;
+        const unsigned dst = sbase + (unsigned)((size_t)ef * FB + (size_t)ch * CHUNK);
         if (CHUNK == 16)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + (unsigned)i),
-                         "l"(g + i));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
         else if (CHUNK == 8)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sbase + (unsigned)i),
-                         "l"(g + i));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src));
         else
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sbase + (unsigned)i),
-                         "l"(g + i));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src));
     }
     asm volatile("cp.async.commit_group;\n" ::);
 }
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // neighbour element across face (j, s) from the element's multi-index, or -1 (wall)
 template <int D>
@@ -1393,13 +1403,11 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     flux_dir<S, Real>(Ph, J, Fh);
     const Real ll = wave_speed<S, J, Real>(Pl), lh = wave_speed<S, J, Real>(Ph);
     const Real lam = max_nonneg(ll, lh);
-    // per element: [2D faces][NFP fields][NFP1 points]
+    // face-major: [faces normal to e_0 | e_1 | e_2][NFP fields][NFP1 points],
+    // one block per face
     constexpr int NFP = DIFF ? 2 * S::NF : S::NF;
-    constexpr size_t EB = (size_t)S::NFACE * NFP * S::NFP1;
-    Real *out_lo = e_lo >= 0 ? A.fbuf + (size_t)e_lo * EB + (size_t)(2 * J + 1) * NFP * S::NFP1 + q
-                             : nullptr;
-    Real *out_hi = e_hi >= 0 ? A.fbuf + (size_t)e_hi * EB + (size_t)(2 * J) * NFP * S::NFP1 + q
-                             : nullptr;
+    const size_t fg = (size_t)(J > 0 ? M.nfaces[0] : 0) + (J > 1 ? M.nfaces[1] : 0) + f;
+    Real *out = A.fbuf + fg * NFP * S::NFP1 + q;
     const Real hl = Real(0.5) * lam;
     // one explicit fma, as in face_point: both schedules round identically
     Real G[S::NF];
@@ -1464,17 +1472,12 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
             }
         }
 #pragma unroll
-        for (int fld = 0; fld < S::NF; ++fld) {
-            if (out_lo) out_lo[(S::NF + fld) * S::NFP1] = Sx[fld];
-            if (out_hi) out_hi[(S::NF + fld) * S::NFP1] = Sx[fld];
-        }
+        for (int fld = 0; fld < S::NF; ++fld) out[(S::NF + fld) * S::NFP1] = Sx[fld];
     }
-    // outward fluxes: +G for the element below the face, -G for the one above
+    // G along +e_J: the outward flux of the element below the face; the one
+    // above lifts -G (the sign sits in its lift coefficient)
 #pragma unroll
-    for (int fld = 0; fld < S::NF; ++fld) {
-        if (out_lo) out_lo[fld * S::NFP1] = G[fld];
-        if (out_hi) out_hi[fld * S::NFP1] = -G[fld];
-    }
+    for (int fld = 0; fld < S::NF; ++fld) out[fld * S::NFP1] = G[fld];
 }
 
 constexpr int kFaceThreads = 128;
@@ -1544,14 +1547,9 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         }
     }
 
-    // face pass: the tile's outward face fluxes are one contiguous block of
-    // fbuf; copy it to shared memory while the nodal phases run
-    if (PF) {
-        constexpr size_t EBB = sizeof(Real) * (size_t)EB;
-        constexpr int CHUNK = EBB % 16 == 0 ? 16 : (EBB % 8 == 0 ? 8 : 4);
-        const int nel = min(S::EPB, ne - bidx * S::EPB);
-        cp_async_block<CHUNK>(s_fh, A.fbuf + (size_t)bidx * S::EPB * EB, EBB * (size_t)nel);
-    }
+    // face pass: copy the tile's face values to shared memory while the
+    // nodal phases run (one contiguous block per face)
+    if (PF) cp_async_faces<S, Real, NFP>(A.fbuf, A.ftab, s_fh, bidx, min(S::EPB, ne - bidx * S::EPB));
 
     // per element: neighbours across the 2D faces (inline faces) and the
     // vertical index
@@ -1718,11 +1716,15 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             const bool scl = A.ref.scaled != 0;
             const Real cm = scl ? A.ref.liftm_s[j][aj] : sc * ref.liftm[aj];
             const Real cp = scl ? A.ref.liftp_s[j][aj] : sc * ref.liftp[aj];
-            // two fmas per face and field (a sum of the two products first
-            // would cost a multiply and an add more)
+            // the low face holds the outward flux (inline) or G along +e_j,
+            // which is minus this element's outward flux (face pass):
+            // fma(-c, -G, r) = fma(c, G, r) exactly, so both schedules round
+            // alike.  Two fmas per face and field (a sum of the two products
+            // first would cost a multiply and an add more).
+            const Real cmo = PF ? cm : -cm;
 #pragma unroll
             for (int f = 0; f < S::NF; ++f)
-                R[f] = fma(-cm, fm[f * S::NFP1], fma(-cp, fp[f * S::NFP1], R[f]));
+                R[f] = fma(cmo, fm[f * S::NFP1], fma(-cp, fp[f * S::NFP1], R[f]));
             if (DIFF) {
                 // symmetry term of Eq. (3.7): + (2/h_j)^2 l_a'(s)/w_a S on both faces
                 const Real *sm = fm + S::NF * S::NFP1;
