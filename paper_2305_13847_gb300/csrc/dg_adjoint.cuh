@@ -45,84 +45,37 @@ __device__ __forceinline__ Dual &operator-=(Dual &a, Dual b) { return a = a - b;
 __device__ __forceinline__ bool operator>(Dual a, Dual b) { return a.v > b.v; }
 __device__ __forceinline__ bool operator<(Dual a, Dual b) { return a.v < b.v; }
 __device__ __forceinline__ bool operator!=(Dual a, Dual b) { return a.v != b.v; }
-__device__ __forceinline__ bool gt0(Dual a) { return a.v > 0.0; }
 __device__ __forceinline__ Dual fma(Dual a, Dual b, Dual c) {
     return Dual(::fma(a.v, b.v, c.v), a.d * b.v + a.v * b.d + c.d);
 }
-__device__ __forceinline__ Dual recip(Dual a) {
-    const double r = 1.0 / a.v;
-    return Dual(r, -a.d * r * r);
-}
-__device__ __forceinline__ Dual sqrt_nr(Dual a) {
-    if (!(a.v > 0.0)) return Dual(0.0, 0.0);
-    const double s = sqrt(a.v);
-    return Dual(s, 0.5 * a.d / s);
-}
-// 1/sqrt(x) and its derivative -1/2 x^(-3/2) x'
-__device__ __forceinline__ Dual rsqrt_nr(Dual a) {
-    const double r = 1.0 / sqrt(a.v);
-    return Dual(r, -0.5 * a.d * r * r * r);
-}
-// |x| with the symmetric derivative 0 at x = 0 (the velocity is exactly 0 in
-// a resting initial state; central differences see 0 there)
-__device__ __forceinline__ Dual fabs(Dual a) {
-    return a.v < 0.0 ? -a : (a.v > 0.0 ? a : Dual(0.0, 0.0));
-}
-__device__ __forceinline__ Dual pow(Dual a, double p) {
-    const double y = ::pow(a.v, p);
-    return Dual(y, p * y / a.v * a.d);
-}
 
-// r^p for rain r > 0 with its derivative taken at max(r, floor) (kRainFloorLin):
-// the powers p < 1 of the warm-rain closure have unbounded derivatives as
-// r -> 0+, and the rain that the DG discretisation leaks into cloud-free
-// elements would otherwise dominate the linearisation.
-__device__ __forceinline__ Dual rain_pow(Dual r, double p, double floor) {
-    const double y = ::pow(r.v, p);
-    const double re = r.v > floor ? r.v : floor;
-    return Dual(y, p * ::pow(re, p - 1.0) * r.d);
-}
-
-__device__ __forceinline__ Dual rain_velocity(Dual rr, Dual rm, const MeshData &M) {
-    const Dual rrp = rr.v > 0.0 ? rr : Dual(0.0);
-    const Dual rw = M.rho_w > 0.0 ? Dual(M.rho_w) : rm + rr;
-    if (!(rrp.v > 0.0) || !(rw.v > 0.0)) return Dual(0.0);
-    // kvr (r / rho_w)^(1/8) = kvr r^(1/8) rho_w^(-1/8)
-    return Dual(M.kvr) * rain_pow(rrp, 0.125, M.rain_floor) * pow(rw, -0.125);
-}
-
-// v_r(rho_r, rho_m) and its partial derivatives, by the rules of
-// rain_velocity(Dual) (derivative of rho_r^(1/8) at max(rho_r, floor)): the
-// dual-number passes below seed these instead of re-evaluating the powers
+// v_r(rho_r, rho_m) and its partial derivatives (the fractional power of
+// rho_r differentiated at max(rho_r, floor), kRainFloorLin: the powers p < 1
+// of the warm-rain closure have unbounded derivatives as rho_r -> 0+, and the
+// rain that the DG discretisation leaks into cloud-free elements would
+// otherwise dominate the linearisation)
 struct RainVel {
     double v, d_rm, d_rr;
 };
 __device__ __forceinline__ RainVel rain_velocity_partials(double rr, double rm, const MeshData &M) {
     RainVel o = {0.0, 0.0, 0.0};
-    const double rrp = rr > 0.0 ? rr : 0.0;
-    const bool lit = !(M.rho_w > 0.0);
+    const bool lit = !gt0(M.rho_w);
     const double rw = lit ? rm + rr : M.rho_w;
-    if (!(rrp > 0.0) || !(rw > 0.0)) return o;
-    const double y = ::pow(rrp, 0.125);
-    const double re = rrp > M.rain_floor ? rrp : M.rain_floor;
-    const double dy = 0.125 * ::pow(re, -0.875);
-    const double z = ::pow(rw, -0.125);
-    const double dz = lit ? -0.125 * z / rw : 0.0;     // d z / d rho_w, rho_w = rho_m + rho_r
+    if (!gt0(rr) || !gt0(rw)) return o;
+    // y = rho_r^(1/8) = x^2 with x = rho_r^(1/16) = rho_r q^15, q = rho_r^(-1/16);
+    // dy/drho_r = y / (8 rho_r), taken at max(rho_r, floor)
+    const double q = inv_root16(rr);
+    const double q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
+    const double x = rr * (q8 * q4 * q2 * q);
+    const double y = x * x;
+    const double dy = rr > M.rain_floor ? 0.125 * y * recip(rr) : 0.125 * ::pow(M.rain_floor, -0.875);
+    const double z = inv_root8(rw);                       // rho_w^(-1/8)
+    const double dz = lit ? -0.125 * z * recip(rw) : 0.0; // d z / d rho_w, rho_w = rho_m + rho_r
     o.v = M.kvr * y * z;
     o.d_rr = M.kvr * (dy * z + y * dz);
     o.d_rm = M.kvr * (y * dz);
     return o;
 }
-__device__ __forceinline__ Dual rain_velocity_seeded(const RainVel &r, double drm, double drr) {
-    return Dual(r.v, r.d_rm * drm + r.d_rr * drr);
-}
-
-// rho_vs(T) with derivative (closed form of Eq. (2.6) / (R_v T))
-__device__ __forceinline__ Dual rho_vs_dual(Dual T) {
-    const double r = rho_vs(T.v, 1.0 / T.v);
-    return Dual(r, r * ((kEsA - 1.0) / T.v + kEsB / (T.v * T.v)) * T.d);
-}
-
 // ---------------------------------------------------------------------------
 struct AdjArgs {
     MeshData M;
@@ -131,6 +84,7 @@ struct AdjArgs {
     const double *derived;  // T, rho_v, p' (, G, v_r) of U
     const double *trace;    // traces of U, [2D][NTR][ne][NFP1]
     const double *bnode, *bface;  // base tables
+    const double *rvs_tab;  // rho_vs Taylor table (dg_math.cuh)
     const double *w;        // adjoint input (ABI layout)
     double *ubar_part;      // [NTR][nodes]: adjoints of U (NF) and of T, rho_v, p'
     double *tadj;           // [2D][NTR][ne][NFP1]: neighbour trace adjoints
@@ -156,7 +110,8 @@ __device__ __forceinline__ void zero_bar(PrimBar<D> &B) {
     for (int i = 0; i < D; ++i) B.m[i] = B.u[i] = 0.0;
 }
 
-// sign with the convention of fabs(Dual): derivative 0 at exactly 0
+// sign, with the derivative of |x| taken as 0 at exactly 0 (the velocity is
+// exactly 0 in a resting initial state; central differences see 0 there)
 __device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
 // Fb . dF_j/dP for the flux of flux_dir (same formulas):
@@ -271,7 +226,8 @@ __device__ __forceinline__ void flux_vjp(const double *x, double brd, double brm
 // forward-mode Jacobian-vector products dotted with the adjoint wv.
 template <class S>
 __device__ __forceinline__ void source_vjp(const double *x, double brd, double brm,
-                                           const double *wv, const MeshData &M, double *xbar) {
+                                           const double *wv, const MeshData &M,
+                                           const double *__restrict__ tab, double *xbar) {
     const double g = M.g;
     // gravity: G_{m_vert} = -g (rho_d' + rho_m' + rho_r'), G_E = -g m_vert
     const double wm = wv[S::IM + S::VERT];
@@ -285,11 +241,22 @@ __device__ __forceinline__ void source_vjp(const double *x, double brd, double b
     const int ins[4] = {1, 2, S::NF, S::NF + 1};
     const double rm0 = brm + x[1];
     const bool sat = rm0 - x[S::NF + 1] > 0.0;
-    // the pieces that depend on one input only, evaluated once: rho_vs(T) and
-    // x_r = rho_r^(1/16) with their derivatives (rules of rho_vs_dual, rain_pow)
-    const Dual rvs1 = rho_vs_dual(Dual(x[S::NF], 1.0));
-    const bool rpos = x[2] > 0.0;
-    const Dual xr1 = rpos ? rain_pow(Dual(x[2], 1.0), 0.0625, M.rain_floor) : Dual(0.0);
+    // the pieces that depend on one input only, evaluated once with their
+    // derivatives: rho_vs(T) (table) and x_r = rho_r^(1/16)
+    double drvs;
+    const double rvs = rho_vs_tab(x[S::NF], tab, drvs);
+    const Dual rvs1(rvs, drvs);
+    // x_r = rho_r^(1/16) = rho_r q^15, q = rho_r^(-1/16); dx_r/drho_r = x_r / (16 rho_r)
+    // at max(rho_r, floor)
+    const bool rpos = gt0(x[2]);
+    Dual xr1(0.0);
+    if (rpos) {
+        const double q = inv_root16(x[2]);
+        const double q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
+        const double xr = x[2] * (q8 * q4 * q2 * q);
+        xr1 = Dual(xr, x[2] > M.rain_floor ? 0.0625 * xr * recip(x[2])
+                                          : 0.0625 * ::pow(M.rain_floor, -0.9375));
+    }
     for (int c = 0; c < 4; ++c) {
         const int k = ins[c];
         const Dual rm = Dual(brm) + Dual(x[1], k == 1 ? 1.0 : 0.0);
@@ -467,7 +434,7 @@ __global__ void __launch_bounds__(S::NT) k_adj_local(AdjArgs A) {
         double wv[S::NF];
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) wv[f] = s_w[f * STR + t];
-        source_vjp<S>(x, brd, brm, wv, M, xbar);
+        source_vjp<S>(x, brd, brm, wv, M, A.rvs_tab, xbar);
     }
     for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
         const int el2 = item / (S::NFACE * S::NFP1);
@@ -510,7 +477,7 @@ __global__ void __launch_bounds__(S::NT) k_adj_local(AdjArgs A) {
 template <class S>
 __device__ __forceinline__ void split_vjp(const double *u, double brd, double brm, double bE,
                                           double T, double rv, double Tb, double rvb, double ppb,
-                                          double *ub) {
+                                          const double *__restrict__ tab, double *ub) {
     const double rd = brd + u[0], rm = brm + u[1], rr = S::RAIN ? u[2] : 0.0;
     const double rho = rd + rm + rr;
     double msq = 0.0;
@@ -527,18 +494,17 @@ __device__ __forceinline__ void split_vjp(const double *u, double brd, double br
         rmb += rvb;
         const double cu = kCvd * rd + kCvv * rm + kCl * rr;
         const double dT = (T - kTref);
-        reb = Tb / cu;
-        rmb += Tb * (-kLprime - kCvv * dT) / cu;
-        rdb += Tb * (-kCvd * dT) / cu;
-        rrb += Tb * (-kCl * dT) / cu;
+        reb = Tb * recip(cu);
+        rmb += reb * (-kLprime - kCvv * dT);
+        rdb += reb * (-kCvd * dT);
+        rrb += reb * (-kCl * dT);
     } else {
-        const double invT = 1.0 / T;
-        const double rvs = rho_vs(T, invT);
-        const double drvs = rvs * invT * ((kEsA - 1.0) + kEsB * invT);
+        double drvs;
+        const double rvs = rho_vs_tab(T, tab, drvs);
         Tb += rvb * drvs;                              // rho_v = rho_vs(T)
         const double heat = kCvd * rd + kCvv * rvs + kCl * (rm - rvs + rr);
         const double dH = heat + ((kCvv - kCl) * (T - kTref) + kLprime) * drvs;
-        const double lam = Tb / dH;                    // dT = -(H_x dx) / H'
+        const double lam = Tb * recip(dH);             // dT = -(H_x dx) / H'
         const double dT = (T - kTref);
         rdb -= lam * kCvd * dT;
         rmb -= lam * kCl * dT;
@@ -546,12 +512,13 @@ __device__ __forceinline__ void split_vjp(const double *u, double brd, double br
         reb = lam;                                     // H_re = -1
     }
     // re = E - |m|^2 / (2 rho)
-    const double rhob = reb * msq / (2.0 * rho * rho);
+    const double irho = recip(rho);
+    const double rhob = 0.5 * reb * msq * irho * irho;
     ub[0] += rdb + rhob;
     ub[1] += rmb + rhob;
     if (S::RAIN) ub[2] += rrb + rhob;
 #pragma unroll
-    for (int j = 0; j < S::D; ++j) ub[S::IM + j] -= reb * u[S::IM + j] / rho;
+    for (int j = 0; j < S::D; ++j) ub[S::IM + j] -= reb * u[S::IM + j] * irho;
     ub[S::IE] += reb;
     (void)bE;
 }
@@ -590,7 +557,7 @@ __global__ void k_adj_gather(AdjArgs A) {
         double brd, brm, bE, bp;
         load_base<S, double>(A.bnode, M.nzlev_node, lev, brd, brm, bE, bp);
         split_vjp<S>(u, brd, brm, bE, A.derived[gi], A.derived[nodes + gi], xb[S::NF], xb[S::NF + 1],
-                     xb[S::NF + 2], xb);
+                     xb[S::NF + 2], A.rvs_tab, xb);
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) {
             const size_t o = f * nodes + gi;
@@ -628,7 +595,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cloud(AdjArgs A, double *partia
         const double T = A.derived[gi], rv = A.derived[nodes + gi];
         acc += W * (brm + u[1] - rv);
         ub[1] += W;                                       // d rho_c / d rho_m'
-        split_vjp<S>(u, brd, brm, bE, T, rv, 0.0, -W, 0.0, ub);
+        split_vjp<S>(u, brd, brm, bE, T, rv, 0.0, -W, 0.0, A.rvs_tab, ub);
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) A.out[f * nodes + gi] = ub[f];
     }

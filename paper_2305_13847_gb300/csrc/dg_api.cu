@@ -406,6 +406,7 @@ AdjArgs adj_args(const dg_ctx *c, const void *U, const double *w, double *out, d
     A.trace = (const double *)c->trace[0];
     A.bnode = c->bnode_d;
     A.bface = c->bface_d;
+    A.rvs_tab = c->rvs_tab;
     A.w = w;
     A.ubar_part = c->ubar_part;
     A.tadj = c->tadj;
