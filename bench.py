@@ -247,9 +247,9 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto
 # named below; they scale with the node count for the same dimension, order
 # and form.  None (-> traffic null) for any other configuration.
 PROFILED_TRAFFIC = {
-    (3, 4, "fp64"): 475.4,        # 32x32x32 Q4 capture: k_face 147.8 + k_stage 327.6
-    (3, 3, "fp32_bulk"): 277.2,   # 64x64x32 Q3 capture: k_face 93.3 + k_stage 183.9
-    (3, 3, "fp32_pert"): 277.2,   # 64x64x32 Q3 capture: k_face 93.3 + k_stage 183.9
+    (3, 4, "fp64"): 411.7,        # 32x32x32 Q4 capture: k_face 117.5 + k_stage 294.2
+    (3, 3, "fp32_bulk"): 237.8,   # 64x64x32 Q3 capture: k_face 74.5 + k_stage 163.3
+    (3, 3, "fp32_pert"): 237.8,   # 64x64x32 Q3 capture: k_face 74.5 + k_stage 163.3
 }
 
 
@@ -399,8 +399,8 @@ def run_gb300(args):
     if args.precision == "fp64":
         # the float64 form is bound by the FP64 pipe, not by HBM: ncu's pipe
         # utilisation of the two kernels of a stage (32x32x32 Q4 capture)
-        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.909, "k_face": 0.847,
-                             "source": "ncu sm__pipe_fp64_cycles_active, 32x32x32 Q4 capture"}
+        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.909, "k_face": 0.848,
+                             "source": "ncu sm__inst_executed_pipe_fp64, 32x32x32 Q4 capture"}
     dm.dg_free(ctx)
     del host
 

@@ -68,7 +68,7 @@ __device__ __forceinline__ RainVel rain_velocity_partials(double rr, double rm, 
     const double q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
     const double x = rr * (q8 * q4 * q2 * q);
     const double y = x * x;
-    const double dy = rr > M.rain_floor ? 0.125 * y * recip(rr) : 0.125 * ::pow(M.rain_floor, -0.875);
+    const double dy = rr > M.rain_floor ? 0.125 * y * recip(rr) : M.rain_d8;
     const double z = inv_root8(rw);                       // rho_w^(-1/8)
     const double dz = lit ? -0.125 * z * recip(rw) : 0.0; // d z / d rho_w, rho_w = rho_m + rho_r
     o.v = M.kvr * y * z;
@@ -254,8 +254,7 @@ __device__ __forceinline__ void source_vjp(const double *x, double brd, double b
         const double q = inv_root16(x[2]);
         const double q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
         const double xr = x[2] * (q8 * q4 * q2 * q);
-        xr1 = Dual(xr, x[2] > M.rain_floor ? 0.0625 * xr * recip(x[2])
-                                          : 0.0625 * ::pow(M.rain_floor, -0.9375));
+        xr1 = Dual(xr, x[2] > M.rain_floor ? 0.0625 * xr * recip(x[2]) : M.rain_d16);
     }
     for (int c = 0; c < 4; ++c) {
         const int k = ins[c];

@@ -520,6 +520,8 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     M.jac = 1.0;
     for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
     M.rain_floor = kRainFloorLin;
+    M.rain_d8 = 0.125 * std::pow(kRainFloorLin, -0.875);
+    M.rain_d16 = 0.0625 * std::pow(kRainFloorLin, -0.9375);
     M.pert_split = (g.precision == DG_FP32_PERT) ? 1 : 0;
     // face grid and the face-pass flux buffer layout
     // the face pass is the faster schedule for every precision on GB300

@@ -79,6 +79,7 @@ struct MeshData {
     double kvr;            // v0 Gamma(4.5)/6 (pi N0)^(-1/8)
     double jac;            // |K| / 2^d
     double rain_floor;     // linearisation only: rain powers differentiated at max(rho_r, floor)
+    double rain_d8, rain_d16;  // d rho_r^(1/8) / d rho_r and d rho_r^(1/16) / d rho_r at the floor
     int pert_split;        // float32 state: 1 = split in perturbation variables (DG_FP32_PERT)
     // faces normal to e_j: a grid of nfn[j] (= n_j, + 1 with walls) x the other n,
     // nfaces[j] of them; face c lies between the elements at coordinates c - 1
@@ -260,16 +261,21 @@ __device__ __forceinline__ float rho_vs_f32(float T) {
 }
 
 // float64 rho_vs(T) and d rho_vs / dT from the Taylor table (dg_math.cuh).
-// Outside the table range the closed form is evaluated directly.
+// Outside the table range the closed form is evaluated directly.  The
+// entry is chosen from the float32-rounded T (within 3e-5 K of T, so
+// |T - T_i| <= 1/256 K + 3e-5 K, where the series is still exact to
+// float64 rounding); T_i = 150 + i/128 is exact in float32 and widened
+// exactly, so the offset needs no float64 <-> integer conversion.
 __device__ __forceinline__ double rho_vs_tab(double T, const double *__restrict__ tab, double &d1) {
-    if (!(T >= kTabT0 && T <= kTabT1 - 1.0)) {
+    const float tf = narrow(T);
+    if (!(tf >= (float)kTabT0 && tf <= (float)(kTabT1 - 1.0))) {
         const double invT = 1.0 / T;
         const double v = rho_vs(T, invT);
         d1 = v * invT * fma(kEsB, invT, kEsA - 1.0);
         return v;
     }
-    const int i = __double2int_rn(fma(T, kTabInvStep, -kTabT0 * kTabInvStep));
-    const double d = T - fma((double)i, 1.0 / kTabInvStep, kTabT0);
+    const int i = __float2int_rn((tf - (float)kTabT0) * (float)kTabInvStep);
+    const double d = T - widen((float)kTabT0 + (float)i * (float)(1.0 / kTabInvStep));
     const double2 *e = reinterpret_cast<const double2 *>(tab + (size_t)kTabStride * i);
     const double2 c01 = __ldg(e), c23 = __ldg(e + 1), c45 = __ldg(e + 2), c67 = __ldg(e + 3);
     d1 = fma(d, fma(d, c67.y, c67.x), c01.y);
@@ -684,12 +690,14 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
         conv = false;
         const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
         float prev = 3.0e38f;
+        bool have_nu = false;
         for (int it = 0; it < 40; ++it) {
             const float T = Tb + tau;
             const float iT = __frcp_rn(T);
             const float em = expm1f(phi_of(tau, iTb, bTb, iT));
             const float nus = Db + Rb * em;                     // rho_vs(T) - rho_v_bar
-            const float dnu = Rb * (1.0f + em) * iT * (am1 + bb * iT);
+            const float p1 = iT * (am1 + bb * iT);              // d phi / d tau
+            const float dnu = Rb * (1.0f + em) * p1;
             const float C = Cb + c0 + (cvv - cl) * nus;
             const float h = C * tau + (c0 + (cvv - cl) * nus) * dTb + nus * lp - de;
             const float dh = C + ((cvv - cl) * (tau + dTb) + lp) * dnu;
@@ -702,12 +710,19 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
             // the last bits and the iteration only dithers)
             const float as = fabsf(step);
             if (as <= 2e-3f || (as <= 1e-2f && as >= 0.5f * prev)) {
+                // nu at the new tau by Taylor from this evaluation:
+                // nu'' = R_bar e^phi (phi'^2 + phi''), and the omitted third-order
+                // term, ~ rho_vs phi'^3 s^3 / 6, is below 1e-12 kg/m^3 for |s| <= 1e-2 K
+                const float p2 = -iT * iT * (am1 + 2.0f * bb * iT);
+                const float d2nu = Rb * (1.0f + em) * (p1 * p1 + p2);
+                nu = fmaf(0.5f * d2nu * step, step, fmaf(-dnu, step, nus));
+                have_nu = true;
                 conv = true;
                 break;
             }
             prev = as;
         }
-        nu = Db + Rb * expm1f(phi_of(tau, iTb, bTb, __frcp_rn(Tb + tau)));
+        if (!have_nu) nu = Db + Rb * expm1f(phi_of(tau, iTb, bTb, __frcp_rn(Tb + tau)));
     }
     const float T = Tb + tau;
     o.Tf = T;

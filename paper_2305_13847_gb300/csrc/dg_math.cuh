@@ -118,25 +118,40 @@ __device__ __forceinline__ double sqrt_nr(double x) { return x > 0.0 ? x * rsqrt
 // ~3e-7), then one third-order step.  With e = 1 - r y^n the exact value is
 // y (1 - e)^(-1/n) = y (1 + e/n + (n+1) e^2/(2 n^2) + O(e^3)); keeping the
 // terms to e^2 leaves ~(n+1)(2n+1) delta^3/6 < 1e-18, float64 rounding.
-// Tiny r, outside the float32 range of the seed, takes the library power
-// function; r > 0 orders like its bit pattern, so that test needs no
-// float64 compare.
+// r below 2^-96, outside the float32 range of the seed (rain that the DG
+// discretisation leaks ahead of a rain region decays far below it), is
+// scaled by 2^128 as often as needed: (r 2^128)^(-1/n) = r^(-1/n) 2^(-128/n),
+// exact powers of two.  Nine scalings reach every positive double (the
+// smallest subnormal is 2^-1074 > 2^-96 2^-1152); the loop stops there also
+// for r <= 0, which the callers exclude (the result is then not a number).
+// r > 0 orders like its bit pattern, so the test needs no float64 compare.
+constexpr double kTiny = 0x1p-96;
+constexpr double kUp = 0x1p128;
+
 __device__ __forceinline__ double inv_root16(double r) {
-    if (__double_as_longlong(r) < __double_as_longlong(1e-30)) return pow(r, -0.0625);
+    double sc = 1.0;
+    for (int it = 0; it < 9 && __double_as_longlong(r) < __double_as_longlong(kTiny); ++it) {
+        r *= kUp;
+        sc *= 0x1p8;
+    }
     const double y = widen(exp2f(-0.0625f * __log2f(narrow(r))));
     const double y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
     const double e = fma(-r, y8 * y8, 1.0);
     const double c = fma(17.0 / 512.0, e, 0.0625);
-    return fma(y * c, e, y);
+    return fma(y * c, e, y) * sc;
 }
 
 __device__ __forceinline__ double inv_root8(double r) {
-    if (__double_as_longlong(r) < __double_as_longlong(1e-30)) return pow(r, -0.125);
+    double sc = 1.0;
+    for (int it = 0; it < 9 && __double_as_longlong(r) < __double_as_longlong(kTiny); ++it) {
+        r *= kUp;
+        sc *= 0x1p16;
+    }
     const double y = widen(exp2f(-0.125f * __log2f(narrow(r))));
     const double y2 = y * y, y4 = y2 * y2;
     const double e = fma(-r, y4 * y4, 1.0);
     const double c = fma(9.0 / 128.0, e, 0.125);
-    return fma(y * c, e, y);
+    return fma(y * c, e, y) * sc;
 }
 
 // x != 0 (either sign of zero is zero), for kernel parameters
