@@ -110,6 +110,25 @@ __device__ __forceinline__ void zero_bar(PrimBar<D> &B) {
     for (int i = 0; i < D; ++i) B.m[i] = B.u[i] = 0.0;
 }
 
+// B += W where c holds (a select per quantity, no branch)
+template <int D>
+__device__ __forceinline__ void add_bar_if(PrimBar<D> &B, const PrimBar<D> &W, bool c) {
+    B.rd += c ? W.rd : 0.0;
+    B.rm += c ? W.rm : 0.0;
+    B.rr += c ? W.rr : 0.0;
+    B.rho += c ? W.rho : 0.0;
+    B.E += c ? W.E : 0.0;
+    B.p += c ? W.p : 0.0;
+    B.T += c ? W.T : 0.0;
+    B.rv += c ? W.rv : 0.0;
+    B.vr += c ? W.vr : 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        B.m[i] += c ? W.m[i] : 0.0;
+        B.u[i] += c ? W.u[i] : 0.0;
+    }
+}
+
 // sign, with the derivative of |x| taken as 0 at exactly 0 (the velocity is
 // exactly 0 in a resting initial state; central differences see 0 there)
 __device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
@@ -340,25 +359,36 @@ __device__ __forceinline__ void face_vjp(const AdjArgs &A, const double *s_w, do
         Fb[f] = hs * fhb[f];
         lb = ::fma(fhb[f], 0.5 * (tm[f] - tp[f]), lb);
     }
-    for (int side = 0; side < 2; ++side) {
-        Prim<S::D, S::RAIN, double> &P = side == 0 ? Pm : Pp;
-        const bool active = side == 0 ? m_active : !m_active;
-        const double jsign = side == 0 ? 1.0 : -1.0;   // d[[U]]/dU^- = 1, d[[U]]/dU^+ = -1
-        RainVel rvel = {0.0, 0.0, 0.0};
-        if (S::RAIN && J == S::VERT) {
-            rvel = rain_velocity_partials(P.rr, P.rm, M);
-            P.vr = rvel.v;
-        }
-        PrimBar<S::D> B;
-        zero_bar<S::D>(B);
-        flux_dir_vjp<S>(P, J, Fb, B);
-        if (active) wave_speed_vjp<S, J>(P, lb, B);
-        double *tb = side == 0 ? tmb : tpb;
+    RainVel rv_m = {0.0, 0.0, 0.0}, rv_p = {0.0, 0.0, 0.0};
+    if (S::RAIN && J == S::VERT) {
+        rv_m = rain_velocity_partials(Pm.rr, Pm.rm, M);
+        rv_p = rain_velocity_partials(Pp.rr, Pp.rm, M);
+        Pm.vr = rv_m.v;
+        Pp.vr = rv_p.v;
+    }
+    PrimBar<S::D> Bm, Bp, Bw;
+    zero_bar<S::D>(Bm);
+    zero_bar<S::D>(Bp);
+    zero_bar<S::D>(Bw);
+    flux_dir_vjp<S>(Pm, J, Fb, Bm);
+    flux_dir_vjp<S>(Pp, J, Fb, Bp);
+    // the wave speed of the active side, once per lane (the side is chosen
+    // per lane by selects, so the warp runs this without divergence)
+    {
+        const Prim<S::D, S::RAIN, double> Pa = m_active ? Pm : Pp;
+        wave_speed_vjp<S, J>(Pa, lb, Bw);
+    }
+    add_bar_if<S::D>(Bm, Bw, m_active);
+    add_bar_if<S::D>(Bp, Bw, !m_active);
 #pragma unroll
-        for (int k = 0; k < S::NTR; ++k) tb[k] = 0.0;
-        prim_to_inputs<S>(P, B, rvel, tb);
+    for (int k = 0; k < S::NTR; ++k) tmb[k] = tpb[k] = 0.0;
+    prim_to_inputs<S>(Pm, Bm, rv_m, tmb);
+    prim_to_inputs<S>(Pp, Bp, rv_p, tpb);
+    // the jump term: d[[U]]/dU^- = 1, d[[U]]/dU^+ = -1
 #pragma unroll
-        for (int f = 0; f < S::NF; ++f) tb[f] = ::fma(0.5 * lam * jsign, fhb[f], tb[f]);
+    for (int f = 0; f < S::NF; ++f) {
+        tmb[f] = ::fma(0.5 * lam, fhb[f], tmb[f]);
+        tpb[f] = ::fma(-0.5 * lam, fhb[f], tpb[f]);
     }
     if (nb >= 0) {
         // the + side is the neighbour's trace on its face (J, -s)
@@ -435,14 +465,21 @@ __global__ void __launch_bounds__(S::NT) k_adj_local(AdjArgs A) {
         for (int f = 0; f < S::NF; ++f) wv[f] = s_w[f * STR + t];
         source_vjp<S>(x, brd, brm, wv, M, A.rvs_tab, xbar);
     }
+    // face points in direction-major order (direction, element, side,
+    // point), so that the lanes of a warp mostly share the face direction
+    // and each direction-specialised body runs with full warps
+    constexpr int PER_J = S::EPB * 2 * S::NFP1;
     for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
-        const int el2 = item / (S::NFACE * S::NFP1);
-        const int rem = item - el2 * (S::NFACE * S::NFP1);
-        const int face = rem / S::NFP1;
-        const int q = rem - face * S::NFP1;
+        const int jd = item / PER_J;
+        const int r = item - jd * PER_J;
+        const int el2 = r / (2 * S::NFP1);
+        const int r2 = r - el2 * (2 * S::NFP1);
+        const int side = r2 / S::NFP1;
+        const int q = r2 - side * S::NFP1;
+        const int face = 2 * jd + side;
         const int e2 = blockIdx.x * S::EPB + el2;
         if (e2 >= ne) continue;
-        switch (face >> 1) {
+        switch (jd) {
             case 0: face_vjp<S, 0>(A, s_w, s_ta, el2, face, q, e2); break;
             case 1: face_vjp<S, 1>(A, s_w, s_ta, el2, face, q, e2); break;
             default: face_vjp<S, (S::D == 3 ? 2 : 1)>(A, s_w, s_ta, el2, face, q, e2); break;
