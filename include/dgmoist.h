@@ -307,7 +307,7 @@ typedef struct dg_stabilisation {
  * DG_ENOTIMPL while either term is on. */
 int dg_set_stabilisation(dg_ctx *ctx, const dg_stabilisation *s);
 
-/* ---- Batched ensemble (SURVEY NEXT-3 form; the paper runs one case at a time) ----
+/* ---- Batched ensemble (not in the paper, which runs one case at a time) ----
  * Many independent 2-D meshes (any sizes, orders 1..5, rain on or off),
  * FP32-bulk, advanced together: each SSPRK(4,3) stage is one persistent
  * launch whose CTAs take element tiles of any member from an atomic work

@@ -12,7 +12,7 @@ and none of the method's arithmetic.
 
 Everything is float64 numpy.  Each function cites the section / equation of
 the paper it follows.  Where the paper is silent or ambiguous the reading taken
-is stated in the docstring and listed in the design doc.
+is stated in the docstring.
 
 Modules
 -------

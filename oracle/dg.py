@@ -13,7 +13,7 @@ Lambda from Eq. (3.4).  Integrals use the (k+1)^d Gauss-Legendre product
 rule at the nodes ("direct" quadrature: the full N_p x N_p matrices of basis
 gradients, no sum factorisation), so M is diagonal: M_aa = W_a |K|/2^d.
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * derived fields T, rho_v and p' are solved at the nodes (Section 3.4) and
     their polynomial interpolants are evaluated on the faces (the L2
     projection onto Q^k of nodal values is the interpolant);

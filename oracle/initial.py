@@ -2,7 +2,7 @@
 
 The paper's own set-ups (Appendix B) use theta_e or relative-humidity
 profiles and external soundings; the synthetic workloads here use a simpler
-profile of the same kind (readings listed in the design doc):
+profile of the same kind:
 
 * Base state: constant dry potential temperature theta = T (p_ref/p)^(R_d/c_pd),
   total-water mixing ratio q_t(z) = q_t0 (1 - z/H) = rho_m / rho_d, pressure

@@ -10,9 +10,9 @@ same float32-rounded state.  Bars (both forms):
   * split: T to 1e-10 relative (perturbation form: 1e-8, float32 relative
     precision of the perturbation tau of a few K), rho_v to 1e-9 (1e-7) of
     rho_m, vapour never supersaturated by more than 1e-7 relative (the
-    north_star bar);
+    float32 form's accuracy target);
   * 100 SSPRK(4,3) steps of the 2-D bubble (and 20 of a 3-D rain case): relative
-    L2 difference per field <= 1e-5 (the benchmark spec bar).
+    L2 difference per field <= 1e-5 (the float32 form's accuracy target).
 """
 import numpy as np
 import pytest
