@@ -63,7 +63,7 @@ extern "C" {
 #define DG_ENOCONV (-4)  /* Newton split hit its iteration cap somewhere */
 #define DG_ENONPHYS (-5) /* non-physical or non-finite state (T, rho <= 0, NaN) */
 #define DG_ESTATE (-6)   /* call order: base state or state not set yet */
-#define DG_ENOTIMPL (-7) /* not available in this build */
+#define DG_ENOTIMPL (-7) /* not implemented for this configuration */
 
 #define DG_FP64 0
 #define DG_FP32_BULK 1

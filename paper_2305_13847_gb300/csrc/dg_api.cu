@@ -445,7 +445,7 @@ const char *dg_strerror(int code) {
         case DG_ENOCONV: return "Newton split did not converge at some node";
         case DG_ENONPHYS: return "non-physical or non-finite state";
         case DG_ESTATE: return "base state or state not set";
-        case DG_ENOTIMPL: return "not available in this build";
+        case DG_ENOTIMPL: return "not implemented for this configuration";
         default: return "unknown status";
     }
 }
