@@ -1699,11 +1699,17 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         // outward fluxes of the face pass, copied asynchronously since the start
         cp_async_wait_all();
     } else {
+        // face points in direction-major order (direction, element, side,
+        // point): the lanes of a warp mostly share the direction, so each
+        // direction-specialised face_point body runs with full warps
+        constexpr int PER_J = S::EPB * 2 * S::NFP1;
         for (int item = t; item < S::EPB * S::NFACE * S::NFP1; item += S::NT) {
-            const int el2 = item / (S::NFACE * S::NFP1);
-            const int rem = item - el2 * (S::NFACE * S::NFP1);
-            const int face = rem / S::NFP1;
-            const int q = rem - face * S::NFP1;
+            const int jd = item / PER_J;
+            const int r = item - jd * PER_J;
+            const int el2 = r / (2 * S::NFP1);
+            const int r2 = r - el2 * (2 * S::NFP1);
+            const int face = 2 * jd + r2 / S::NFP1;
+            const int q = r2 - (face & 1) * S::NFP1;
             const int e2 = bidx * S::EPB + el2;
             if (e2 >= ne) continue;
             const int nb = s_info[el2 * 16 + face], iz2 = s_info[el2 * 16 + 6];
