@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(kEnsThreads, MINB) k_ens_stage(const EnsMember
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ KArgs<float> s_args;
     __shared__ int s_item, s_k, s_rain;
+    // work queue, not a wait: every pass takes the next item from a counter
+    // that only grows, so a CTA leaves after at most n_items + 1 passes
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
         __syncthreads();
