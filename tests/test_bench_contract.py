@@ -53,3 +53,36 @@ def test_algorithmic_bytes_per_node():
     # write + read T, rho_v, p'
     assert bench.algorithmic_bytes_per_node(7, 8) == pytest.approx(174.0)
     assert bench.algorithmic_bytes_per_node(7, 4) == pytest.approx(87.0)
+
+
+def test_roofline_arithmetic():
+    """frac = achieved / peak with achieved = algorithmic bytes per launch over
+    the mean launch time; traffic is the profiled bytes per node scaled to the
+    mesh, and null for a configuration without a capture."""
+    sys.path.insert(0, ROOT)
+    import importlib
+    import types
+    bench = importlib.import_module("bench")
+    info = types.SimpleNamespace(n_fields=7, n_nodes=16_384_000, launches_per_stage=2)
+    t_total, steps, peak = 0.5, 10, 6705.5
+    r = bench._roofline(info, 8, t_total, steps, peak, "measured",
+                        bench._traffic({"dim": 3, "order": 4}, "fp64", info))
+    launch_s = t_total / (bench.STAGES * steps)
+    assert r["avg_launch_ms"] == pytest.approx(1000.0 * launch_s)
+    assert r["algorithmic_bytes_per_launch"] == pytest.approx(174.0 * info.n_nodes)
+    assert r["achieved"] == pytest.approx(174.0 * info.n_nodes / launch_s / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["traffic"] == pytest.approx(bench.PROFILED_TRAFFIC[(3, 4, "fp64")] * info.n_nodes)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    # no capture for this configuration, or the inline schedule: traffic null
+    assert bench._traffic({"dim": 2, "order": 3}, "fp64", info) is None
+    inline = types.SimpleNamespace(n_fields=7, n_nodes=10, launches_per_stage=1)
+    assert bench._traffic({"dim": 3, "order": 4}, "fp64", inline) is None
+
+
+def test_whole_job_rate_is_weak_scaling():
+    sys.path.insert(0, ROOT)
+    import importlib
+    bench = importlib.import_module("bench")
+    # every rank steps a full replica: twice the ranks, twice the work per time
+    assert bench.whole_job_rate(2, 100.0, 1.0) == 2 * bench.whole_job_rate(1, 100.0, 1.0)
