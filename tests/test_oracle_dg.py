@@ -3,8 +3,9 @@
 Free-stream preservation, preservation of a resting hydrostatic atmosphere
 (Section 4.4's round-off magnitudes), discrete conservation, the eigenvalue
 bound of Eq. (3.4), optimal k+1 convergence on an exact travelling solution
-(Section 4.1), the SSPRK(4,3) stability polynomial (Remark 3.1) and the
-degree-of-freedom counts printed in Section 4.3.
+(Section 4.1), the SSPRK(4,3) stability polynomial (Remark 3.1), third
+order in time of the full moist step (with a planted first-order step that
+the pin rejects) and the degree-of-freedom counts printed in Section 4.3.
 """
 import json
 import os
@@ -282,6 +283,53 @@ def test_ssprk43_third_order_nonlinear():
             y = dg.ssprk43_step(lambda v: -v * v, y, 1.0 / n)
         return abs(y[0] - 0.5)
     assert np.log2(solve(20) / solve(40)) == pytest.approx(3.0, abs=0.15)
+
+
+def test_full_step_converges_at_third_order_in_time():
+    """SSPRK(4,3) applied to the whole moist DG operator (Remark 3.1), not a
+    scalar ODE: on a fixed mesh, differences between runs to the same time
+    with dt, dt/2, dt/4 shrink by 2^3 = 8 per halving (9-10 before the
+    asymptotic range at these step sizes).  A stage combination of the
+    wrong order would give 4 (second) or 16 (fourth); one that is first
+    order, 2."""
+    prob, U0 = _moving_bubble()
+    ratios = _time_ratios(prob, U0)
+    assert all(6.5 < r < 12.0 for r in ratios), ratios
+
+
+def _moving_bubble():
+    """2-D Q2 warm bubble with a smooth horizontal wind and some rain, so
+    that every term of the operator moves."""
+    mesh = Mesh(2, (6, 4), (6e3, 4e3), 2, (True, False))
+    node, face, _ = initial.base_tables(mesh, H=4e3)
+    prob = dg.Problem(mesh, node, face, rain=True)
+    U0 = initial.bubble_state(prob, 2.0, [3e3, 0.8e3], [1.2e3, 0.8e3], H=4e3)
+    xs = mesh.node_coords()
+    U0[prob.i_m[0]] += 2.0 * np.sin(2 * np.pi * xs[0] / 6e3) * np.cos(np.pi * xs[1] / 4e3)
+    U0[prob.i_rr] = 1e-4 * (0.5 + 0.5 * np.sin(2 * np.pi * xs[0] / 6e3 + 1.0))
+    return prob, U0
+
+
+def _time_ratios(prob, U0):
+    dt0 = dg.cfl_dt(prob, U0, 0.05)
+    T = 4 * dt0
+    res = {n: dg.run(prob, U0, T / n, n) for n in (4, 8, 16)}
+    ratios = []
+    for f in range(prob.nf):
+        e1 = np.abs(res[4][f] - res[8][f]).max()
+        e2 = np.abs(res[8][f] - res[16][f]).max()
+        assert e2 > 1e-8 * np.abs(res[16][f]).max(), f        # above the split's tolerance
+        ratios.append(e1 / e2)
+    return ratios
+
+
+def test_time_convergence_pin_detects_a_first_order_step(monkeypatch):
+    """The measurement above, with a forward-Euler step planted in the oracle
+    in place of SSPRK(4,3): the ratios fall to about 2, outside the pin."""
+    prob, U0 = _moving_bubble()
+    monkeypatch.setattr(dg, "ssprk43_step", lambda L, U, dt: U + dt * L(U))
+    ratios = _time_ratios(prob, U0)
+    assert all(r < 3.0 for r in ratios), ratios
 
 
 def test_base_column_is_hydrostatic_and_matches_profile():
