@@ -1,0 +1,78 @@
+"""Planted mistakes: each one, planted in the oracle on the CPU, fails the pin
+that is meant to catch it.
+
+The pins of test_oracle_dg.py check the oracle against closed forms and
+invariants.  These controls show that plausible slips in the flux, the
+wave-speed bound or the sources do not pass them:
+
+* the pressure term p' of the momentum flux dropped: the flux Jacobian of
+  a frozen ideal-gas mixture no longer has spectral radius Lambda (Eq. (3.4));
+* the sound speed missing from Lambda: Lambda no longer bounds it;
+* the sign of the gravity work in the energy source flipped: E + rho g z is
+  no longer conserved (Eq. (2.11e));
+* the momentum carried by falling rain dropped (Eq. (2.1e)): the vertical
+  momentum flux no longer differs from the no-fall flux by u times the rain
+  mass flux.
+
+A third control, the forward-Euler step planted in place of SSPRK(4,3),
+sits beside its pin in test_oracle_dg.py.
+"""
+import numpy as np
+import pytest
+
+from oracle import dg
+from tests import test_oracle_dg as pins
+
+
+def test_dropped_pressure_flux_fails_the_spectral_radius_pin(monkeypatch):
+    orig = dg.physical_flux
+
+    def planted(prob, j, P):
+        F = orig(prob, j, P)
+        F[prob.i_m[j]] = F[prob.i_m[j]] - P["p_prime"]
+        return F
+
+    monkeypatch.setattr(dg, "physical_flux", planted)
+    with pytest.raises(AssertionError):
+        pins.test_lambda_bounds_flux_jacobian_eigenvalues("dry", 0)
+
+
+def test_lambda_without_sound_speed_fails_the_bound_pin(monkeypatch):
+    def planted(prob, j, P):
+        lam = np.abs(P["u"][j])
+        if j == prob.mesh.vert:
+            lam = lam + np.abs(P["v_r"])
+        return lam
+
+    monkeypatch.setattr(dg, "wave_speed", planted)
+    with pytest.raises(AssertionError):
+        pins.test_lambda_bounds_flux_jacobian_eigenvalues("moist_sat", 1)
+
+
+def test_flipped_gravity_work_fails_the_energy_pin(monkeypatch):
+    orig = dg.source
+
+    def planted(prob, Uf, P):
+        G = orig(prob, Uf, P)
+        G[prob.i_E] = -G[prob.i_E]
+        return G
+
+    monkeypatch.setattr(dg, "source", planted)
+    with pytest.raises(AssertionError):
+        pins.test_total_energy_with_potential_energy_conserved()
+
+
+def test_dropped_rain_momentum_fails_the_rain_flux_pin(monkeypatch):
+    orig = dg.physical_flux
+
+    def planted(prob, j, P):
+        F = orig(prob, j, P)
+        if j == prob.mesh.vert:
+            rvr = P["rho_r"] * P["v_r"]
+            for i in range(prob.mesh.dim):
+                F[prob.i_m[i]] = F[prob.i_m[i]] + rvr * P["u"][i]
+        return F
+
+    monkeypatch.setattr(dg, "physical_flux", planted)
+    with pytest.raises(AssertionError):
+        pins.test_rain_fluxes_carry_their_energy_and_momentum()
