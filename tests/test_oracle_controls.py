@@ -14,14 +14,22 @@ wave-speed bound or the sources do not pass them:
   momentum flux no longer differs from the no-fall flux by u times the rain
   mass flux.
 
-A third control, the forward-Euler step planted in place of SSPRK(4,3),
+and for the thermodynamics of test_oracle_thermo.py:
+
+* the exponent a = (c_pv - c_l)/R_v of Eq. (2.6) with the wrong sign:
+  e_s no longer solves Clausius-Clapeyron with the linear latent heat;
+* the cloud water's heat capacity dropped from the split's energy residual
+  (Eq. (2.8a)): the split no longer reproduces the internal energy.
+
+A further control, the forward-Euler step planted in place of SSPRK(4,3),
 sits beside its pin in test_oracle_dg.py.
 """
 import numpy as np
 import pytest
 
-from oracle import dg
+from oracle import dg, thermo
 from tests import test_oracle_dg as pins
+from tests import test_oracle_thermo as thermo_pins
 
 
 def test_dropped_pressure_flux_fails_the_spectral_radius_pin(monkeypatch):
@@ -76,3 +84,18 @@ def test_dropped_rain_momentum_fails_the_rain_flux_pin(monkeypatch):
     monkeypatch.setattr(dg, "physical_flux", planted)
     with pytest.raises(AssertionError):
         pins.test_rain_fluxes_carry_their_energy_and_momentum()
+
+
+def test_wrong_sign_of_es_exponent_fails_clausius_clapeyron(monkeypatch):
+    monkeypatch.setattr(thermo, "ES_A", -thermo.ES_A)
+    with pytest.raises(AssertionError):
+        thermo_pins.test_es_satisfies_clausius_clapeyron(290.0)
+
+
+def test_split_without_cloud_heat_capacity_fails_the_invariants(monkeypatch):
+    def planted(T, rho_d, rho_m, rho_r, rho_e, rho_v):
+        return thermo.internal_energy(rho_d, rho_v, 0.0 * rho_m, rho_r, T) - rho_e
+
+    monkeypatch.setattr(thermo, "_residual", planted)
+    with pytest.raises(AssertionError):
+        thermo_pins.test_split_invariants()
