@@ -21,6 +21,15 @@ and for the thermodynamics of test_oracle_thermo.py:
 * the cloud water's heat capacity dropped from the split's energy residual
   (Eq. (2.8a)): the split no longer reproduces the internal energy.
 
+and for the stabilisation of test_oracle_stabilisation.py (Section 3.5-3.6):
+
+* the sponge without its mass fix (the moisture removed not returned to
+  rho_d'): the density at a node is no longer kept;
+* the interior-penalty term lost (sigma -> 0 inside the form): the SIP
+  form is no longer positive semidefinite at sigma = 10;
+* the diffusion scaled by a wrong factor: its energy no longer converges to
+  alpha int |grad u|^2.
+
 A further control, the forward-Euler step planted in place of SSPRK(4,3),
 sits beside its pin in test_oracle_dg.py.
 """
@@ -28,7 +37,9 @@ import numpy as np
 import pytest
 
 from oracle import dg, thermo
+from oracle import stabilisation as st
 from tests import test_oracle_dg as pins
+from tests import test_oracle_stabilisation as stab_pins
 from tests import test_oracle_thermo as thermo_pins
 
 
@@ -99,3 +110,32 @@ def test_split_without_cloud_heat_capacity_fails_the_invariants(monkeypatch):
     monkeypatch.setattr(thermo, "_residual", planted)
     with pytest.raises(AssertionError):
         thermo_pins.test_split_invariants()
+
+
+def test_sponge_without_mass_fix_fails_the_sponge_pin(monkeypatch):
+    orig = st.apply_sponge
+
+    def planted(prob, U, z_d, alpha_s):
+        V = orig(prob, U, z_d, alpha_s)
+        V[prob.i_rd] = U[prob.i_rd]
+        return V
+
+    monkeypatch.setattr(st, "apply_sponge", planted)
+    with pytest.raises(AssertionError):
+        stab_pins.test_sponge_mass_fix_and_damping()
+
+
+def test_lost_penalty_fails_the_definiteness_pin(monkeypatch):
+    orig = st.diffusion_rhs
+    monkeypatch.setattr(st, "diffusion_rhs",
+                        lambda prob, U, aU, aR, sigma: orig(prob, U, aU, aR, 0.0))
+    with pytest.raises(AssertionError):
+        stab_pins.test_sip_matrix_symmetric_nullspace_and_definite(2, (True, False))
+
+
+def test_wrongly_scaled_diffusion_fails_the_laplacian_pin(monkeypatch):
+    orig = st.diffusion_rhs
+    monkeypatch.setattr(st, "diffusion_rhs",
+                        lambda prob, U, aU, aR, sigma: 2.0 * orig(prob, U, aU, aR, sigma))
+    with pytest.raises(AssertionError):
+        stab_pins.test_sip_converges_to_laplacian()
