@@ -30,6 +30,12 @@ and for the stabilisation of test_oracle_stabilisation.py (Section 3.5-3.6):
 * the diffusion scaled by a wrong factor: its energy no longer converges to
   alpha int |grad u|^2.
 
+and for the complex-step tangent that the adjoint's tests compare with:
+
+* |x| taken as the complex modulus (np.abs) instead of by the sign of the
+  real part: the imaginary part is lost and the tangent no longer matches
+  central differences.
+
 A further control, the forward-Euler step planted in place of SSPRK(4,3),
 sits beside its pin in test_oracle_dg.py.
 """
@@ -139,3 +145,9 @@ def test_wrongly_scaled_diffusion_fails_the_laplacian_pin(monkeypatch):
                         lambda prob, U, aU, aR, sigma: 2.0 * orig(prob, U, aU, aR, sigma))
     with pytest.raises(AssertionError):
         stab_pins.test_sip_converges_to_laplacian()
+
+
+def test_modulus_for_abs_fails_the_complex_step_pin(monkeypatch):
+    monkeypatch.setattr(dg, "_abs", np.abs)
+    with pytest.raises(AssertionError):
+        pins.test_complex_step_tangent_matches_central_differences()
