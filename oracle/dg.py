@@ -237,6 +237,15 @@ def rhs(prob, U, elements=None, return_stats=False):
 
     U: array (n_f, Ne, Np).  ``elements`` restricts the evaluation to a subset
     (the neighbours' states are still read).  Returns (n_f, len(elements), Np).
+
+    With ``return_stats`` also a dict: ``n_unconverged`` (split nodes whose
+    Newton iteration hit its cap) and ``wall_water_outflow``, the water
+    (rho_m + rho_r) leaving the domain per unit time through the walls of the
+    selected elements: the integral over wall faces of the outward
+    Lax-Friedrichs flux of the two water densities, sum_q Wf_q J_F Fhat(q),
+    J_F = prod_{i != j} h_i / 2 (the face term of Eq. (3.3) with test function
+    1).  Interior faces cancel and the microphysics moves water between rho_m
+    and rho_r only, so the total water changes by exactly minus this flux.
     """
     mesh = prob.mesh
     d = mesh.dim
@@ -270,8 +279,11 @@ def rhs(prob, U, elements=None, return_stats=False):
             R[f] += (2.0 / mesh.h[j]) * ((F[f] * W[None, :]) @ ref.G[j]) / W[None, :]
 
     # face terms: -(1 / (W_a J)) sum_q Wf_q J_F Fhat_out(q) phi_a(q), J_F / J = 2 / h_j
+    water = [prob.i_rm] + ([prob.i_rr] if prob.rain else [])
+    outflow = 0.0
     for j in range(d):
         Wf = ref.Wf[j]
+        JF = float(np.prod([mesh.h[i] / 2.0 for i in range(d) if i != j]))
         for s in (-1, 1):
             B_in = ref.B[(j, s)]
             B_out = ref.B[(j, -s)]
@@ -313,13 +325,15 @@ def rhs(prob, U, elements=None, return_stats=False):
             for f in range(prob.nf):
                 fhat = 0.5 * s * (Fm[f] + Fp[f]) + 0.5 * lam * (Um[f] - Up[f])
                 R[f] -= (2.0 / mesh.h[j]) * ((fhat * Wf[None, :]) @ B_in) / W[None, :]
+                if f in water and wall.any():
+                    outflow += JF * np.sum(fhat[wall] * Wf[None, :])
 
     G = source(prob, Uf, P)
     for f in range(prob.nf):
         R[f] += G[f]
     out = np.stack(R)
     if return_stats:
-        return out, {"n_unconverged": n_bad}
+        return out, {"n_unconverged": n_bad, "wall_water_outflow": outflow}
     return out
 
 
@@ -343,6 +357,32 @@ def run(prob, U, dt, nsteps):
     for _ in range(nsteps):
         U = ssprk43_step(lambda V: rhs(prob, V), U, dt)
     return U
+
+
+def run_with_fallout(prob, U, dt, nsteps, fallout=0.0):
+    """nsteps SSPRK(4,3) steps as ``run``, and the fall-out: the water that
+    has left through the walls (rain falling out at the bottom, Section 4's
+    rain examples; minus the rain the mirrored ghost state lets in at the
+    top).  It is advanced as one more unknown F with dF/dt equal to the wall
+    outflow of ``rhs``, by the same Shu-Osher stages as the state, so that
+    sum M (rho_m' + rho_r') + F stays constant to rounding (Section 3.6's
+    mass conservation with the boundary flux accounted for).
+    Returns (U, F)."""
+    def L(V):
+        R, st = rhs(prob, V, return_stats=True)
+        return R, st["wall_water_outflow"]
+    F = float(fallout)
+    for _ in range(nsteps):
+        r0, w0 = L(U)
+        u1, f1 = U + 0.5 * dt * r0, F + 0.5 * dt * w0
+        r1, w1 = L(u1)
+        u2, f2 = u1 + 0.5 * dt * r1, f1 + 0.5 * dt * w1
+        r2, w2 = L(u2)
+        u3 = (2.0 / 3.0) * U + (1.0 / 3.0) * u2 + (dt / 6.0) * r2
+        f3 = (2.0 / 3.0) * F + (1.0 / 3.0) * f2 + (dt / 6.0) * w2
+        r3, w3 = L(u3)
+        U, F = u3 + 0.5 * dt * r3, f3 + 0.5 * dt * w3
+    return U, F
 
 
 def max_wave_speed(prob, U):

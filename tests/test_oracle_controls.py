@@ -151,3 +151,43 @@ def test_modulus_for_abs_fails_the_complex_step_pin(monkeypatch):
     monkeypatch.setattr(dg, "_abs", np.abs)
     with pytest.raises(AssertionError):
         pins.test_complex_step_tangent_matches_central_differences()
+
+
+def test_fallout_with_a_wrong_face_jacobian_fails_the_water_budget_pin(monkeypatch):
+    """The wall outflow integrated with the element Jacobian |K|/2^d instead
+    of the face's |F|/2^(d-1) (a factor h_j/2 off): the water in the domain
+    plus the fall-out is no longer constant."""
+    orig = dg.rhs
+
+    def planted(prob, U, elements=None, return_stats=False):
+        out = orig(prob, U, elements, return_stats)
+        if return_stats:
+            R, stats = out
+            stats = dict(stats, wall_water_outflow=stats["wall_water_outflow"] * prob.mesh.h[-1] / 2.0)
+            return R, stats
+        return out
+
+    monkeypatch.setattr(dg, "rhs", planted)
+    with pytest.raises(AssertionError):
+        pins.test_water_budget_closes_with_the_fallout()
+
+
+def test_fallout_advanced_by_the_stage_weights_fails_the_water_budget_pin(monkeypatch):
+    """The fall-out accumulated with the stage weights of the Shu-Osher form
+    (dt/2, dt/2, dt/6, dt/2 on the four outflows) instead of their weights in
+    u^{n+1} once the stages are expanded: the budget no longer closes."""
+    def planted(prob, U, dt, nsteps, fallout=0.0):
+        F = float(fallout)
+        for _ in range(nsteps):
+            stages = []
+            def L(V):
+                R, st = dg.rhs(prob, V, return_stats=True)
+                stages.append(st["wall_water_outflow"])
+                return R
+            U = dg.ssprk43_step(L, U, dt)
+            F += dt * (0.5 * stages[0] + 0.5 * stages[1] + stages[2] / 6.0 + 0.5 * stages[3])
+        return U, F
+
+    monkeypatch.setattr(dg, "run_with_fallout", planted)
+    with pytest.raises(AssertionError):
+        pins.test_water_budget_closes_with_the_fallout()

@@ -456,3 +456,39 @@ def test_warm_bubble_rises():
     far = np.abs(xs[0] - w["centre"][0]) > 6.0e3
     assert U[prob.i_m[1]][near].min() > 0.05
     assert np.abs(U[prob.i_m[1]][far]).max() < 1e-3
+
+
+def _falling_rain_walls():
+    """2-D Q2 warm-rain case with walls on every side and rain in the lowest
+    kilometre, so that rain leaves through the bottom wall at once."""
+    mesh = Mesh(2, (5, 4), (5e3, 4e3), 2, (False, False))
+    node, face, _ = initial.base_tables(mesh, H=4e3)
+    prob = dg.Problem(mesh, node, face, rain=True)
+    U0 = initial.bubble_state(prob, 2.0, [2.5e3, 1.5e3], [1.2e3, 0.8e3], H=4e3)
+    xs = mesh.node_coords()
+    U0[prob.i_m[0]] += 1.5 * np.sin(np.pi * xs[0] / 5e3) * np.sin(np.pi * xs[1] / 4e3)
+    U0[prob.i_rr] = 1e-3 * np.exp(-(xs[1] / 1e3) ** 2) * (0.6 + 0.4 * np.cos(2 * np.pi * xs[0] / 5e3))
+    return prob, U0
+
+
+def water_total(prob, U):
+    """sum M (rho_m_bar + rho_m' + rho_r'): all the water in the domain."""
+    lev = prob.mesh.node_level_index()
+    return dg.mass_integral(prob, prob.base_node["rho_m"][lev] + U[prob.i_rm] + U[prob.i_rr])
+
+
+def test_water_budget_closes_with_the_fallout():
+    """Walls on every side: the water in the domain plus the fall-out (the
+    time integral of the outward water flux through the walls, advanced by
+    the same SSPRK(4,3) stages) stays constant to rounding over 10 steps,
+    while the fall-out itself grows to a sizeable share of the rain."""
+    prob, U0 = _falling_rain_walls()
+    dt = dg.cfl_dt(prob, U0, 0.05)
+    W0 = water_total(prob, U0)
+    U, F = dg.run_with_fallout(prob, U0, dt, 10)
+    rain0 = dg.mass_integral(prob, U0[prob.i_rr])
+    assert F > 1e-3 * rain0
+    assert abs(water_total(prob, U) + F - W0) <= 1e-13 * W0
+    assert abs(water_total(prob, U) + F - W0) <= 1e-8 * F
+    # the state itself is that of the plain run
+    assert np.array_equal(U, dg.run(prob, U0, dt, 10))
