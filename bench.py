@@ -152,6 +152,209 @@ def oracle_sample_rate(repeats):
     return s.dofs * repeats / sec, sec, s.desc + ", %d repeats" % repeats
 
 
+# ---------------------------------------------------------------------------
+# the oracle on all host cores: worker processes (spawn) over element blocks,
+# the state in shared memory; each worker evaluates the oracle's rhs on its
+# own block exactly as the single-core sample does
+# ---------------------------------------------------------------------------
+_WORKER = {}
+
+
+def _problem_from(spec):
+    from oracle import dg, initial
+    from oracle.mesh import Mesh
+    mesh = Mesh(spec["dim"], spec["n"], spec["L"], spec["order"], spec["periodic"])
+    node, face, _ = initial.base_tables(mesh, H=spec["L"][-1])
+    return dg.Problem(mesh, node, face, rain=spec["rain"])
+
+
+def _pool_init(spec, names, shape, blocks):
+    from multiprocessing import shared_memory
+    from oracle import dg
+    _WORKER["dg"] = dg
+    _WORKER["prob"] = _problem_from(spec)
+    _WORKER["shm"] = [shared_memory.SharedMemory(name=n) for n in names]
+    _WORKER["U"] = np.ndarray(shape, dtype=np.float64, buffer=_WORKER["shm"][0].buf)
+    _WORKER["R"] = np.ndarray(shape, dtype=np.float64, buffer=_WORKER["shm"][1].buf)
+    _WORKER["blocks"] = blocks
+
+
+def _pool_rhs(b):
+    blk = _WORKER["blocks"][b]
+    _WORKER["R"][:, blk] = _WORKER["dg"].rhs(_WORKER["prob"], _WORKER["U"], elements=blk)
+    return b
+
+
+class OraclePool:
+    """The oracle's rhs evaluated by `workers` spawned processes, one element
+    block each (blocks: list of element index arrays covering what is needed)."""
+
+    def __init__(self, spec, shape, blocks, workers):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        nbytes = int(np.prod(shape)) * 8
+        self.shm = [shared_memory.SharedMemory(create=True, size=nbytes) for _ in range(2)]
+        self.U = np.ndarray(shape, dtype=np.float64, buffer=self.shm[0].buf)
+        self.R = np.ndarray(shape, dtype=np.float64, buffer=self.shm[1].buf)
+        self.nblocks = len(blocks)
+        self.pool = mp.get_context("spawn").Pool(
+            workers, initializer=_pool_init,
+            initargs=(spec, [m.name for m in self.shm], shape, blocks))
+
+    def rhs(self, U):
+        self.U[...] = U
+        self.pool.map(_pool_rhs, range(self.nblocks), chunksize=1)
+        return self.R.copy()
+
+    def rhs_in_place(self):
+        """rhs of the blocks of the state already in self.U, into self.R."""
+        self.pool.map(_pool_rhs, range(self.nblocks), chunksize=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for m in self.shm:
+            m.close()
+            m.unlink()
+
+
+def _host_cpu():
+    """CPU model and usable core count of this host (lscpu / os)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return model, len(os.sched_getaffinity(0))
+
+
+# the float32 forms' error against the float64 oracle: the precision form's
+# set-up (3-D warm rain, Q3, white noise) on a 16 x 16 x 8 mesh, 200 steps
+ERR_MESH = (16, 16, 8)
+ERR_STEPS = 200
+
+
+def cpu_leg_main(tmpdir):
+    """Child process of the GB300 arm, on the host cores while the GPU legs run.
+
+    1. Inputs of the error case from the oracle's own set-up (base tables,
+       bubble with the workload's noise, float32-rounded; dt from CFL 0.05)
+       -> inputs.npz, which the GPU legs read.
+    2. 200 oracle steps on all host cores (OraclePool).
+    3. The oracle's rhs + stage update on all host cores: 16 of the
+       single-core baseline's 4 x 4 x 32 column blocks, one per process.
+    4. Waits for the GPU's final states (gpu.npz) and compares them.
+    Prints one JSON line."""
+    from oracle import dg, initial
+    from paper_2305_13847_gb300 import inputs
+    out = {}
+    model, cores = _host_cpu()
+    workers = max(1, cores - 1)
+    out["host_cpu"] = {"model": model, "cores": cores}
+    w = inputs.workload("rain3d_q3_fp32", n=ERR_MESH)
+    spec = {k: w[k] for k in ("dim", "n", "L", "order", "periodic", "rain")}
+    prob = _problem_from(spec)
+    mesh = prob.mesh
+    noise = inputs.node_noise(w, mesh.Ne, mesh.Np)
+    U0 = initial.bubble_state(prob, w["A"], w["centre"], w["radius"], noise=noise, H=w["H"])
+    U0 = U0.astype(np.float32).astype(np.float64)
+    dt = dg.cfl_dt(prob, U0, w["cfl"])
+    keys = ("rho_d", "rho_m", "E", "p")
+    tmp = os.path.join(tmpdir, "inputs.tmp.npz")
+    np.savez(tmp, U0=U0, node=np.stack([prob.base_node[k] for k in keys]),
+             face=np.stack([prob.base_face[k] for k in keys]), dt=dt, steps=ERR_STEPS)
+    os.replace(tmp, os.path.join(tmpdir, "inputs.npz"))
+
+    t0 = time.perf_counter()
+    pool = OraclePool(spec, U0.shape, column_tiles(mesh, 4, 4), workers)
+    try:
+        U = U0
+        for _ in range(ERR_STEPS):
+            U = dg.ssprk43_step(pool.rhs, U, dt)
+    finally:
+        pool.close()
+    out["oracle_run"] = {"mesh": "x".join(map(str, ERR_MESH)), "steps": ERR_STEPS, "dt": dt,
+                         "workers": workers, "seconds": time.perf_counter() - t0}
+
+    # all-cores oracle throughput on the single-core baseline's sample shape
+    try:
+        out["oracle_all_cores"] = oracle_all_cores_rate(workers)
+    except Exception as e:  # reported, not hidden
+        out["oracle_all_cores"] = {"error": "%s: %s" % (type(e).__name__, str(e)[:200])}
+
+    gpu = os.path.join(tmpdir, "gpu.npz")
+    t_wait = time.time()
+    while not os.path.exists(gpu) and time.time() - t_wait < 900:
+        time.sleep(1.0)
+    if os.path.exists(gpu):
+        g = np.load(gpu)
+        names = dg.field_names(3, True)
+        for form in ("fp32_bulk", "fp32_pert"):
+            if form not in g:
+                continue
+            Ug = g[form].astype(np.float64)
+            rel = [float(np.linalg.norm(Ug[f] - U[f]) / np.linalg.norm(U[f])) for f in range(prob.nf)]
+            out[form] = {"rel_l2": dict(zip(names, rel)), "rel_l2_max": max(rel)}
+    else:
+        out["error"] = "no GPU result within 900 s"
+    print(json.dumps(out))
+
+
+def column_tiles(mesh, tx, ty):
+    """Element index arrays of tx x ty element columns (all vertical layers):
+    a block's neighbours are then only its horizontal ring."""
+    nx, ny, nz = mesh.n
+    tiles = []
+    for by in range(0, ny, ty):
+        for bx in range(0, nx, tx):
+            blk = [mesh.elem_index([np.array(ix), np.array(iy), np.array(iz)])
+                   for iz in range(nz) for iy in range(by, min(by + ty, ny))
+                   for ix in range(bx, min(bx + tx, nx))]
+            tiles.append(np.array(blk, dtype=np.int64).ravel())
+    return tiles
+
+
+def oracle_all_cores_rate(workers, repeats=4):
+    """RHS + stage update of the oracle on `workers` column blocks of 4 x 4 x 32
+    elements of the 64 x 64 x 32 Q4 workload, one block per process, all at
+    once: the all-cores counterpart of the single-core baseline."""
+    from oracle.mesh import Mesh  # noqa: F401  (the workers import the oracle themselves)
+    s = OracleSample()
+    mesh = s.prob.mesh
+    nx, ny = SAMPLE_COLUMNS
+    per_row = mesh.n[0] // nx
+    blocks = []
+    for b in range(workers):
+        bx, by = (b % per_row) * nx, (b // per_row) * ny
+        blk = [mesh.elem_index([np.array(ix), np.array(iy), np.array(iz)])
+               for iz in range(mesh.n[2]) for iy in range(by, by + ny) for ix in range(bx, bx + nx)]
+        blocks.append(np.array(blk, dtype=np.int64).ravel())
+    w = s.prob
+    spec = {"dim": w.mesh.dim, "n": w.mesh.n, "L": w.mesh.L, "order": w.mesh.k,
+            "periodic": w.mesh.periodic, "rain": w.rain}
+    pool = OraclePool(spec, s.U.shape, blocks, workers)
+    try:
+        pool.U[...] = s.U
+        pool.rhs_in_place()                             # warm-up: workers built, caches filled
+        t0 = time.perf_counter()
+        for _ in range(repeats):
+            pool.rhs_in_place()
+            for blk in blocks:
+                pool.U[:, blk] = pool.U[:, blk] + 0.01 * pool.R[:, blk]
+        sec = time.perf_counter() - t0
+    finally:
+        pool.close()
+    dofs = sum(b.size for b in blocks) * mesh.Np * s.prob.nf
+    return {"value": dofs * repeats / sec, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": "%d column blocks of 4x4x32 elements (%d DOFs) of the 64x64x32 Q4 mesh, one "
+                      "process each, %d x (RHS + stage update) (%.1f s)"
+                      % (workers, dofs, repeats, sec)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -230,7 +433,7 @@ def _measure(torch, dm, ctx, info, dt, steps, warmup, stream, barrier, dist):
     return max_over_ranks(torch, dist, total_ms, "cuda") / 1000.0, step_ms
 
 
-FACES = {"auto": 0, "inline": 1, "pass": 2}
+FACES = {"auto": 0, "inline": 1, "pass": 2, "column": 3}
 
 
 def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto"):
@@ -274,6 +477,80 @@ def _roofline(info, word, t_total, steps, peak, peak_kind, traffic=None):
             "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": 1000.0 * launch_s}
+
+
+# GB300 float64: 2 FMA per SM and clock.  The nominal 1.25 TFLOP/s of the
+# part is 152 SMs x 2.07 GHz x 2 FMA x 2 flop = 1.259 TFLOP/s.
+FP64_FMA_PER_SM_CLK = 2
+
+
+def fp64_flops_per_node(dim, order, nf, rain):
+    """Algorithmic float64 operations per node and SSPRK stage of the
+    sum-factorised DG stage (fma = 2, any other operation 1, a transcendental
+    or a division 1).  Items follow the method's formulas; the face terms
+    are per face point times d / (k + 1) face points per node."""
+    P, d, R = order + 1, dim, 1 if rain else 0
+    ntr_faces = d * (nf + 2) + R                 # traced fields summed over the d directions
+    items = {
+        # Eq. (3.2): d n_f contractions of length k+1 at every node
+        "volume": 2 * d * nf * P,
+        # face term of Eq. (3.3): two faces per direction, n_f fmas each
+        "lift": 4 * d * nf,
+        # traces of U, rho_v, p' (and T on horizontal faces with rain): k+1 fmas
+        # per face value, 2d face values per node
+        "traces": 4 * ntr_faces,
+        # Eq. (2.11) at the node: totals, u, p, E + p; d directions; rain terms
+        "nodal_flux": (6 + d) + d * (4 + R + d) + R * (8 + 4 * d),
+        # gravity; Eq. (2.4) with rho_r^(1/16) powers and v_r
+        "sources": 4 + R * 26,
+        # Eq. (2.8): rho e, T_u, rho_vs(T) (exp, log), one Newton step, p'
+        "split": 2 * d + 49,
+        # Section 3.2: both sides' flux and wave speed, LF per field, per face point
+        "face_flux": (2 * (6 + d + 4 + R + d + 16 + 5 * R) + 1 + 5 * nf + 2 * R * (8 + 4 * d) / d)
+                     * d / P,
+        # Remark 3.1: beta u + gdt R (+ alpha U^n on one stage in four)
+        "stage_update": 3.5 * nf,
+    }
+    return float(sum(items.values())), items
+
+
+def fp64_alu_roofline(info, w, t_total, steps, sm_count, sm_mhz, probe_tflops, hbm, traffic):
+    launch_s = t_total / (STAGES * steps)
+    fpn, items = fp64_flops_per_node(w["dim"], w["order"], info.n_fields, w["rain"])
+    achieved = fpn * info.n_nodes / launch_s / 1e12
+    peak = sm_count * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+    out = {"bound": "alu", "kernel": hbm["kernel"], "achieved": achieved, "peak": peak,
+           "unit": "TFLOP/s", "frac": achieved / peak,
+           "peak_kind": "derived: %d SMs x %d FP64 FMA/clk x 2 flop x %.0f MHz (median SM clock "
+                        "sampled in the timed region)" % (sm_count, FP64_FMA_PER_SM_CLK, sm_mhz),
+           "traffic": traffic, "algorithmic_flops_per_node": fpn,
+           "flops_per_node_items": items, "avg_launch_ms": 1000.0 * launch_s,
+           "hbm": {k: hbm[k] for k in ("achieved", "peak", "peak_kind", "unit", "frac",
+                                       "algorithmic_bytes_per_launch")}}
+    if probe_tflops:
+        out["fp64_fma_probe"] = {"tflops": probe_tflops, "frac_of_probe": achieved / probe_tflops}
+    return out
+
+
+def measure_fp64_probe(torch, dm, stream, sm_count, repeats=5):
+    """Float64 FMA rate of the device: the library's probe kernel (8 CTAs of
+    256 threads per SM, 8 independent fma chains per thread), CUDA events on
+    the launching stream, best of `repeats`."""
+    blocks = sm_count * 8
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    iters = 8000
+    dm.dg_fp64_fma_probe(out, blocks, iters, stream)
+    best = None
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = dm.dg_fp64_fma_probe(out, blocks, iters, stream)
+        e1.record(stream)
+        e1.synchronize()
+        rate = flops / (e0.elapsed_time(e1) / 1000.0) / 1e12
+        best = rate if best is None else max(best, rate)
+    assert torch.isfinite(out).all()
+    return best
 
 
 def measure_ensemble(torch, dm, inputs, args, world, dist):
@@ -345,6 +622,90 @@ def measure_adjoint(torch, dm, inputs, workloads, stream, steps):
         dm.dg_free(ctx)
 
 
+def _wait_for(path, seconds):
+    t0 = time.time()
+    while not os.path.exists(path):
+        if time.time() - t0 > seconds:
+            raise TimeoutError("%s not written within %d s" % (os.path.basename(path), seconds))
+        time.sleep(0.5)
+
+
+def gpu_error_case(torch, dm, tmpdir, stream):
+    """The float32 forms on the error case (16 x 16 x 8 Q3, 200 steps) from
+    the inputs the CPU leg wrote; their final states go to gpu.npz for the
+    comparison with the oracle there.  Returns each form's largest
+    supersaturation (dg_reduce, the split's float64 T and rho_v)."""
+    path = os.path.join(tmpdir, "inputs.npz")
+    _wait_for(path, 600)
+    d = np.load(path)
+    U0, dt, steps = d["U0"], float(d["dt"]), int(d["steps"])
+    res, states = {}, {}
+    for form, code in (("fp32_bulk", dm.DG_FP32_BULK), ("fp32_pert", dm.DG_FP32_PERT)):
+        cfg = dm.make_config(3, ERR_MESH, (20.0e3, 20.0e3, 10.0e3), 3, 3, 1, code)
+        ctx = dm.dg_init_mesh(cfg, stream)
+        try:
+            dm.dg_set_base_state(ctx, d["node"], d["face"])
+            dm.dg_set_state(ctx, np.ascontiguousarray(U0.astype(np.float32)), dm.DG_HOST)
+            dm.dg_step(ctx, dt, steps)
+            Ug = np.empty(U0.shape, dtype=np.float32)
+            dm.dg_get_state(ctx, Ug, dm.DG_HOST)
+            states[form] = Ug
+            res[form] = {"max_supersaturation": float(dm.dg_reduce(ctx)[6])}
+        finally:
+            dm.dg_free(ctx)
+    tmp = os.path.join(tmpdir, "gpu.tmp.npz")
+    np.savez(tmp, **states)
+    os.replace(tmp, os.path.join(tmpdir, "gpu.npz"))
+    return res
+
+
+def gpu_fp32_vs_fp64_fullsize(torch, dm, workloads, inputs, stream, steps):
+    """The precision workload at full size (128 x 128 x 64 Q3): each float32
+    form and the float64 form stepped `steps` steps from the same
+    float32-rounded initial state; relative L2 difference per field over every
+    8th element in each direction (16 x 16 x 8 sampled elements)."""
+    w = inputs.workload("rain3d_q3_fp32")
+    ref_ctx = workloads.open_workload(w, stream=stream, precision="fp32_bulk")
+    out = {}
+    try:
+        info = dm.dg_get_info(ref_ctx)
+        shape = (info.n_fields, info.n_elem, info.nodes_per_elem)
+        U32 = torch.empty(shape, dtype=torch.float32, device="cuda")
+        dm.dg_get_state(ref_ctx, U32, dm.DG_DEVICE)
+        lam = dm.dg_reduce(ref_ctx)[5]
+        dt = w["cfl"] * min(L / n for L, n in zip(w["L"], w["n"])) / lam
+        nx, ny, nz = w["n"]
+        ix, iy, iz = np.meshgrid(np.arange(0, nx, 8), np.arange(0, ny, 8), np.arange(0, nz, 8),
+                                 indexing="ij")
+        sel = torch.from_numpy((ix + nx * (iy + ny * iz)).ravel()).cuda()
+
+        def run(form, state):
+            # the context's own set-up builds the same base state (no noise:
+            # the state is replaced by the shared initial state)
+            ctx = workloads.open_workload(w, stream=stream, precision=form, with_noise=False)
+            try:
+                dm.dg_set_state(ctx, state, dm.DG_DEVICE)
+                dm.dg_step(ctx, dt, steps)
+                Uo = torch.empty_like(state)
+                dm.dg_get_state(ctx, Uo, dm.DG_DEVICE)
+                return Uo[:, sel].double().cpu().numpy()
+            finally:
+                dm.dg_free(ctx)
+
+        ref = run("fp64", U32.double())
+        for form in ("fp32_bulk", "fp32_pert"):
+            got = run(form, U32.clone())
+            rel = [float(np.linalg.norm(got[f] - ref[f]) / np.linalg.norm(ref[f]))
+                   for f in range(info.n_fields)]
+            out[form] = {"rel_l2_max": max(rel), "rel_l2": rel}
+        out["steps"] = steps
+        out["dt"] = dt
+        out["sample"] = "every 8th element per direction (%d elements)" % sel.numel()
+    finally:
+        dm.dg_free(ref_ctx)
+    return out
+
+
 def run_gb300(args):
     import torch
     from paper_2305_13847_gb300 import dgmoist as dm
@@ -366,6 +727,19 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
     peak, peak_kind = measured_peaks()
     word = 4 if args.precision.startswith("fp32") else 8
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+
+    # the CPU leg (the oracle on the host cores: the float32 forms' error
+    # case and the all-cores oracle rate) runs beside the GPU legs
+    cpu_leg, tmpdir = None, None
+    if rank == 0 and not args.no_error_legs and args.workload == WORKLOAD and args.precision == "fp64":
+        import tempfile
+        tmpdir = tempfile.mkdtemp(prefix="dgbench_")
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        cpu_leg = subprocess.Popen([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-leg", tmpdir],
+                                   stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
+                                   cwd=ROOT)
     w, ctx, info, dt = _open(dm, workloads, inputs, args.workload, args.precision, stream, args.mesh,
                              args.faces)
 
@@ -398,10 +772,16 @@ def run_gb300(args):
     roof = _roofline(info, word, t_max, args.steps, peak, peak_kind,
                      _traffic(w, args.precision, info))
     if args.precision == "fp64":
-        # the float64 form is bound by the FP64 pipe, not by HBM: ncu's pipe
-        # utilisation of the two kernels of a stage (32x32x32 Q4 capture)
-        roof["fp64_pipe"] = {"bound": "alu", "k_stage": 0.909, "k_face": 0.848,
-                             "source": "ncu sm__inst_executed_pipe_fp64, 32x32x32 Q4 capture"}
+        # the float64 form is bound by the FP64 pipe (GB300 runs float64 at
+        # ~1/60 of the float32 rate), not by HBM: its roofline is the FP64
+        # rate; the HBM fraction stays in roofline.hbm
+        try:
+            probe = measure_fp64_probe(torch, dm, stream, sm_count)
+        except Exception:
+            probe = None
+        sm_mhz = clocks.get("sm_mhz") or 2070.0
+        roof = fp64_alu_roofline(info, w, t_max, args.steps, sm_count, sm_mhz, probe, roof,
+                                 roof["traffic"])
     dm.dg_free(ctx)
     del host
 
@@ -441,6 +821,15 @@ def run_gb300(args):
                                       ("fp32_pert", "rain3d_q3_fp32", None, "fp32_pert")):
             guarded(key, lambda: measure_form(name, mesh, form))
 
+    # the float32 forms' error against float64: (i) on the 16 x 16 x 8 mesh
+    # against the oracle (the comparison happens in the CPU leg), (ii) at full
+    # size against the library's float64 form on sampled elements
+    err_gpu = {}
+    if cpu_leg is not None:
+        guarded("_err_i", lambda: err_gpu.update(gpu_error_case(torch, dm, tmpdir, stream)))
+        guarded("_err_ii", lambda: gpu_fp32_vs_fp64_fullsize(torch, dm, workloads, inputs, stream,
+                                                             ERR_STEPS))
+
     # the float64 step with the paper's stabilisation: artificial diffusion
     # (gamma 0.06 as in the paper's 2-D rain example, sigma 10) and a sponge in
     # the top quarter (alpha 0.1).  The 3-D example's gamma 0.6 (Q2, h = 100 m)
@@ -477,6 +866,38 @@ def run_gb300(args):
     if not args.no_ensemble:
         guarded("ensemble", lambda: measure_ensemble(torch, dm, inputs, args, world, dist))
 
+    # collect the CPU leg and file the error figures under their forms
+    cpu_out = {}
+    if cpu_leg is not None:
+        so, se = "", ""
+        try:
+            so, se = cpu_leg.communicate(timeout=1200)
+            cpu_out = json.loads(so.strip().splitlines()[-1])
+        except Exception as e:  # reported, not hidden
+            if cpu_leg.poll() is None:
+                cpu_leg.kill()
+            cpu_out = {"error": "CPU leg failed: %s; %s" % (str(e)[:200], (se or "")[-300:])}
+        finally:
+            import shutil
+            shutil.rmtree(tmpdir, ignore_errors=True)
+        full = extra.pop("_err_ii", {})
+        extra.pop("_err_i", None)
+        for form in ("fp32_bulk", "fp32_pert"):
+            if form not in extra or "error" in extra[form]:
+                continue
+            e = {"target": "rel L2 <= 1e-5 per field, supersaturation <= 1e-7 relative"}
+            if form in cpu_out:
+                e["vs_fp64_oracle_16x16x8"] = dict(cpu_out[form], steps=ERR_STEPS,
+                                                   **err_gpu.get(form, {}))
+            if form in full:
+                e["vs_fp64_gpu_fullsize_sampled"] = dict(full[form], steps=full["steps"],
+                                                         sample=full["sample"])
+            elif "error" in full:
+                e["vs_fp64_gpu_fullsize_sampled"] = full
+            if "error" in cpu_out:
+                e["vs_fp64_oracle_16x16x8"] = {"error": cpu_out["error"]}
+            extra[form]["error_vs_fp64"] = e
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -504,6 +925,12 @@ def run_gb300(args):
         line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_subprocess()
+            if "host_cpu" in cpu_out:
+                line["cpu_baseline"]["host_cpu"] = cpu_out["host_cpu"]
+            if "oracle_all_cores" in cpu_out:
+                line["cpu_baseline"]["all_cores"] = cpu_out["oracle_all_cores"]
+        if "oracle_run" in cpu_out:
+            line["oracle_error_run"] = cpu_out["oracle_run"]
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -532,7 +959,13 @@ def main():
                     help="override the element counts, e.g. 40,40,20 (profiling runs only)")
     ap.add_argument("--ensemble-members", type=int, default=256,
                     help="ensemble size (profiling runs only; the measurement uses 256)")
+    ap.add_argument("--no-error-legs", action="store_true",
+                    help="skip the float32 forms' error runs (oracle on the host, full-size float64)")
+    ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_leg:
+        cpu_leg_main(args.cpu_leg)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -73,7 +73,7 @@ extern "C" {
 #define DG_DEVICE 1
 
 /* Number of values written by dg_reduce. */
-#define DG_NREDUCE 8
+#define DG_NREDUCE 9
 
 typedef struct dg_ctx dg_ctx;
 
@@ -98,14 +98,19 @@ typedef struct dg_config {
                            face pass); DG_FACES_INLINE in the stage kernel, by both
                            elements of a face; DG_FACES_PASS once per face point in a
                            separate face kernel (an extra flux buffer of
-                           n_f (k+1)^(d-1) values per face).  The results agree to
-                           rounding; in both the two sides of a face get exactly
-                           opposite fluxes. */
+                           n_f (k+1)^(d-1) values per face); DG_FACES_COLUMN (float32
+                           forms only) in one kernel that marches each brick of
+                           element columns upward and keeps the faces between
+                           its elements on chip, only the brick sides' traces
+                           passing through device memory.  The results agree to
+                           rounding (float32 forms: bitwise); in every schedule
+                           the two sides of a face get exactly opposite fluxes. */
 } dg_config;
 
 #define DG_FACES_AUTO 0
 #define DG_FACES_INLINE 1
 #define DG_FACES_PASS 2
+#define DG_FACES_COLUMN 3
 
 typedef struct dg_info {
     int n_fields;               /* n_f */
@@ -138,7 +143,8 @@ typedef struct dg_bubble {
  * to cuda_stream (a cudaStream_t, NULL for the default stream).  Allocates the
  * device state (two copies), derived fields and face-trace buffers.
  * Errors: DG_EINVAL for out-of-range fields or a mesh whose
- * n_nodes * n_fields exceeds 2^31 - 1; DG_ENOMEM; DG_ECUDA. */
+ * n_nodes * n_fields exceeds 2^31 - 1; DG_ENOTIMPL for DG_FACES_COLUMN with
+ * DG_FP64; DG_ENOMEM; DG_ECUDA. */
 int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream);
 
 /* Release everything owned by ctx (NULL is ignored). */
@@ -199,6 +205,14 @@ int dg_step(dg_ctx *ctx, double dt, int nsteps);
  * check (read it later with dg_check_status). */
 int dg_step_async(dg_ctx *ctx, double dt, int nsteps);
 
+/* Iteration cap of the Newton loops of the split Eq. (2.8) (Section 3.4) in
+ * the following calls on ctx: max_iterations in 1..1000, default 50.  A node
+ * whose iteration reaches the cap keeps its last iterate and is counted as
+ * not converged (DG_ENOCONV from the synchronising calls).  Host setting, no
+ * device work; an ensemble member takes it at the next dg_ensemble_configure.
+ * Errors: DG_EINVAL. */
+int dg_set_newton_limit(dg_ctx *ctx, int max_iterations);
+
 /* Synchronise the stream and report (and clear) the failure counters
  * accumulated since the last check: DG_OK, DG_ENOCONV or DG_ENONPHYS.
  * counts (may be NULL) receives {n_unconverged, n_nonphysical}. */
@@ -213,6 +227,16 @@ int dg_check_status(dg_ctx *ctx, long long counts[2]);
  *   out[5] max over nodes of |u| + v_r + c_m (for a CFL time step)
  *   out[6] max over nodes of (rho_v - rho_vs(T)) / rho_vs(T) (supersaturation)
  *   out[7] integral of E'
+ *   out[8] rain fall-out: the water (rho_m + rho_r) that has left through
+ *          the bottom and top walls since the state was last set
+ *          (dg_set_state, dg_init_bubble), i.e. the time integral of the
+ *          outward Lax-Friedrichs water flux over the wall faces, each
+ *          stage weighted by its share of the step (dt/6, dt/6, dt/6, dt/2).
+ *          The microphysics only moves water between rho_m and rho_r and
+ *          interior faces cancel, so out[1] + out[8] is constant over
+ *          dg_step calls up to rounding (Section 3.6's mass conservation,
+ *          the rain examples of Section 4); the sponge layer, which turns
+ *          moisture into dry air, breaks that balance.  0 without rain.
  * Integrals use the Gauss rule of the DG space (the diagonal mass matrix). */
 int dg_reduce(dg_ctx *ctx, double out[DG_NREDUCE]);
 
@@ -220,31 +244,48 @@ int dg_reduce(dg_ctx *ctx, double out[DG_NREDUCE]);
 #define DG_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 
 /* dg_rhs without any device allocation.  No counterpart in the paper: the
- * arithmetic is exactly dg_rhs's; only where its scratch lives differs.
+ * arithmetic is that of dg_rhs's kernels with the face fluxes evaluated
+ * inside the stage kernel (the DG_FACES_INLINE schedule), so the result
+ * agrees with dg_rhs to rounding; only where its scratch lives differs.
  *
  * For callers that cannot call cudaMalloc -- a host program whose memory
  * pool owns all device memory (a stray allocation would fragment it or
  * escape its accounting), a latency-critical loop that cannot pay for the
  * device synchronisation an allocation may imply, a process with a
  * device-memory budget fixed at start-up.  No context is needed: cfg
- * describes the mesh (precision must be DG_FP64), base_node[4][n_zlev_node]
- * and base_face[4][n_zlev_face] are the base-state tables (device, float64,
- * rows rho_d, rho_m, E, p, levels as in dg_zlevels), U the state and dUdt the
- * output (device, ABI layout, float64, not overlapping).  Work goes to
- * cuda_stream (a cudaStream_t, NULL = default stream); the call is
- * asynchronous and allocates nothing: its scratch (derived fields, face
- * traces, failure counters) is one file-scope device array of
+ * describes the mesh (precision must be DG_FP64, faces DG_FACES_AUTO or
+ * DG_FACES_INLINE), base_node[4][n_zlev_node] and base_face[4][n_zlev_face]
+ * are the base-state tables (device, float64, rows rho_d, rho_m, E, p,
+ * levels as in dg_zlevels), U the state and dUdt the output (device, ABI
+ * layout, float64, not overlapping).  Work goes to cuda_stream (a
+ * cudaStream_t, NULL = default stream); the call is asynchronous and
+ * allocates nothing: its scratch (saturation-density table, failure
+ * counters, derived fields, face traces) is one file-scope device array of
  * DG_STATIC_SCRATCH_BYTES that each GPU loading the library holds until the
- * process exits.  The first call on a device looks up that array's address
- * (with the device current) -- make that first call before any stream
- * capture.  Every call shares the one array, so calls whose work overlaps on
- * the GPU (different streams, different host threads) race; serialise them.
- * Errors: DG_EINVAL for a bad argument, a non-float64 precision, or a mesh
- * whose scratch (derived fields + face traces) exceeds
+ * process exits.  The first call on a device (this one or
+ * dg_rhs_noalloc_status) sets the array up with that device current -- looks
+ * up its address, fills the table, zeroes the counters, and waits for that
+ * work on the legacy default stream -- so make that first call before any
+ * stream capture.  cudaDeviceReset invalidates the set-up: do not use these
+ * entry points on a device after resetting it.  Every call shares the one
+ * array, so calls whose work overlaps on the GPU (different streams,
+ * different host threads) race; serialise them.  Newton iterations that hit
+ * their cap and non-physical nodes are counted in the array across calls;
+ * read them with dg_rhs_noalloc_status.
+ * Errors: DG_EINVAL for a bad argument, a non-float64 precision, the face
+ * pass, or a mesh whose scratch (derived fields + face traces) exceeds
  * DG_STATIC_SCRATCH_BYTES (e.g. about 1,800 elements of 3-D Q4 with rain);
  * DG_ECUDA. */
 int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, const double *base_face,
                    const void *U, void *dUdt, void *cuda_stream);
+
+/* Failure counters of the dg_rhs_noalloc calls on the current device since
+ * the last read: copies {n_unconverged, n_nonphysical} into counts (may be
+ * NULL) and clears them, in order on cuda_stream, then synchronises that
+ * stream.  Returns DG_ENONPHYS if any node was non-physical, else
+ * DG_ENOCONV if a Newton iteration hit its cap, else DG_OK; DG_ECUDA.
+ * Allocates nothing. */
+int dg_rhs_noalloc_status(long long counts[2], void *cuda_stream);
 
 /* Adjoint of the right-hand side: ubar = (dR/dU)^T w for R = dg_rhs at the
  * state U (device, ABI layout, float64), w and ubar device float64 arrays in
@@ -286,7 +327,7 @@ int dg_cloud_functional(dg_ctx *ctx, const void *U, double *J, double *dJdU);
  * over the elements at each vertex; penalty sigma k^2 / h_j on interior
  * faces (walls carry no diffusive flux).  The coefficient follows the state
  * the right-hand side is evaluated on.  Needs the face pass (dg_config.faces
- * != DG_FACES_INLINE).
+ * == DG_FACES_AUTO or DG_FACES_PASS).
  *
  * Sponge (Section 3.6, Eq. (3.8)), after every dg_step step:
  * rho_m', rho_r', m, E' <- (1 - delta) (.) and rho_d' += delta (rho_m' + rho_r')
@@ -354,6 +395,54 @@ int dg_ensemble_step_async(dg_ensemble *ens, int nsteps);
 
 /* Free the ensemble and its members (NULL is ignored). */
 void dg_ensemble_free(dg_ensemble *ens);
+
+/* ---- Self-test of the library's float64 elementary functions -------------
+ * Not part of the method (no counterpart in the paper): a verification aid.
+ * The float64 kernels replace CUDA's conversions, divisions, square roots,
+ * pow and exp/log on their hot paths by their own functions -- float32 <->
+ * float64 conversions and compares on the bit pattern, Newton-Raphson
+ * refinement of the hardware's approximate reciprocal and reciprocal square
+ * root, one third-order step for r^(-1/16) and r^(-1/8) from a float32
+ * estimate, a Taylor table for rho_vs(T) of Eq. (2.6).  dg_selftest_math
+ * evaluates function fn of the library at the n float64 values x (device)
+ * and writes, to out[4n] (device, float64):
+ *   out[0 .. n)    the library's value,
+ *   out[n .. 2n)   the value of the function it stands in for, computed by
+ *                  CUDA: the hardware conversion (NARROW: float64 -> float32,
+ *                  WIDEN: float32 -> float64 of the float32-rounded x), IEEE
+ *                  division 1/x (RECIP), 1/sqrt(x) by IEEE sqrt and division
+ *                  (RSQRT), IEEE sqrt (SQRT), pow(x, -1/16) (INV_ROOT16),
+ *                  pow(x, -1/8) (INV_ROOT8), the closed form
+ *                  e_s(T) / (R_v T) with exp and log (RHO_VS; RHO_VS_F32 takes
+ *                  the float32-rounded temperature, the overload the float32
+ *                  pre-solve uses), or for COMPARE the bits of the plain
+ *                  float64 compares x > 0, x > 1.5, x < 1.5, |x| <= 1.5,
+ *                  isfinite(x), max(|x|, 1.5) against those of the library's
+ *                  bit-pattern compares;
+ *   out[2n .. 4n)  for RHO_VS / RHO_VS_F32 the derivative d rho_vs / dT, the
+ *                  library's and the closed form's; 0 otherwise.
+ * Uses ctx's rho_vs table and stream; synchronises.  Errors: DG_EINVAL
+ * (bad fn or n, or a device other than ctx's current); DG_ECUDA. */
+#define DG_MATH_NARROW 0
+#define DG_MATH_WIDEN 1
+#define DG_MATH_RECIP 2
+#define DG_MATH_RSQRT 3
+#define DG_MATH_SQRT 4
+#define DG_MATH_INV_ROOT16 5
+#define DG_MATH_INV_ROOT8 6
+#define DG_MATH_RHO_VS 7
+#define DG_MATH_RHO_VS_F32 8
+#define DG_MATH_COMPARE 9
+int dg_selftest_math(dg_ctx *ctx, int fn, const double *x, double *out, long long n);
+
+/* Float64 FMA throughput probe (a measurement aid, not part of the method):
+ * enqueues on cuda_stream one kernel of `blocks` CTAs x 256 threads, each
+ * thread running 8 independent chains of `iters` dependent fmas, and writes
+ * each thread's result to out[blocks * 256] (device, float64).  *flops (host,
+ * may be NULL) receives the kernel's float64 operation count, 2 per fma, so
+ * that the caller's timing of the launch gives the FP64 rate.  Asynchronous.
+ * Errors: DG_EINVAL, DG_ECUDA. */
+int dg_fp64_fma_probe(double *out, int blocks, long long iters, void *cuda_stream, double *flops);
 
 /* Text for a status code. */
 const char *dg_strerror(int code);

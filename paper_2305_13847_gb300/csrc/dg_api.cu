@@ -221,6 +221,7 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     A.alphaK = (Real *)c->alphaK;
     A.alphaV = (const Real *)c->alphaV;
     A.flags = c->flags;
+    A.fallout = c->fallout;
     return A;
 }
 
@@ -238,11 +239,16 @@ int prepare(dg_ctx *c, const void *U, int tb) {
                    : do_prepare<double>(c, c->L64, c->ref64, U, tb);
 }
 
-// last: the stage that ends a time step (the sponge layer acts there)
+// last: the stage that ends a time step (the sponge layer acts there);
+// fall_w: the stage's weight b_s dt in the step for the rain fall-out (0: the
+// stage adds nothing to it)
 template <typename Real>
 int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int mode, const void *Uin,
-             const void *Un, void *Uout, int tin, double alpha, double beta, double gdt, bool last) {
+             const void *Un, void *Uout, int tin, double alpha, double beta, double gdt, bool last,
+             double fall_w) {
     KArgs<Real> A = base_args<Real>(c, ref);
+    A.fall_w = fall_w;
+    if (fall_w == 0.0 || mode != MODE_STAGE) A.fallout = nullptr;
     A.Uin = (const Real *)Uin;
     A.Un = (const Real *)Un;
     A.Uout = (Real *)Uout;
@@ -258,6 +264,7 @@ int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int 
         const int st = cuda_status(L->alpha_vertex(A, c->stream));
         if (st != DG_OK) return st;
     }
+    if (c->column) return cuda_status(L->column(A, mode, c->stream));
     if (c->face_pass) {
         const int st = cuda_status(L->face(A, c->diff, c->stream));
         if (st != DG_OK) return st;
@@ -266,11 +273,19 @@ int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int 
 }
 
 int stage(dg_ctx *c, int mode, const void *Uin, const void *Un, void *Uout, int tin, double alpha,
-          double beta, double gdt, bool last = false) {
+          double beta, double gdt, bool last = false, double fall_w = 0.0) {
     return c->fp32 ? do_stage<float>(c, c->L32, c->ref32, mode, Uin, Un, Uout, tin, alpha, beta, gdt,
-                                     last)
+                                     last, fall_w)
                    : do_stage<double>(c, c->L64, c->ref64, mode, Uin, Un, Uout, tin, alpha, beta, gdt,
-                                      last);
+                                      last, fall_w);
+}
+
+// the fall-out starts again from zero with every new state
+int reset_fallout(dg_ctx *c) {
+    if (!c->fallout) return DG_OK;
+    return cudaMemsetAsync(c->fallout, 0, sizeof(double) * c->fallout_len, c->stream) == cudaSuccess
+               ? DG_OK
+               : DG_ECUDA;
 }
 
 void release(dg_ctx *c) {
@@ -278,7 +293,7 @@ void release(dg_ctx *c) {
                     c->bface_d, c->bnode_r, c->bface_r, c->flags, c->partials, c->rvs_tab,
                     c->adjX[0], c->adjX[1], c->adjX[2], c->adjL[0], c->adjL[1], c->adjL[2],
                     c->ubar_part, c->tadj, c->bsplit, c->fbuf, c->ftab, c->alphaK, c->alphaV,
-                    c->dtrace[0], c->dtrace[1], c->sponge};
+                    c->dtrace[0], c->dtrace[1], c->sponge, c->fallout};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -465,7 +480,8 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     if (g.precision != DG_FP64 && g.precision != DG_FP32_BULK && g.precision != DG_FP32_PERT)
         return DG_EINVAL;
     if (g.rain != 0 && g.rain != 1) return DG_EINVAL;
-    if (g.faces != DG_FACES_AUTO && g.faces != DG_FACES_INLINE && g.faces != DG_FACES_PASS)
+    if (g.faces != DG_FACES_AUTO && g.faces != DG_FACES_INLINE && g.faces != DG_FACES_PASS &&
+        g.faces != DG_FACES_COLUMN)
         return DG_EINVAL;
     long long ne = 1;
     for (int j = 0; j < g.dim; ++j) {
@@ -477,6 +493,7 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     const int np = g.dim == 2 ? p1 * p1 : p1 * p1 * p1;
     const int nf = (g.rain ? 4 : 3) + g.dim;
     if (ne * np * (long long)(nf + 3) * 2 > 2147483647LL) return DG_EINVAL;
+    if (g.faces == DG_FACES_COLUMN && g.precision == DG_FP64) return DG_ENOTIMPL;
 
     dg_ctx *c = new (std::nothrow) dg_ctx();
     if (!c) return DG_ENOMEM;
@@ -523,10 +540,12 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     M.rain_d8 = 0.125 * std::pow(kRainFloorLin, -0.875);
     M.rain_d16 = 0.0625 * std::pow(kRainFloorLin, -0.9375);
     M.pert_split = (g.precision == DG_FP32_PERT) ? 1 : 0;
+    M.newton_cap = kMaxNewton;
     // face grid and the face-pass flux buffer layout
     // the face pass is the faster schedule for every precision on GB300
     // (measured: float64 -21 %, float32 forms -8 to -11 % per step)
-    c->face_pass = g.faces != DG_FACES_INLINE;
+    c->face_pass = g.faces == DG_FACES_AUTO || g.faces == DG_FACES_PASS;
+    c->column = g.faces == DG_FACES_COLUMN;
     const long long fbuf_len = set_face_layout(c, nf);
     mesh_float_copies(M);
     c->ref64 = make_ref<double>(g.order);
@@ -597,6 +616,12 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
                                       cudaMemcpyHostToDevice) != cudaSuccess)
             st = DG_ECUDA;
     }
+    if (st == DG_OK && g.rain) {
+        // fall-out accumulator: the points of the bottom and top wall faces
+        c->fallout_len = (size_t)2 * (ne / g.n[g.dim - 1]) * c->nfp1;
+        st = alloc(c, (void **)&c->fallout, sizeof(double) * c->fallout_len);
+        if (st == DG_OK) st = reset_fallout(c);
+    }
     if (st == DG_OK && cudaMemsetAsync(c->flags, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
         st = DG_ECUDA;
     if (st == DG_OK) {
@@ -646,7 +671,7 @@ int dg_get_info(const dg_ctx *c, dg_info *info) {
     info->n_dofs = c->nodes * c->nf;
     info->state_bytes = (size_t)c->nodes * c->nf * c->rsz;
     info->device_bytes = c->device_bytes;
-    info->launches_per_stage = c->face_pass ? 2 : 1;
+    info->launches_per_stage = c->face_pass ? 2 : 1;   // column march and inline faces: 1
     return DG_OK;
 }
 
@@ -720,6 +745,7 @@ int dg_init_bubble(dg_ctx *c, const dg_bubble *b, const double *noise, int where
         e = c->L64->init_bubble(A, B, c->stream);
     }
     if (e != cudaSuccess) return DG_ECUDA;
+    if (reset_fallout(c) != DG_OK) return DG_ECUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DG_ECUDA;
     c->state_set = true;
     c->derived_valid = false;
@@ -734,6 +760,7 @@ int dg_set_state(dg_ctx *c, const void *U, int where) {
                                     where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                                     c->stream);
     if (e != cudaSuccess) return DG_ECUDA;
+    if (reset_fallout(c) != DG_OK) return DG_ECUDA;
     c->state_set = true;
     c->derived_valid = false;
     return DG_OK;
@@ -766,6 +793,12 @@ int dg_check_status(dg_ctx *c, long long counts[2]) {
     }
     if (h[1]) return DG_ENONPHYS;
     if (h[0]) return DG_ENOCONV;
+    return DG_OK;
+}
+
+int dg_set_newton_limit(dg_ctx *c, int max_iterations) {
+    if (!c || max_iterations < 1 || max_iterations > 1000) return DG_EINVAL;
+    c->M.newton_cap = max_iterations;
     return DG_OK;
 }
 
@@ -827,14 +860,17 @@ int dg_step_async(dg_ctx *c, double dt, int nsteps) {
     //   u1 = u + dt/2 L(u); u2 = u1 + dt/2 L(u1); u3 = 2/3 u + 1/3 u2 + dt/6 L(u2);
     //   u^{n+1} = u3 + dt/2 L(u3)
     for (int n = 0; n < nsteps && st == DG_OK; ++n) {
+        // the fall-out weights are those of L(u_s) in u^{n+1} once the
+        // stages are expanded: dt (1/6, 1/6, 1/6, 1/2)
         int p = c->parity;
-        st = stage(c, MODE_STAGE, Un, Un, Uw, p, 0.0, 1.0, 0.5 * dt);
+        st = stage(c, MODE_STAGE, Un, Un, Uw, p, 0.0, 1.0, 0.5 * dt, false, dt / 6.0);
         p ^= 1;
-        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Uw, p, 0.0, 1.0, 0.5 * dt);
+        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Uw, p, 0.0, 1.0, 0.5 * dt, false, dt / 6.0);
         p ^= 1;
-        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Un, Uw, p, 2.0 / 3.0, 1.0 / 3.0, dt / 6.0);
+        if (st == DG_OK)
+            st = stage(c, MODE_STAGE, Uw, Un, Uw, p, 2.0 / 3.0, 1.0 / 3.0, dt / 6.0, false, dt / 6.0);
         p ^= 1;
-        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Un, p, 0.0, 1.0, 0.5 * dt, true);
+        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Un, p, 0.0, 1.0, 0.5 * dt, true, 0.5 * dt);
         p ^= 1;
         c->parity = p;
     }

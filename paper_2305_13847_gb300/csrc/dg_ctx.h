@@ -29,10 +29,13 @@ struct dg_ctx {
     double *bnode_d = nullptr, *bface_d = nullptr;
     void *bnode_r = nullptr, *bface_r = nullptr;
     unsigned long long *flags = nullptr;
+    double *fallout = nullptr;   // rain: accumulated outward water flux per wall face point
+    size_t fallout_len = 0;
     double *partials = nullptr;
     double *rvs_tab = nullptr;
     float *bsplit = nullptr;     // DG_FP32_PERT: base-state split tables
     bool face_pass = false;      // faces in k_face (DG_FACES_PASS) instead of in the stage kernel
+    bool column = false;         // DG_FACES_COLUMN: the column-march stage kernel (float32 forms)
     void *fbuf = nullptr;        // face pass: fluxes per face point
     int *ftab = nullptr;         // face pass: index in fbuf of each element's 2D faces [ne][2D]
     // artificial diffusion and sponge layer (dg_set_stabilisation)

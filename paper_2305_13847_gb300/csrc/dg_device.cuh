@@ -81,6 +81,7 @@ struct MeshData {
     double rain_floor;     // linearisation only: rain powers differentiated at max(rho_r, floor)
     double rain_d8, rain_d16;  // d rho_r^(1/8) / d rho_r and d rho_r^(1/16) / d rho_r at the floor
     int pert_split;        // float32 state: 1 = split in perturbation variables (DG_FP32_PERT)
+    int newton_cap;        // iteration cap of every Newton loop of the split (default kMaxNewton)
     // faces normal to e_j: a grid of nfn[j] (= n_j, + 1 with walls) x the other n,
     // nfaces[j] of them; face c lies between the elements at coordinates c - 1
     // and c along e_j.  The face kernel covers direction j with fblk[j] CTAs
@@ -156,7 +157,29 @@ struct KArgs {
     const Real *sponge;    // sponge delta_R at the node levels (last stage of a step) or null
     Real alpha, beta, gdt; // Uout = alpha Un + beta Uin + gdt dU/dt
     unsigned long long *flags;  // [0] Newton failures, [1] non-physical nodes
+    // rain fall-out (time steps with rain): per point of the bottom and top
+    // wall faces, the time integral of the outward water flux
+    // [2 (bottom, top)][faces per wall][NFP1], float64; fall_w = this stage's
+    // weight in the step (dt/6, dt/6, dt/6, dt/2); null when not accumulating
+    double *fallout;
+    double fall_w;
 };
+
+// float64 value of a storage-type value (widen: integer pipe)
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return widen(x); }
+
+// Fall-out: add this stage's outward water flux (rho_m + rho_r, outward
+// normal) at point q of a bottom (top = false) or top wall face over
+// horizontal element position h.  Each wall face point has one writer per
+// stage, so the sum is deterministic.
+template <class S, typename Real>
+__device__ __forceinline__ void add_fallout(const KArgs<Real> &A, bool top, int h, int q,
+                                            double out_water) {
+    const int nh = S::D == 3 ? A.M.n[0] * A.M.n[1] : A.M.n[0];
+    double *p = A.fallout + ((size_t)(top ? nh : 0) + h) * S::NFP1 + q;
+    *p = fma(A.fall_w, out_water, *p);
+}
 
 // ---------------------------------------------------------------------------
 // Compile-time layout of one (D, K, RAIN) configuration
@@ -320,7 +343,8 @@ struct SplitResult {
 // float64 Newton iteration (cap kMaxNewton).
 template <bool NEED_DEFICIT>
 __device__ __forceinline__ SplitResult split_point(double rd, double rm, double rr, double re,
-                                                   const double *__restrict__ tab) {
+                                                   const double *__restrict__ tab,
+                                                   int cap = kMaxNewton) {
     SplitResult r;
     // T_u = T_ref + X / C_u.  X (a difference of large terms) is float64; the
     // float32 T_u decides saturation (with a 1e-5 margin) and starts the
@@ -362,7 +386,8 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     float t = tuf;
     {
         const float cdf = narrow(cdry), ref = narrow(re), tref = (float)kTref;
-        for (int it = 0; it < 30; ++it) {
+        const int n32 = cap < 30 ? cap : 30;
+        for (int it = 0; it < n32; ++it) {
             const float rvs = rho_vs_f32(t);
             const float it_ = __frcp_rn(t);
             const float drvs = rvs * it_ * (am1 + bb * it_);
@@ -410,7 +435,7 @@ __device__ __forceinline__ SplitResult split_point(double rd, double rm, double 
     double tn0 = ((double)t > tu) ? (double)t : tu;
     double lo = tu, hi = INFINITY, rvs = 0.0, drvs = 0.0, step = INFINITY;
     bool done = false;
-    for (int it = 0; it < kMaxNewton; ++it) {
+    for (int it = 0; it < cap; ++it) {
         rvs = rho_vs_tab(tn0, tab, drvs);
         const double heat = fma(kCvv - kCl, rvs, cdry);
         const double h = fma(heat, tn0 - kTref, fma(rvs, kLprime, -re));
@@ -467,7 +492,7 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
     NodeDerived o;
     const double rho = rd + rm + rr;
     const double re = E - 0.5 * msq * recip(rho);
-    const SplitResult s = split_point<RAIN>(rd, rm, rr, re, tab);
+    const SplitResult s = split_point<RAIN>(rd, rm, rr, re, tab, M.newton_cap);
     o.T = s.T;
     o.rv = s.rv;
     o.conv = s.converged;
@@ -561,7 +586,8 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
         // is one (not below T_u, which lies below the saturated root)
         float t = Tprev > tuf ? Tprev : tuf;
         bool conv = false;
-        for (int it = 0; it < 40; ++it) {
+        const int n32 = M.newton_cap < 40 ? M.newton_cap : 40;
+        for (int it = 0; it < n32; ++it) {
             const float rvs = rho_vs_f32(t);
             const float it_ = __frcp_rn(t);
             const float drvs = rvs * it_ * (am1 + bb * it_);
@@ -691,7 +717,8 @@ __device__ __forceinline__ NodeDerived node_derived_pert(const float *u, int im,
         const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
         float prev = 3.0e38f;
         bool have_nu = false;
-        for (int it = 0; it < 40; ++it) {
+        const int n32 = M.newton_cap < 40 ? M.newton_cap : 40;
+        for (int it = 0; it < n32; ++it) {
             const float T = Tb + tau;
             const float iT = __frcp_rn(T);
             const float em = expm1f(phi_of(tau, iTb, bTb, iT));
@@ -1123,7 +1150,8 @@ __device__ __forceinline__ NodeDerived derive_node(const float *u, const KArgs<f
                                       A.bnode[lev], A.bnode[nl + lev], A.M, A.rvs_tab, Tprev);
 }
 
-template <class S, typename Real, bool DIFF = false>
+// STRIDE: nodes per field row of s_tr (0: the stage tile's EPB NP)
+template <class S, typename Real, bool DIFF = false, int STRIDE = 0>
 __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real *u, int e, int a,
                                                 int iz, Real *s_tr, int t, Real *s_red = nullptr,
                                                 Real Tprev = Real(-1)) {
@@ -1155,7 +1183,7 @@ __device__ __forceinline__ void split_and_store(const KArgs<Real> &A, const Real
         A.derived[4 * nodes + gi] = vr;
     }
     if (DIFF) alpha_accumulate<S, Real>(A, A.ref, u, vr, a, lev, s_red + 2 * (t / S::NP));
-    const int str = S::EPB * S::NP;
+    const int str = STRIDE > 0 ? STRIDE : S::EPB * S::NP;
 #pragma unroll
     for (int f = 0; f < S::NF; ++f) s_tr[f * str + t] = u[f];
     s_tr[S::NF * str + t] = T;
@@ -1341,14 +1369,47 @@ __device__ __forceinline__ void face_point(const KArgs<Real> &A, const RefData<R
     const Real hs = Real(0.5) * Real(s), hl = Real(0.5) * lam;
     Real *out = s_fh + ((el2 * S::NFACE + face) * S::NF) * S::NFP1 + q;
     // one explicit fma, as in face_flux: both schedules round identically
+    Real o[S::NF];
 #pragma unroll
-    for (int f = 0; f < S::NF; ++f)
-        out[f * S::NFP1] = fma(hs, add_rn(Fm[f], Fp[f]), hl * (tm[f] - tp[f]));
+    for (int f = 0; f < S::NF; ++f) {
+        o[f] = fma(hs, add_rn(Fm[f], Fp[f]), hl * (tm[f] - tp[f]));
+        out[f * S::NFP1] = o[f];
+    }
+    if (S::RAIN && J == S::VERT && nb < 0 && A.fallout) {
+        const int nh = S::D == 3 ? M.n[0] * M.n[1] : M.n[0];
+        add_fallout<S, Real>(A, s > 0, e2 % nh, q, to_f64(o[1]) + to_f64(o[2]));
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Face pass: the Lax-Friedrichs flux of Section 3.2 once per face point
 // ---------------------------------------------------------------------------
+// G = {{F_J}} + Lambda/2 (U_lo - U_hi) along +e_J at one face point from the
+// traces tl (element at the lower coordinate) and th (upper) and the base
+// state at the point.  The sum F_lo + F_hi is an unfused add and G one
+// explicit fma, so G does not depend on which side evaluates it, and the
+// inline schedule's outward fluxes are +G and -G exactly.
+template <class S, typename Real, int J>
+__device__ __forceinline__ void lf_flux(const Real *tl, const Real *th, Real brd, Real brm, Real bE,
+                                        Real bp, const MeshData &M, Real *G) {
+    Prim<S::D, S::RAIN, Real> Pl, Ph;
+    make_prim<S, Real>(Pl, tl, brd, brm, bE, bp, tl[S::NF], tl[S::NF + 1], tl[S::NF + 2]);
+    make_prim<S, Real>(Ph, th, brd, brm, bE, bp, th[S::NF], th[S::NF + 1], th[S::NF + 2]);
+    if (S::RAIN) {
+        Pl.vr = rain_velocity(Pl.rr, Pl.rm, M);
+        Ph.vr = rain_velocity(Ph.rr, Ph.rm, M);
+    }
+    Real Fl[S::NF], Fh[S::NF];
+    flux_dir<S, Real>(Pl, J, Fl);
+    flux_dir<S, Real>(Ph, J, Fh);
+    const Real ll = wave_speed<S, J, Real>(Pl), lh = wave_speed<S, J, Real>(Ph);
+    const Real lam = max_nonneg(ll, lh);
+    const Real hl = Real(0.5) * lam;
+#pragma unroll
+    for (int fld = 0; fld < S::NF; ++fld)
+        G[fld] = fma(Real(0.5), add_rn(Fl[fld], Fh[fld]), hl * (tl[fld] - th[fld]));
+}
+
 // G = {{F_j}} + Lambda/2 (U_lo - U_hi) along +e_j from the traces of the two
 // elements (lo at coordinate c - 1, hi at c); a slip wall stands in for a
 // missing element with the ghost state m -> m - 2 (m.n) n.  The element on
@@ -1406,29 +1467,13 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
         load_base<S, Real>(A.bnode, M.nzlev_node, im[S::VERT] * S::P1 + face_q_vert<S::D, S::P1>(J, q),
                            brd, brm, bE, bp);
     }
-    Prim<S::D, S::RAIN, Real> Pl, Ph;
-    make_prim<S, Real>(Pl, tl, brd, brm, bE, bp, tl[S::NF], tl[S::NF + 1], tl[S::NF + 2]);
-    make_prim<S, Real>(Ph, th, brd, brm, bE, bp, th[S::NF], th[S::NF + 1], th[S::NF + 2]);
-    if (S::RAIN) {
-        Pl.vr = rain_velocity(Pl.rr, Pl.rm, M);
-        Ph.vr = rain_velocity(Ph.rr, Ph.rm, M);
-    }
-    Real Fl[S::NF], Fh[S::NF];
-    flux_dir<S, Real>(Pl, J, Fl);
-    flux_dir<S, Real>(Ph, J, Fh);
-    const Real ll = wave_speed<S, J, Real>(Pl), lh = wave_speed<S, J, Real>(Ph);
-    const Real lam = max_nonneg(ll, lh);
     // face-major: [faces normal to e_0 | e_1 | e_2][NFP fields][NFP1 points],
     // one block per face
     constexpr int NFP = DIFF ? 2 * S::NF : S::NF;
     const size_t fg = (size_t)(J > 0 ? M.nfaces[0] : 0) + (J > 1 ? M.nfaces[1] : 0) + f;
     Real *out = A.fbuf + fg * NFP * S::NFP1 + q;
-    const Real hl = Real(0.5) * lam;
-    // one explicit fma, as in face_point: both schedules round identically
     Real G[S::NF];
-#pragma unroll
-    for (int fld = 0; fld < S::NF; ++fld)
-        G[fld] = fma(Real(0.5), add_rn(Fl[fld], Fh[fld]), hl * (tl[fld] - th[fld]));
+    lf_flux<S, Real, J>(tl, th, brd, brm, bE, bp, M, G);
     if (DIFF) {
         // interior penalty (Eq. (3.7)) on interior faces: viscous flux along +e_j
         //   V = -alpha {{du/dx_j}} + sigma k^2/h_j alpha [[u]],  [[u]] = u_lo - u_hi,
@@ -1493,6 +1538,12 @@ __device__ __forceinline__ void face_flux(const KArgs<Real> &A, int f, int q) {
     // above lifts -G (the sign sits in its lift coefficient)
 #pragma unroll
     for (int fld = 0; fld < S::NF; ++fld) out[fld * S::NFP1] = G[fld];
+    if (S::RAIN && J == S::VERT && (e_lo < 0 || e_hi < 0) && A.fallout) {
+        // outward normal -e_z at the bottom wall, +e_z at the top
+        const int nh = S::D == 3 ? M.n[0] * M.n[1] : M.n[0];
+        const double gw = to_f64(G[1]) + to_f64(G[2]);
+        add_fallout<S, Real>(A, e_lo >= 0, f - c * nh, q, e_lo < 0 ? -gw : gw);
+    }
 }
 
 constexpr int kFaceThreads = 128;
@@ -1885,7 +1936,7 @@ __global__ void k_init_bubble(KArgs<Real> A, BubbleArgs B) {
 // Reductions (deterministic: fixed per-block tree, then one block in order)
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
-constexpr int kNRed = 8;
+constexpr int kNRed = 9;
 
 template <class S, typename Real>
 __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(KArgs<Real> A, double *partials) {
@@ -1907,8 +1958,14 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(KArgs<Real> A, d
         const double urd = (double)A.Uin[gi], urm = (double)A.Uin[nodes + gi];
         const double urr = S::RAIN ? (double)A.Uin[2 * nodes + gi] : 0.0;
         const double rd = A.bnode_d[lev] + urd, rm = A.bnode_d[nl + lev] + urm, rr = urr;
-        const double T = (double)A.derived[gi], rv = (double)A.derived[nodes + gi];
-        const double pp = (double)A.derived[2 * nodes + gi];
+        // the split's float64 T, rho_v, p' (the float32 forms store their
+        // derived fields in float32, whose rounding of T alone moves rho_vs(T)
+        // by ~2e-6 relative: too coarse for the supersaturation diagnostic)
+        Real u[S::NF];
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) u[f] = A.Uin[f * nodes + gi];
+        const NodeDerived nd = derive_node<S>(u, A, lev);
+        const double T = nd.T, rv = nd.rv, pp = nd.pp;
         const double rho = rd + rm + rr;
         double msq = 0.0;
 #pragma unroll
@@ -1930,6 +1987,20 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(KArgs<Real> A, d
         const double rvs = rho_vs(T, 1.0 / T);
         acc[6] = fmax(acc[6], (rv - rvs) / rvs);
         acc[7] += W * (double)A.Uin[S::IE * nodes + gi];
+    }
+    // fall-out: sum over the wall face points of Wf_q J_F x the accumulated
+    // outward water flux, J_F = |K| / 2^d x 2 / h_z
+    if (S::RAIN && A.fallout) {
+        const int nh = S::D == 3 ? A.M.n[0] * A.M.n[1] : A.M.n[0];
+        const size_t npt = (size_t)2 * nh * S::NFP1;
+        const double jf = A.M.jac * A.M.two_over_h[S::VERT];
+        for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npt;
+             p += (size_t)gridDim.x * blockDim.x) {
+            const int q = (int)(p % S::NFP1);
+            double wq = jf * (double)A.ref.w[q % S::P1];
+            if (S::D == 3) wq *= (double)A.ref.w[q / S::P1];
+            acc[8] += wq * A.fallout[p];
+        }
     }
 #pragma unroll
     for (int r = 0; r < kNRed; ++r) sh[r][threadIdx.x] = acc[r];

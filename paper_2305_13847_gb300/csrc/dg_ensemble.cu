@@ -28,6 +28,7 @@ struct EnsMember {
     float *U[2];         // U^n, work stage
     float *trace[2];
     float g_half, g_sixth;
+    double fall_w[4];    // the stages' weights in the step for the rain fall-out
     int K, rain;
 };
 
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(kEnsThreads, MINB) k_ens_stage(const EnsMember
                          s_args.alpha = 0.0f; s_args.beta = 1.0f; s_args.gdt = m->g_half;
                          s_args.trace_in = m->trace[1]; s_args.trace_out = m->trace[0]; break;
             }
+            s_args.fall_w = m->fall_w[stage];
             s_k = m->K;
             s_rain = m->rain;
         }
@@ -187,6 +189,9 @@ int build(dg_ensemble *E) {
         A.rvs_tab = c->rvs_tab;
         A.bsplit = c->bsplit;
         A.flags = c->flags;
+        A.fallout = c->fallout;
+        for (int s = 0; s < 3; ++s) m.fall_w[s] = E->dt[i] / 6.0;
+        m.fall_w[3] = 0.5 * E->dt[i];
         m.U[0] = (float *)c->U[0];
         m.U[1] = (float *)c->U[1];
         m.trace[0] = (float *)c->trace[0];

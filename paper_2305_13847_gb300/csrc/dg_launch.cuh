@@ -3,6 +3,9 @@
 // compile in parallel.
 #pragma once
 
+#include <type_traits>
+
+#include "dg_column.cuh"
 #include "dg_device.cuh"
 
 namespace dgm {
@@ -20,6 +23,9 @@ struct Launchers {
     cudaError_t (*split)(const KArgs<Real> &, double *, double *, double *, double *, cudaStream_t);
     cudaError_t (*init_bubble)(const KArgs<Real> &, const BubbleArgs &, cudaStream_t);
     cudaError_t (*reduce)(const KArgs<Real> &, double *partials, int nblocks, cudaStream_t);
+    // column march (float32 forms only; null for float64): a stage or the
+    // right-hand side with the face fluxes evaluated on chip
+    cudaError_t (*column)(const KArgs<Real> &, int mode, cudaStream_t);
 };
 
 constexpr int kGridStrideBlocks = 152 * 8;
@@ -119,6 +125,27 @@ struct Impl {
         return cudaGetLastError();
     }
 
+    template <int MODE>
+    static cudaError_t launch_column(const KArgs<Real> &A, cudaStream_t st) {
+        using C = ColShape<S>;
+        constexpr size_t smem = column_smem_bytes<S, Real>();
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t err = cudaFuncSetAttribute(k_column<S, Real, MODE>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            attr = true;
+        }
+        const int nxb = (A.M.n[0] + C::BX - 1) / C::BX;
+        const int nyb = S::D == 3 ? (A.M.n[1] + C::BY - 1) / C::BY : 1;
+        k_column<S, Real, MODE><<<nxb * nyb, C::NT, smem, st>>>(A);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t column(const KArgs<Real> &A, int mode, cudaStream_t st) {
+        return mode == MODE_RHS ? launch_column<MODE_RHS>(A, st) : launch_column<MODE_STAGE>(A, st);
+    }
+
     static Launchers<Real> table() {
         Launchers<Real> L;
         L.nf = S::NF;
@@ -137,6 +164,10 @@ struct Impl {
         L.split = &split;
         L.init_bubble = &init_bubble;
         L.reduce = &reduce;
+        if constexpr (std::is_same<Real, float>::value)
+            L.column = &column;
+        else
+            L.column = nullptr;
         return L;
     }
 };

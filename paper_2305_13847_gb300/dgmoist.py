@@ -28,9 +28,12 @@ DG_FP32_PERT = 2
 DG_FACES_AUTO = 0
 DG_FACES_INLINE = 1
 DG_FACES_PASS = 2
+DG_FACES_COLUMN = 3
 DG_HOST = 0
 DG_DEVICE = 1
-DG_NREDUCE = 8
+DG_NREDUCE = 9
+DG_MATH = {"narrow": 0, "widen": 1, "recip": 2, "rsqrt": 3, "sqrt": 4, "inv_root16": 5,
+           "inv_root8": 6, "rho_vs": 7, "rho_vs_f32": 8, "compare": 9}
 
 
 class DGError(RuntimeError):
@@ -87,10 +90,14 @@ SIGNATURES = [
     ("dg_step", _I, [_VP, ctypes.c_double, _I]),
     ("dg_step_async", _I, [_VP, ctypes.c_double, _I]),
     ("dg_check_status", _I, [_VP, _VP]),
+    ("dg_set_newton_limit", _I, [_VP, _I]),
     ("dg_reduce", _I, [_VP, _VP]),
     ("dg_adjoint_step", _I, [_VP, ctypes.c_double, _VP, _VP, _VP]),
     ("dg_strerror", ctypes.c_char_p, [_I]),
+    ("dg_selftest_math", _I, [_VP, _I, _VP, _VP, ctypes.c_longlong]),
+    ("dg_fp64_fma_probe", _I, [_VP, _I, ctypes.c_longlong, _VP, ctypes.POINTER(ctypes.c_double)]),
     ("dg_rhs_noalloc", _I, [ctypes.POINTER(dg_config), _VP, _VP, _VP, _VP, _VP]),
+    ("dg_rhs_noalloc_status", _I, [_VP, _VP]),
     ("dg_rhs_adjoint", _I, [_VP, _VP, _VP, _VP]),
     ("dg_cloud_functional", _I, [_VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     ("dg_set_stabilisation", _I, [_VP, ctypes.POINTER(dg_stabilisation)]),
@@ -255,6 +262,10 @@ def dg_check_status(ctx):
     return st, counts
 
 
+def dg_set_newton_limit(ctx, max_iterations):
+    _check(lib().dg_set_newton_limit(ctx, int(max_iterations)), "dg_set_newton_limit")
+
+
 def dg_reduce(ctx):
     out = np.zeros(DG_NREDUCE)
     _check(lib().dg_reduce(ctx, _addr(out)), "dg_reduce")
@@ -306,10 +317,34 @@ def dg_rhs_noalloc(cfg, base_node, base_face, U, dUdt, stream=None):
                                 _addr(dUdt), _stream_handle(stream)), "dg_rhs_noalloc")
 
 
-def dg_rhs_noalloc_status(cfg, base_node, base_face, U, dUdt, stream=None):
-    """Raw status of dg_rhs_noalloc (for the size-limit check)."""
+def dg_rhs_noalloc_rc(cfg, base_node, base_face, U, dUdt, stream=None):
+    """Raw status of dg_rhs_noalloc (for the argument and size-limit checks)."""
     return lib().dg_rhs_noalloc(ctypes.byref(cfg), _addr(base_node), _addr(base_face), _addr(U),
                                 _addr(dUdt), _stream_handle(stream))
+
+
+def dg_rhs_noalloc_status(stream=None):
+    """Status and failure counts {n_unconverged, n_nonphysical} of the
+    dg_rhs_noalloc calls since the last read (read and cleared)."""
+    counts = np.zeros(2, dtype=np.int64)
+    st = lib().dg_rhs_noalloc_status(_addr(counts), _stream_handle(stream))
+    return st, counts
+
+
+def dg_selftest_math(ctx, fn, x, out):
+    """The library's float64 function `fn` (a DG_MATH key) and CUDA's at the
+    device values x: out (device, 4 * len(x) float64) receives ours, CUDA's,
+    and for rho_vs both derivatives."""
+    _check(lib().dg_selftest_math(ctx, DG_MATH[fn], _addr(x), _addr(out), int(x.numel())),
+           "dg_selftest_math")
+
+
+def dg_fp64_fma_probe(out, blocks, iters, stream=None):
+    """Enqueue the float64 FMA probe; returns its float64 operation count."""
+    flops = ctypes.c_double(0.0)
+    _check(lib().dg_fp64_fma_probe(_addr(out), int(blocks), int(iters), _stream_handle(stream),
+                                   ctypes.byref(flops)), "dg_fp64_fma_probe")
+    return flops.value
 
 
 def dg_strerror(code):

@@ -312,3 +312,120 @@ def test_status_and_error_paths():
         assert st == dm.DG_OK and counts.sum() == 0
     finally:
         dm.dg_free(ctx)
+
+
+_ORACLE_RUNS = {}
+
+
+def _oracle_run(key, prob, U0, dt, steps):
+    """The oracle's trajectory, shared by the face schedules of one case."""
+    if key not in _ORACLE_RUNS:
+        _ORACLE_RUNS[key] = dg.run(prob, U0, dt, steps)
+    return _ORACLE_RUNS[key]
+
+
+@pytest.mark.parametrize("faces", FACES)
+def test_step_parity_rain3d_20_steps(faces):
+    """20 SSPRK(4,3) steps of 3-D warm rain on an 8 x 6 x 5 Q4 mesh (240
+    elements, 120 stage tiles, five element layers per column) against the
+    oracle: relative L2 <= 1e-11 per field."""
+    prob, _ = oracle_problem(3, (8, 6, 5), (16e3, 12e3, 10e3), 4, (True, True, False), True)
+    U0 = perturbed_state(prob, 29)
+    dt = dg.cfl_dt(prob, U0, 0.05)
+    Uo = _oracle_run("rain3d_8x6x5_q4", prob, U0, dt, 20)
+    ctx = library_context(prob, faces=faces)
+    try:
+        dm.dg_set_state(ctx, np.ascontiguousarray(U0), dm.DG_HOST)
+        dm.dg_step(ctx, dt, 20)
+        Ug = np.empty_like(U0)
+        dm.dg_get_state(ctx, Ug, dm.DG_HOST)
+        for f in range(prob.nf):
+            rel = np.linalg.norm(Ug[f] - Uo[f]) / np.linalg.norm(Uo[f])
+            assert rel <= 1e-11, (dg.field_names(3, True)[f], rel)
+    finally:
+        dm.dg_free(ctx)
+
+
+@pytest.mark.parametrize("precision", [dm.DG_FP64, dm.DG_FP32_BULK, dm.DG_FP32_PERT])
+def test_newton_cap_reports_unconverged_nodes(precision):
+    """With the Newton cap set to one iteration the split cannot reach its
+    tolerance at cloudy nodes: dg_saturation_split counts them and dg_step
+    returns DG_ENOCONV.  Back at the default cap the same context steps
+    cleanly (no device trap, nothing left in the counters)."""
+    prob, U = _setup("rain2d_q2_walls")
+    dtype = torch.float64 if precision == dm.DG_FP64 else torch.float32
+    if precision != dm.DG_FP64:
+        U = U.astype(np.float32).astype(np.float64)
+    dt = dg.cfl_dt(prob, U, 0.05)
+    ctx = library_context(prob, precision=precision)
+    try:
+        Ud = to_device(U, dtype)
+        n = prob.mesh.Ne * prob.mesh.Np
+        outs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
+        assert dm.dg_saturation_split(ctx, Ud, *outs) == 0
+        dm.dg_set_newton_limit(ctx, 1)
+        assert dm.dg_saturation_split(ctx, Ud, *outs) > 0
+        dm.dg_set_state(ctx, Ud, dm.DG_DEVICE)
+        assert dm.lib().dg_step(ctx, dt, 1) == dm.DG_ENOCONV
+        dm.dg_set_newton_limit(ctx, 50)
+        dm.dg_set_state(ctx, Ud, dm.DG_DEVICE)
+        dm.dg_step(ctx, dt, 2)
+        st, counts = dm.dg_check_status(ctx)
+        assert st == dm.DG_OK and counts.sum() == 0
+        with pytest.raises(dm.DGError):
+            dm.dg_set_newton_limit(ctx, 0)
+    finally:
+        dm.dg_free(ctx)
+
+
+def _falling_rain_3d():
+    prob, _ = oracle_problem(3, (4, 3, 3), (4e3, 3e3, 3e3), 2, (True, False, False), True)
+    U0 = initial.bubble_state(prob, 2.0, [2e3, 1.5e3, 1.2e3], [1.0e3, 1.0e3, 0.8e3], H=3e3)
+    xs = prob.mesh.node_coords()
+    U0[prob.i_m[1]] += 1.0 * np.sin(np.pi * xs[1] / 3e3) * np.sin(np.pi * xs[2] / 3e3)
+    U0[prob.i_rr] = 1e-3 * np.exp(-(xs[2] / 0.8e3) ** 2) * (0.6 + 0.4 * np.cos(2 * np.pi * xs[0] / 4e3))
+    return prob, U0
+
+
+def _fallout_case(case):
+    from tests.test_oracle_dg import _falling_rain_walls
+    return _falling_rain_walls() if case == "walls2d" else _falling_rain_3d()
+
+
+@pytest.mark.parametrize("faces", FACES)
+@pytest.mark.parametrize("precision", [dm.DG_FP64, dm.DG_FP32_BULK, dm.DG_FP32_PERT])
+@pytest.mark.parametrize("case", ["walls2d", "wall_y_3d"])
+def test_fallout_matches_oracle_and_closes_the_water_budget(case, precision, faces):
+    """dg_reduce's fall-out (out[8]) after 10 steps against the oracle's
+    (dg.run_with_fallout: the wall outflow integrated by the same stages),
+    and the library's own budget: the water perturbation (out[1]) plus the
+    fall-out is constant.  Float64: fall-out to 1e-11 relative, budget to
+    1e-13 of the total water; float32 forms: 1e-5 and 2e-8 (the float32
+    state rounds the water densities by 6e-8 relative at every stage)."""
+    from tests.test_oracle_dg import water_total
+    prob, U0 = _fallout_case(case)
+    fp64 = precision == dm.DG_FP64
+    if not fp64:
+        U0 = U0.astype(np.float32).astype(np.float64)
+    dt = dg.cfl_dt(prob, U0, 0.05)
+    key = (case, fp64)
+    if key not in _ORACLE_RUNS:
+        _ORACLE_RUNS[key] = dg.run_with_fallout(prob, U0, dt, 10)
+    Uo, Fo = _ORACLE_RUNS[key]
+    W0 = water_total(prob, U0)
+    ctx = library_context(prob, precision=precision, faces=faces)
+    try:
+        host = np.ascontiguousarray(U0 if fp64 else U0.astype(np.float32))
+        dm.dg_set_state(ctx, host, dm.DG_HOST)
+        r0 = dm.dg_reduce(ctx)
+        assert r0[8] == 0.0
+        dm.dg_step(ctx, dt, 10)
+        r1 = dm.dg_reduce(ctx)
+        assert Fo > 1e-3 * dg.mass_integral(prob, U0[prob.i_rr])
+        assert abs(r1[8] - Fo) <= (1e-11 if fp64 else 1e-5) * abs(Fo), (r1[8], Fo)
+        assert abs(r1[1] + r1[8] - r0[1]) <= (1e-13 if fp64 else 2e-8) * W0
+        # a new state starts the fall-out again
+        dm.dg_set_state(ctx, host, dm.DG_HOST)
+        assert dm.dg_reduce(ctx)[8] == 0.0
+    finally:
+        dm.dg_free(ctx)

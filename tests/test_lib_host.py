@@ -76,3 +76,16 @@ def test_null_context_is_rejected(lib):
     assert h.dg_reduce(None, None) == lib.DG_EINVAL
     assert h.dg_get_info(None, None) == lib.DG_EINVAL
     lib.dg_free(None)
+
+
+def test_new_entry_points_validate_before_the_gpu(lib):
+    h = lib.lib()
+    assert h.dg_set_newton_limit(None, 5) == lib.DG_EINVAL
+    assert h.dg_selftest_math(None, 0, None, None, 1) == lib.DG_EINVAL
+    # dg_rhs_noalloc refuses the face pass and meshes beyond 32-bit indexing
+    # before it touches a device (the pointers are never dereferenced)
+    for kw in (dict(n=(4, 4), faces=lib.DG_FACES_PASS), dict(n=(1 << 21, 4)),
+               dict(n=(1 << 20, 1 << 20))):
+        cfg = lib.make_config(2, kw["n"], (1e3, 1e3), 2, 1, 1, lib.DG_FP64,
+                              faces=kw.get("faces", 0))
+        assert lib.dg_rhs_noalloc_rc(cfg, 8, 8, 8, 16) == lib.DG_EINVAL

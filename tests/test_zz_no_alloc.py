@@ -5,7 +5,8 @@ device, a latency-critical loop, a fixed start-up memory budget) use
 dg_rhs_noalloc, whose scratch is a fixed device array inside the library.
 This file checks, through the C interface, that two calls in a row give the
 same tendencies as dg_rhs (within the tolerance of the other parity tests:
-1e-12 of the per-field flux scale) and that a mesh too large for the array
+1e-12 of the per-field flux scale), that failures are counted until
+dg_rhs_noalloc_status reads them, and that a mesh too large for the array
 is refused.  It is named so that pytest collects it last.
 """
 import numpy as np
@@ -64,6 +65,32 @@ def test_noalloc_rhs_matches_dg_rhs_twice(name):
         assert np.all(err <= 1e-12 * scale), (call, err / scale)
 
 
+def test_noalloc_counts_failures_until_they_are_read():
+    """A non-finite node is counted by every call that meets it, and the
+    count stays in the fixed scratch array until dg_rhs_noalloc_status reads
+    and clears it."""
+    dim, n, L, k, per, rain = CASES["bubble2d_q3"]
+    prob, _ = oracle_problem(dim, n, L, k, per, rain)
+    U = perturbed_state(prob, 23)
+    bad = U.copy()
+    bad[prob.i_E, 3, 5] = np.nan
+    cfg = dm.make_config(dim, n, L, k, 1, rain, dm.DG_FP64, prob.g, 0.0)
+    bn, bf = _base_tables(prob)
+    Ud, Bd = to_device(U, torch.float64), to_device(bad, torch.float64)
+    out = torch.empty_like(Ud)
+    dm.dg_rhs_noalloc_status()                      # start from clear counters
+    dm.dg_rhs_noalloc(cfg, bn, bf, Bd, out)
+    dm.dg_rhs_noalloc(cfg, bn, bf, Bd, out)
+    st, counts = dm.dg_rhs_noalloc_status()
+    assert st == dm.DG_ENONPHYS and counts.tolist() == [0, 2]
+    st, counts = dm.dg_rhs_noalloc_status()
+    assert st == dm.DG_OK and counts.tolist() == [0, 0]
+    dm.dg_rhs_noalloc(cfg, bn, bf, Ud, out)
+    st, counts = dm.dg_rhs_noalloc_status()
+    assert st == dm.DG_OK and counts.tolist() == [0, 0]
+    assert torch.isfinite(out).all()
+
+
 def test_noalloc_rejects_meshes_beyond_the_scratch_size():
     # 3-D Q4 with rain needs about 17 kB of scratch per element
     cfg = dm.make_config(3, (16, 16, 16), (1e3, 1e3, 1e3), 4, 3, 1, dm.DG_FP64)
@@ -71,6 +98,6 @@ def test_noalloc_rejects_meshes_beyond_the_scratch_size():
     bf = torch.zeros(4 * 17, dtype=torch.float64, device="cuda")
     U = torch.zeros(7 * 16 ** 3 * 125, dtype=torch.float64, device="cuda")
     out = torch.zeros_like(U)
-    assert dm.dg_rhs_noalloc_status(cfg, bn, bf, U, out) == dm.DG_EINVAL
+    assert dm.dg_rhs_noalloc_rc(cfg, bn, bf, U, out) == dm.DG_EINVAL
     cfg32 = dm.make_config(2, (4, 4), (1e3, 1e3), 2, 1, 1, dm.DG_FP32_BULK)
-    assert dm.dg_rhs_noalloc_status(cfg32, bn, bf, U, out) == dm.DG_EINVAL
+    assert dm.dg_rhs_noalloc_rc(cfg32, bn, bf, U, out) == dm.DG_EINVAL
