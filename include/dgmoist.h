@@ -375,12 +375,14 @@ long long dg_ensemble_dofs(const dg_ensemble *ens);
 /* Set the members' time steps dt[n] (s, host) and the launch shape:
  * blocks_per_sm persistent CTAs per SM (capped by occupancy), the order of
  * work items (0 member by member, 1 round-robin over members, 2 largest
- * members first) and the register budget regs (0: 128 registers per thread,
- * two CTAs per SM; 1: 80 registers, three CTAs per SM); re-derives each
- * member's split and traces if needed and re-captures the step graph.
- * Synchronises. */
+ * members first), the register budget regs (0: 128 registers per thread,
+ * two CTAs per SM; 1: 80 registers, three CTAs per SM) and tiles_per_item
+ * (1..64) element tiles of one member per work item (a CTA takes that many
+ * consecutive tiles at once: fewer queue operations and barriers per
+ * element, coarser balance); re-derives each member's split and traces if
+ * needed and re-captures the step graph.  Synchronises. */
 int dg_ensemble_configure(dg_ensemble *ens, const double *dt, int blocks_per_sm, int item_order,
-                          int regs);
+                          int regs, int tiles_per_item);
 
 /* The persistent grid size and the number of work items (element tiles)
  * of the captured step. */

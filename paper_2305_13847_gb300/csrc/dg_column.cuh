@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(ColShape<S>::NT, ColShape<S>::MINB) k_column(K
                 Real unew[S::NF];
 #pragma unroll
                 for (int f = 0; f < S::NF; ++f) {
-                    Real v = A.beta * u[f] + A.gdt * R[f];
+                    // one explicit fma: every stage kernel rounds the update alike
+                    Real v = fma(A.gdt, R[f], A.beta * u[f]);
                     if (nonzero(A.alpha)) v = fma(A.alpha, A.Un[f * nodes + gi], v);
                     unew[f] = v;
                 }

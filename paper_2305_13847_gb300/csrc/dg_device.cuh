@@ -1816,7 +1816,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             Real un[S::NF];
 #pragma unroll
             for (int f = 0; f < S::NF; ++f) {
-                Real v = A.beta * u[f] + A.gdt * R[f];
+                // one explicit fma: every stage kernel rounds the update alike
+                Real v = fma(A.gdt, R[f], A.beta * u[f]);
                 if (nonzero(A.alpha)) v = fma(A.alpha, A.Un[f * nodes + gi], v);
                 un[f] = v;
             }

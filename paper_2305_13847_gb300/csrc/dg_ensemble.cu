@@ -30,6 +30,7 @@ struct EnsMember {
     float g_half, g_sixth;
     double fall_w[4];    // the stages' weights in the step for the rain fall-out
     int K, rain;
+    int tiles;           // element tiles of this member
 };
 
 template <int K, bool RAIN>
@@ -59,13 +60,17 @@ __device__ __noinline__ void ens_tile(const KArgs<float> &A, int tile, unsigned 
 
 // MINB: CTAs per SM the register budget is sized for (2: 128 registers per
 // thread, 3: 80); one of the autotuner's knobs.
+// An item is up to tiles_per_item consecutive element tiles of one member
+// (items[i] = (member, first tile)).
 template <int MINB>
 __global__ void __launch_bounds__(kEnsThreads, MINB) k_ens_stage(const EnsMember *members,
                                                              const int2 *items, int n_items,
-                                                             int stage, unsigned int *counter) {
+                                                             int tiles_per_item, int stage,
+                                                             unsigned int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ KArgs<float> s_args;
-    __shared__ int s_item, s_k, s_rain;
+    __shared__ int s_item, s_k, s_rain, s_member;
+    if (threadIdx.x == 0) s_member = -1;
     // work queue, not a wait: every pass takes the next item from a counter
     // that only grows, so a CTA leaves after at most n_items + 1 passes
     for (;;) {
@@ -75,14 +80,18 @@ __global__ void __launch_bounds__(kEnsThreads, MINB) k_ens_stage(const EnsMember
         if (it >= n_items) break;
         const int2 wi = items[it];
         const EnsMember *m = members + wi.x;
-        {
+        // the member's arguments stay in shared memory while the CTA's items
+        // belong to the same member (s_member was set before the last barrier)
+        const bool fresh = wi.x != s_member;
+        if (fresh) {
             const int *src = reinterpret_cast<const int *>(&m->args);
             int *dst = reinterpret_cast<int *>(&s_args);
             for (int i = threadIdx.x; i < (int)(sizeof(KArgs<float>) / sizeof(int)); i += blockDim.x)
                 dst[i] = src[i];
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && fresh) {
+            s_member = wi.x;
             // SSPRK(4,3) Shu-Osher stages; the traces of U^n sit in trace[0] at each step start
             float *Un = m->U[0], *Uw = m->U[1];
             switch (stage) {
@@ -105,25 +114,27 @@ __global__ void __launch_bounds__(kEnsThreads, MINB) k_ens_stage(const EnsMember
             s_rain = m->rain;
         }
         __syncthreads();
-        const int tile = wi.y;
-        if (s_rain) {
-            switch (s_k) {
-                case 1: ens_tile<1, true>(s_args, tile, smem_raw); break;
-                case 2: ens_tile<2, true>(s_args, tile, smem_raw); break;
-                case 3: ens_tile<3, true>(s_args, tile, smem_raw); break;
-                case 4: ens_tile<4, true>(s_args, tile, smem_raw); break;
-                default: ens_tile<5, true>(s_args, tile, smem_raw); break;
+        const int t_end = min(wi.y + tiles_per_item, m->tiles);
+        for (int tile = wi.y; tile < t_end; ++tile) {
+            if (s_rain) {
+                switch (s_k) {
+                    case 1: ens_tile<1, true>(s_args, tile, smem_raw); break;
+                    case 2: ens_tile<2, true>(s_args, tile, smem_raw); break;
+                    case 3: ens_tile<3, true>(s_args, tile, smem_raw); break;
+                    case 4: ens_tile<4, true>(s_args, tile, smem_raw); break;
+                    default: ens_tile<5, true>(s_args, tile, smem_raw); break;
+                }
+            } else {
+                switch (s_k) {
+                    case 1: ens_tile<1, false>(s_args, tile, smem_raw); break;
+                    case 2: ens_tile<2, false>(s_args, tile, smem_raw); break;
+                    case 3: ens_tile<3, false>(s_args, tile, smem_raw); break;
+                    case 4: ens_tile<4, false>(s_args, tile, smem_raw); break;
+                    default: ens_tile<5, false>(s_args, tile, smem_raw); break;
+                }
             }
-        } else {
-            switch (s_k) {
-                case 1: ens_tile<1, false>(s_args, tile, smem_raw); break;
-                case 2: ens_tile<2, false>(s_args, tile, smem_raw); break;
-                case 3: ens_tile<3, false>(s_args, tile, smem_raw); break;
-                case 4: ens_tile<4, false>(s_args, tile, smem_raw); break;
-                default: ens_tile<5, false>(s_args, tile, smem_raw); break;
-            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -156,6 +167,7 @@ struct dg_ensemble {
     int blocks_per_sm = 2;
     int item_order = 1;
     int regs = 0;                    // 0: k_ens_stage<2>, 1: k_ens_stage<3>
+    int tiles_per_item = 1;
     int sm_count = 0;
     int grid = 0;
     long long dofs = 0;
@@ -200,6 +212,7 @@ int build(dg_ensemble *E) {
         m.g_sixth = (float)(E->dt[i] / 6.0);
         m.K = c->cfg.order;
         m.rain = c->cfg.rain;
+        m.tiles = E->tiles[i];
     }
     {
         RefData<float> refs[5];
@@ -216,15 +229,16 @@ int build(dg_ensemble *E) {
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             return E->members[a]->nodes > E->members[b]->nodes;
         });
+    const int tpi = E->tiles_per_item;
     if (E->item_order == 1) {
         int maxt = 0;
         for (int i = 0; i < E->n; ++i) maxt = std::max(maxt, E->tiles[i]);
-        for (int t = 0; t < maxt; ++t)
+        for (int t = 0; t < maxt; t += tpi)
             for (int i : order)
                 if (t < E->tiles[i]) items.push_back(make_int2(i, t));
     } else {
         for (int i : order)
-            for (int t = 0; t < E->tiles[i]; ++t) items.push_back(make_int2(i, t));
+            for (int t = 0; t < E->tiles[i]; t += tpi) items.push_back(make_int2(i, t));
     }
     E->n_items = (int)items.size();
     if (E->d_members) cudaFree(E->d_members);
@@ -257,8 +271,8 @@ int build(dg_ensemble *E) {
         return DG_ECUDA;
     cudaError_t err = cudaMemsetAsync(E->d_counters, 0, 4 * sizeof(unsigned int), E->stream);
     for (int s = 0; s < 4 && err == cudaSuccess; ++s) {
-        kern<<<grid, kEnsThreads, kEnsSmem, E->stream>>>(E->d_members, E->d_items, E->n_items, s,
-                                                         E->d_counters + s);
+        kern<<<grid, kEnsThreads, kEnsSmem, E->stream>>>(E->d_members, E->d_items, E->n_items,
+                                                         E->tiles_per_item, s, E->d_counters + s);
         err = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;
@@ -351,10 +365,12 @@ int dg_ensemble_launch_shape(const dg_ensemble *E, int *grid, int *n_items) {
 }
 
 int dg_ensemble_configure(dg_ensemble *E, const double *dt, int blocks_per_sm, int item_order,
-                          int regs) {
+                          int regs, int tiles_per_item) {
     if (!E || !dt || blocks_per_sm < 1 || item_order < 0 || item_order > 2) return DG_EINVAL;
     if (regs != 0 && regs != 1) return DG_EINVAL;
+    if (tiles_per_item < 1 || tiles_per_item > 64) return DG_EINVAL;
     E->regs = regs;
+    E->tiles_per_item = tiles_per_item;
     for (int i = 0; i < E->n; ++i) {
         if (!(dt[i] > 0.0)) return DG_EINVAL;
         E->dt[i] = dt[i];

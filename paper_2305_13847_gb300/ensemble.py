@@ -5,7 +5,8 @@ launch per stage, captured in a CUDA graph.  This module marshals the
 member descriptions (paper_2305_13847_gb300.inputs.ensemble_members), picks
 each member's time step from its own wave speed, and times the library's
 launch-shape knobs -- persistent CTAs per SM, work-item order, register
-budget -- keeping the fastest and writing the measured table as JSON.
+budget, element tiles per work item -- keeping the fastest and writing the
+measured table as JSON.
 """
 import itertools
 import json
@@ -44,19 +45,22 @@ def time_steps(ens, steps, stream):
 
 
 def autotune(ens, dt, stream, steps=2, json_path=None,
-             blocks_per_sm=(1, 2, 3), orders=(0, 1, 2), regs=(0, 1)):
+             blocks_per_sm=(1, 2, 3), orders=(0, 1, 2), regs=(0, 1), tiles_per_item=(1, 2, 4, 8)):
     """Time every launch shape for `steps` steps (after one warm-up step);
-    configure the fastest and return (best, table)."""
+    configure the fastest and return (best, table).  The shape: persistent
+    CTAs per SM, work-item order, register budget and element tiles per work
+    item (the elements a CTA takes at once)."""
     table = []
-    for r, b, o in itertools.product(regs, blocks_per_sm, orders):
-        dm.dg_ensemble_configure(ens, dt, b, o, r)
+    for r, b, o, tp in itertools.product(regs, blocks_per_sm, orders, tiles_per_item):
+        dm.dg_ensemble_configure(ens, dt, b, o, r, tp)
         grid, items = dm.dg_ensemble_launch_shape(ens)
         dm.dg_ensemble_step(ens, 1)
         ms = time_steps(ens, steps, stream)
-        table.append({"regs": r, "blocks_per_sm": b, "item_order": o, "grid": grid,
-                      "items": items, "ms_per_step": ms})
+        table.append({"regs": r, "blocks_per_sm": b, "item_order": o, "tiles_per_item": tp,
+                      "grid": grid, "items": items, "ms_per_step": ms})
     best = min(table, key=lambda t: t["ms_per_step"])
-    dm.dg_ensemble_configure(ens, dt, best["blocks_per_sm"], best["item_order"], best["regs"])
+    dm.dg_ensemble_configure(ens, dt, best["blocks_per_sm"], best["item_order"], best["regs"],
+                             best["tiles_per_item"])
     if json_path:
         with open(json_path, "w") as f:
             json.dump({"when": time.strftime("%Y-%m-%dT%H:%M:%S"), "device": torch.cuda.get_device_name(),

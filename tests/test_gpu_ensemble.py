@@ -89,7 +89,9 @@ def test_ensemble_matches_members_stepped_alone():
         ens = ensemble.open_ensemble(ms, stream)
         try:
             dts = ensemble.member_dt(ens, ms)
-            dm.dg_ensemble_configure(ens, dts, 2, 1, 0)
+            # three tiles per work item: tiles of a stage are independent, so
+            # grouping them changes nothing in the result
+            dm.dg_ensemble_configure(ens, dts, 2, 1, 0, 3)
             dm.dg_ensemble_step(ens, 3)
             for i, m in enumerate(ms):
                 ctx_e = dm.dg_ensemble_member(ens, i)
@@ -117,8 +119,10 @@ def test_autotuner_writes_table(tmp_path):
             dts = ensemble.member_dt(ens, ms)
             path = os.path.join(str(tmp_path), "tune.json")
             best, table = ensemble.autotune(ens, dts, stream, steps=1, json_path=path,
-                                            blocks_per_sm=(1, 2), orders=(0, 1), regs=(0, 1))
-            assert len(table) == 8
+                                            blocks_per_sm=(1, 2), orders=(0, 1), regs=(0, 1),
+                                            tiles_per_item=(1, 4))
+            assert len(table) == 16
+            assert {t["tiles_per_item"] for t in table} == {1, 4}
             d = json.load(open(path))
             assert d["best"] == best and d["dofs"] == dm.dg_ensemble_dofs(ens)
             dm.dg_ensemble_step(ens, 1)

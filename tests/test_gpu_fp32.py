@@ -51,7 +51,10 @@ def _setup(name, seed=5):
 FORMS = [dm.DG_FP32_BULK, dm.DG_FP32_PERT]
 
 
-@pytest.mark.parametrize("faces", [dm.DG_FACES_INLINE, dm.DG_FACES_PASS])
+SCHEDULES = [dm.DG_FACES_INLINE, dm.DG_FACES_PASS, dm.DG_FACES_COLUMN]
+
+
+@pytest.mark.parametrize("faces", SCHEDULES)
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp32_rhs_close_to_oracle(name, form, faces):
@@ -124,7 +127,7 @@ def test_fp32_bubble2d_100_steps_within_1e5(form):
 _ORACLE = {}
 
 
-@pytest.mark.parametrize("faces", [dm.DG_FACES_INLINE, dm.DG_FACES_PASS])
+@pytest.mark.parametrize("faces", SCHEDULES)
 @pytest.mark.parametrize("form", FORMS)
 def test_fp32_rain3d_100_steps_within_1e5(form, faces):
     """100 steps of 3-D warm rain in both float32 forms and both face

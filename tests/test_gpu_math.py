@@ -222,6 +222,8 @@ def test_rho_vs_table_against_the_closed_form(ctx):
         # 4 c_4 d^3 / c_1 ~ (4/24) (d ln rho_vs/dT)^3 d^3 with |d| <= 1/256 K +
         # 3e-5 K, is at most 2.7e-10 relative (0.30 /K at 150 K)
         assert rel_d.max() <= 5e-10, stats
-        # outside the table: the closed form itself
-        out = (Tt < 150.0) | (Tt > 399.0)
+        # outside the table (the library decides on the float32-rounded T):
+        # the closed form itself
+        T32 = Tt.astype(np.float32).astype(np.float64)
+        out = (T32 < 150.0) | (T32 > 399.0)
         assert same_bits(ours[out], ref[out]).all()

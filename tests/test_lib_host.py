@@ -58,7 +58,7 @@ def test_strerror(lib):
     dict(dim=4), dict(dim=1), dict(order=0), dict(order=6), dict(n=(0, 4, 4)),
     dict(n=(4, -1, 4)), dict(L=(1e3, 0.0, 1e3)), dict(rain=2), dict(precision=7),
     dict(n=(4096, 4096, 64), order=5),      # n_nodes * n_fields beyond 2^31 - 1
-    dict(faces=3), dict(faces=-1),
+    dict(faces=4), dict(faces=-1),
 ])
 def test_init_mesh_rejects_bad_configs(lib, kw):
     base = dict(dim=3, n=(4, 4, 4), L=(1e3, 1e3, 1e3), order=3, periodic_mask=3, rain=1,
@@ -89,3 +89,9 @@ def test_new_entry_points_validate_before_the_gpu(lib):
         cfg = lib.make_config(2, kw["n"], (1e3, 1e3), 2, 1, 1, lib.DG_FP64,
                               faces=kw.get("faces", 0))
         assert lib.dg_rhs_noalloc_rc(cfg, 8, 8, 8, 16) == lib.DG_EINVAL
+
+
+def test_column_schedule_is_float32_only(lib):
+    cfg = lib.make_config(3, (4, 4, 4), (1e3, 1e3, 1e3), 3, 3, 1, lib.DG_FP64,
+                          faces=lib.DG_FACES_COLUMN)
+    assert lib.dg_init_mesh_status(cfg) == lib.DG_ENOTIMPL

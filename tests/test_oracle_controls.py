@@ -191,3 +191,20 @@ def test_fallout_advanced_by_the_stage_weights_fails_the_water_budget_pin(monkey
     monkeypatch.setattr(dg, "run_with_fallout", planted)
     with pytest.raises(AssertionError):
         pins.test_water_budget_closes_with_the_fallout()
+
+
+def test_flipped_evaporation_temperature_term_fails_its_pin(monkeypatch):
+    """The temperature term of the evaporation coefficient of Eq. (2.4) with
+    the wrong sign: the coefficient no longer vanishes at 314.17 K."""
+    from oracle import constants as C
+    monkeypatch.setattr(C, "S_EV_B", -C.S_EV_B)
+    with pytest.raises(AssertionError):
+        thermo_pins.test_evaporation_coefficient_vanishes_where_the_paper_puts_it()
+
+
+def test_sound_speed_without_gamma_fails_the_wave_speed_pin(monkeypatch):
+    """c = sqrt(p / rho) (gamma dropped): the hand value of the largest wave
+    speed at a uniform state no longer matches."""
+    monkeypatch.setattr(thermo, "gamma_moist", lambda *a: 1.0)
+    with pytest.raises(AssertionError):
+        pins.test_max_wave_speed_and_cfl_step_by_hand()

@@ -8,6 +8,7 @@ order in time of the full moist step (with a planted first-order step that
 the pin rejects) and the degree-of-freedom counts printed in Section 4.3.
 """
 import json
+import math
 import os
 
 import numpy as np
@@ -492,3 +493,35 @@ def test_water_budget_closes_with_the_fallout():
     assert abs(water_total(prob, U) + F - W0) <= 1e-8 * F
     # the state itself is that of the plain run
     assert np.array_equal(U, dg.run(prob, U0, dt, 10))
+
+
+def test_mass_integral_is_the_exact_integral_of_a_polynomial():
+    """The Gauss rule of the DG space integrates polynomials of degree 2k+1
+    per direction exactly: mass_integral of x^2 z^3 (2-D, k = 2) and of
+    x y^2 z (3-D, k = 1) over the domain equals the closed form.  A wrong
+    Jacobian |K|/2^d or weight fails this by a constant factor."""
+    mesh = Mesh(2, (3, 4), (3000.0, 2000.0), 2, (True, False))
+    prob = dg.Problem(mesh, *zero_base(mesh), rain=False)
+    x, z = mesh.node_coords()
+    Lx, Lz = mesh.L
+    assert dg.mass_integral(prob, x ** 2 * z ** 3) == pytest.approx(Lx ** 3 / 3 * Lz ** 4 / 4, rel=1e-14)
+    mesh = Mesh(3, (2, 3, 2), (2000.0, 3000.0, 1500.0), 1, (True, True, False))
+    prob = dg.Problem(mesh, *zero_base(mesh), rain=True)
+    x, y, z = mesh.node_coords()
+    Lx, Ly, Lz = mesh.L
+    assert dg.mass_integral(prob, x * y ** 2 * z) == pytest.approx(
+        Lx ** 2 / 2 * Ly ** 3 / 3 * Lz ** 2 / 2, rel=1e-14)
+
+
+def test_max_wave_speed_and_cfl_step_by_hand():
+    """At a uniform dry state (rho_d = 1.1 kg/m^3, T = 290 K, u = (12, -5)
+    m/s) the largest wave speed is |u| + c with c^2 = (c_vd + R_d)/c_vd p /
+    rho, p = rho_d R_d T (Section 3.2 in the dry limit); the CFL step is
+    cfl min(h) over it.  Constants are the paper's Table 1 values."""
+    mesh = Mesh(2, (4, 3), (4000.0, 1500.0), 2, (True, False))
+    prob = dg.Problem(mesh, *zero_base(mesh), rain=False, g=0.0)
+    U = uniform_state(prob, 1.1, 0.0, 0.0, (12.0, -5.0), 290.0)
+    c = math.sqrt((718.0 + 287.05) / 718.0 * 1.1 * 287.05 * 290.0 / 1.1)
+    lam = 13.0 + c
+    assert dg.max_wave_speed(prob, U) == pytest.approx(lam, rel=1e-13)
+    assert dg.cfl_dt(prob, U, 0.1) == pytest.approx(0.1 * 500.0 / lam, rel=1e-13)

@@ -188,3 +188,30 @@ def test_source_structure():
     # no rain: no evaporation and no accretion
     assert thermo.sources(T, 0.5 * rvs, 1e-3, 0.0)[0] == 0.0
     assert thermo.sources(T, 0.5 * rvs, 1e-3, 0.0)[2] == 0.0
+
+
+def test_evaporation_coefficient_vanishes_where_the_paper_puts_it():
+    """Eq. (2.4): the evaporation coefficient 3.86e-3 - 9.41e-5 (T - T_ref)
+    (printed constants, tests/golden) changes sign at T_ref + 3.86e-3/9.41e-5
+    = 314.17 K.  S_ev of subsaturated air is positive below that, zero there
+    and negative above; its ratio to the value at T_ref falls linearly with
+    slope -9.41e-5/3.86e-3 per K.  A dropped or mis-signed temperature term
+    fails this."""
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    micro, tref = gold["microphysics"], gold["table1_constants"]["T_ref"]
+    a, b = micro["S_ev_a"], micro["S_ev_b"]
+    T0 = tref + a / b
+    r = 1e-4
+
+    def s_ev(T):
+        rvs = float(thermo.saturation_vapour_density(T))
+        return float(thermo.sources(T, 0.5 * rvs, 0.0, r)[0]) / (0.5 * rvs)
+
+    assert s_ev(T0 - 1.0) > 0 and s_ev(T0 + 1.0) < 0
+    # T0 itself carries a rounding of ~6e-14 K, so the zero holds to ~1e-13
+    assert abs(s_ev(T0)) <= 1e-12 * abs(s_ev(T0 - 1.0))
+    ref = s_ev(tref)
+    for dT in (-20.0, 5.0, 30.0):
+        T = tref + dT
+        assert s_ev(T) / ref == pytest.approx(1.0 - (b / a) * dT, rel=1e-12)
