@@ -45,8 +45,11 @@ class Problem:
     Eq. (2.9)-(2.10)); rho_r has no base part.
     """
 
-    def __init__(self, mesh, base_node, base_face, rain, g=C.G_DEFAULT, rho_w=None):
+    def __init__(self, mesh, base_node, base_face, rain, g=C.G_DEFAULT, rho_w=None, rain_floor=None):
         self.mesh = mesh
+        # complex-step tangents only: fractional rain powers differentiated at
+        # max(rho_r, rain_floor) (thermo.floored_root); None = exact
+        self.rain_floor = rain_floor
         self.base_node = {k: np.asarray(v, dtype=np.float64) for k, v in base_node.items()}
         self.base_face = {k: np.asarray(v, dtype=np.float64) for k, v in base_face.items()}
         self.rain = bool(rain)
@@ -84,7 +87,7 @@ def primitives(prob, Uf, base, T, rho_v, p_prime):
     P["rho_v"] = rho_v
     P["rho_c"] = P["rho_m"] - rho_v
     if prob.rain:
-        P["v_r"] = thermo.rain_velocity(P["rho_r"], P["rho_m"], prob.rho_w)
+        P["v_r"] = thermo.rain_velocity(P["rho_r"], P["rho_m"], prob.rho_w, prob.rain_floor)
     else:
         P["v_r"] = np.zeros_like(P["rho_d"])
     return P
@@ -146,7 +149,7 @@ def source(prob, Uf, P):
     """
     G = [np.zeros_like(P["rho_d"]) for _ in range(prob.nf)]
     if prob.rain:
-        s_ev, s_au, s_ac = thermo.sources(P["T"], P["rho_v"], P["rho_c"], P["rho_r"])
+        s_ev, s_au, s_ac = thermo.sources(P["T"], P["rho_v"], P["rho_c"], P["rho_r"], prob.rain_floor)
         G[prob.i_rm] = s_ev - s_au - s_ac
         G[prob.i_rr] = s_au + s_ac - s_ev
     rho_pert = Uf[prob.i_rd] + Uf[prob.i_rm] + (Uf[prob.i_rr] if prob.rain else 0.0)

@@ -177,7 +177,23 @@ def sound_speed(rho_d, rho_v, rho_c, rho_r, p):
     return np.sqrt(gamma_moist(rho_d, rho_v, rho_c, rho_r) * p / rho)
 
 
-def rain_velocity(rho_r, rho_m, rho_w=None):
+def floored_root(rho_r, n, floor):
+    """rho_r^(1/n) for a complex-step tangent whose fractional power is
+    differentiated at max(rho_r, floor): the real part is max(rho_r, 0)^(1/n),
+    the imaginary part (the tangent) (1/n) max(rho_r, floor)^(1/n - 1)
+    Im(rho_r), and 0 where rho_r <= 0.
+
+    This is the linearisation reading of the adjoint: the powers p < 1 of the
+    warm-rain closure (Eq. (2.4), v_r) have unbounded derivatives as rho_r ->
+    0+, so they are differentiated at the floor below it."""
+    re = np.maximum(np.real(rho_r), 0.0)
+    val = re ** (1.0 / n)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        der = np.where(np.real(rho_r) > 0.0, (1.0 / n) * np.maximum(re, floor) ** (1.0 / n - 1.0), 0.0)
+    return val + 1j * der * np.imag(rho_r)
+
+
+def rain_velocity(rho_r, rho_m, rho_w=None, floor=None):
     """Terminal rain speed v_r (Section 2.1).
 
     v_r = (pi rho_w N0)^(-1/8) v0 Gamma(4.5)/6 rho_r^(1/8).
@@ -185,6 +201,8 @@ def rain_velocity(rho_r, rho_m, rho_w=None):
     (reading taken literally); passing ``rho_w`` > 0 uses a constant instead.
     Negative or zero rain gives v_r = 0 (the fractional power of a negative
     DG undershoot is not defined; the paper is silent).
+    ``floor``: for complex-step tangents only, rho_r^(1/8) is differentiated
+    at max(rho_r, floor) (``floored_root``); real inputs are unaffected.
     """
     rho_r = _arr(rho_r)
     rr = np.maximum(rho_r, 0.0)
@@ -194,21 +212,32 @@ def rain_velocity(rho_r, rho_m, rho_w=None):
         rw = np.full_like(rr, float(rho_w))
     coef = C.V0_R * C.GAMMA_4_5 / 6.0
     with np.errstate(divide="ignore", invalid="ignore"):
+        if floor is not None and np.iscomplexobj(rho_r):
+            y = floored_root(rho_r, 8, floor)
+            v = coef * (np.pi * rw * C.N0_R) ** (-0.125) * y
+            return np.where((np.real(rho_r) > 0.0) & (np.real(rw) > 0.0), v, 0.0)
         v = coef * (np.pi * rw * C.N0_R) ** (-0.125) * rr ** 0.125
     return np.where((rr > 0.0) & (rw > 0.0), v, 0.0)
 
 
-def sources(T, rho_v, rho_c, rho_r):
+def sources(T, rho_v, rho_c, rho_r, floor=None):
     """Warm-rain source terms S_ev, S_au, S_ac of Eq. (2.4), q_au = 0.
 
     Fractional powers use max(rho_r, 0) (negative rain from DG undershoot has
-    no real power; the paper is silent).
+    no real power; the paper is silent).  ``floor``: for complex-step tangents
+    only, the powers are taken as powers of x = rho_r^(1/16) differentiated at
+    max(rho_r, floor) (``floored_root``); real inputs are unaffected.
     """
     rr = np.maximum(_arr(rho_r), 0.0)
     rvs = saturation_vapour_density(T)
-    s_ev = ((C.S_EV_A - C.S_EV_B * (T - C.T_ref)) * (1.0 + C.S_EV_C * rr ** (3.0 / 16.0))
-            * (rvs - rho_v) * rr ** 0.5)
+    if floor is not None and np.iscomplexobj(rho_r):
+        x = floored_root(_arr(rho_r), 16, floor)
+        p316, p12, p78 = x ** 3, x ** 8, x ** 14
+    else:
+        p316, p12, p78 = rr ** (3.0 / 16.0), rr ** 0.5, rr ** (7.0 / 8.0)
+    s_ev = ((C.S_EV_A - C.S_EV_B * (T - C.T_ref)) * (1.0 + C.S_EV_C * p316)
+            * (rvs - rho_v) * p12)
     # S_au = 0.001 max(rho_c - q_au rho, 0) with q_au = 0
     s_au = C.S_AU * np.maximum(rho_c, 0.0)
-    s_ac = C.S_AC * rho_c * rr ** (7.0 / 8.0)
+    s_ac = C.S_AC * rho_c * p78
     return s_ev, s_au, s_ac

@@ -525,3 +525,24 @@ def test_max_wave_speed_and_cfl_step_by_hand():
     lam = 13.0 + c
     assert dg.max_wave_speed(prob, U) == pytest.approx(lam, rel=1e-13)
     assert dg.cfl_dt(prob, U, 0.1) == pytest.approx(0.1 * 500.0 / lam, rel=1e-13)
+
+
+def test_floored_tangent_equals_the_exact_one_above_the_floor():
+    """With every rain density above the floor, the complex-step tangent of
+    the right-hand side with the rain floor (powers of x = rho_r^(1/16))
+    equals the exact one (direct powers) to rounding."""
+    mesh = Mesh(2, (4, 3), (4000.0, 3000.0), 2, (True, False))
+    node, face, _ = initial.base_tables(mesh, H=3000.0)
+    exact = dg.Problem(mesh, node, face, rain=True)
+    floored = dg.Problem(mesh, node, face, rain=True, rain_floor=1e-12)
+    U = initial.bubble_state(exact, 2.0, [2e3, 1e3], [1e3, 0.8e3], H=3000.0)
+    xs = mesh.node_coords()
+    U[exact.i_rr] = 1e-4 * (0.6 + 0.4 * np.sin(2 * np.pi * xs[0] / 4000.0))
+    U[exact.i_m[0]] += 1.0
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(U.shape) * (np.abs(U).max(axis=(1, 2), keepdims=True) + 1e-6)
+    h = 1e-30
+    t0 = dg.rhs(exact, U + 1j * h * v).imag / h
+    t1 = dg.rhs(floored, U + 1j * h * v).imag / h
+    scale = np.abs(t0).reshape(exact.nf, -1).max(axis=1)
+    assert np.all(np.abs(t1 - t0).reshape(exact.nf, -1).max(axis=1) <= 1e-12 * scale)

@@ -215,3 +215,28 @@ def test_evaporation_coefficient_vanishes_where_the_paper_puts_it():
     for dT in (-20.0, 5.0, 30.0):
         T = tref + dT
         assert s_ev(T) / ref == pytest.approx(1.0 - (b / a) * dT, rel=1e-12)
+
+
+def test_floored_root_tangent():
+    """The linearisation reading of the adjoint (fractional rain powers
+    differentiated at max(rho_r, floor)), as a complex-step tangent: above
+    the floor the tangent is the exact derivative (1/n) r^(1/n - 1), below it
+    the derivative at the floor, (1/n) floor^(1/n - 1), continuous at the
+    floor; 0 for r <= 0; the value is r^(1/n) throughout."""
+    h, floor = 1e-30, 1e-12
+    for n in (8, 16):
+        r = np.array([3e-5, 2e-12, 1e-12, 5e-13, 1e-20, 0.0, -1e-13])
+        y = thermo.floored_root(r + 1j * h, n, floor)
+        assert np.allclose(y.real, np.maximum(r, 0.0) ** (1.0 / n), rtol=1e-15, atol=0)
+        d = y.imag / h
+        for ri, di in zip(r, d):
+            if ri >= floor:
+                assert di == pytest.approx(ri ** (1.0 / n - 1.0) / n, rel=1e-14)
+            elif ri > 0:
+                assert di == pytest.approx(floor ** (1.0 / n - 1.0) / n, rel=1e-14)
+            else:
+                assert di == 0.0
+    # real inputs: the floor is ignored
+    r = np.array([1e-13, 2e-5])
+    assert np.array_equal(thermo.sources(280.0, 1e-3, 1e-4, r, floor=1e-12)[2],
+                          thermo.sources(280.0, 1e-3, 1e-4, r)[2])
