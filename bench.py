@@ -446,25 +446,33 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto
     return w, ctx, info, dt
 
 
-# DRAM bytes per node and SSPRK stage (k_face + k_stage, face pass) from ncu
-# captures (dram__bytes_read.sum + dram__bytes_write.sum) of the small cases
-# named below; they scale with the node count for the same dimension, order
-# and form.  None (-> traffic null) for any other configuration.
+# DRAM bytes per node and SSPRK stage of the face-pass schedule (k_face +
+# k_stage), dram__bytes_read.sum + dram__bytes_write.sum from the ncu
+# captures summarised in the named profile, which gives the command; they
+# scale with the node count for the same dimension, order and form.  None
+# (-> traffic null) for any other configuration or schedule.  A capture
+# must be retaken whenever one of the two kernels changes.
 PROFILED_TRAFFIC = {
-    (3, 4, "fp64"): 411.7,        # 32x32x32 Q4 capture: k_face 117.5 + k_stage 294.2
-    (3, 3, "fp32_bulk"): 237.8,   # 64x64x32 Q3 capture: k_face 74.5 + k_stage 163.3
-    (3, 3, "fp32_pert"): 237.8,   # 64x64x32 Q3 capture: k_face 74.5 + k_stage 163.3
+    (3, 4, "fp64"): (411.8, "profiles/k_face_k_stage_rain3d_q4_fp64.md: 32x32x32 Q4, "
+                            "k_face 117.6 + k_stage 294.2 B/node"),
+    (3, 3, "fp32_bulk"): (237.8, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
+                                 "k_face 74.5 + k_stage 163.3 B/node"),
+    (3, 3, "fp32_pert"): (237.8, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
+                                 "k_face 74.5 + k_stage 163.3 B/node"),
 }
 
 
 def _traffic(w, precision, info):
+    """(bytes per stage at this mesh, source) from PROFILED_TRAFFIC, or (None, None)."""
     if info.launches_per_stage != 2:
-        return None
-    b = PROFILED_TRAFFIC.get((w["dim"], w["order"], precision))
-    return None if b is None else b * info.n_nodes
+        return None, None
+    entry = PROFILED_TRAFFIC.get((w["dim"], w["order"], precision))
+    if entry is None:
+        return None, None
+    return entry[0] * info.n_nodes, "ncu capture, " + entry[1]
 
 
-def _roofline(info, word, t_total, steps, peak, peak_kind, traffic=None):
+def _roofline(info, word, t_total, steps, peak, peak_kind, traffic=(None, None)):
     # one SSPRK stage: k_stage, preceded by k_face when the face pass is on
     launch_s = t_total / (STAGES * steps)
     bytes_per_launch = algorithmic_bytes_per_node(info.n_fields, word) * info.n_nodes
@@ -474,7 +482,7 @@ def _roofline(info, word, t_total, steps, peak, peak_kind, traffic=None):
               "k_stage (fused RHS + SSPRK stage + next split)")
     return {"bound": "hbm", "kernel": kernel,
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic,
+            "frac": achieved / peak, "traffic": traffic[0], "traffic_source": traffic[1],
             "algorithmic_bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": 1000.0 * launch_s}
 
@@ -514,7 +522,7 @@ def fp64_flops_per_node(dim, order, nf, rain):
     return float(sum(items.values())), items
 
 
-def fp64_alu_roofline(info, w, t_total, steps, sm_count, sm_mhz, probe_tflops, hbm, traffic):
+def fp64_alu_roofline(info, w, t_total, steps, sm_count, sm_mhz, probe_tflops, hbm):
     launch_s = t_total / (STAGES * steps)
     fpn, items = fp64_flops_per_node(w["dim"], w["order"], info.n_fields, w["rain"])
     achieved = fpn * info.n_nodes / launch_s / 1e12
@@ -523,7 +531,8 @@ def fp64_alu_roofline(info, w, t_total, steps, sm_count, sm_mhz, probe_tflops, h
            "unit": "TFLOP/s", "frac": achieved / peak,
            "peak_kind": "derived: %d SMs x %d FP64 FMA/clk x 2 flop x %.0f MHz (median SM clock "
                         "sampled in the timed region)" % (sm_count, FP64_FMA_PER_SM_CLK, sm_mhz),
-           "traffic": traffic, "algorithmic_flops_per_node": fpn,
+           "traffic": hbm["traffic"], "traffic_source": hbm["traffic_source"],
+           "algorithmic_flops_per_node": fpn,
            "flops_per_node_items": items, "avg_launch_ms": 1000.0 * launch_s,
            "hbm": {k: hbm[k] for k in ("achieved", "peak", "peak_kind", "unit", "frac",
                                        "algorithmic_bytes_per_launch")}}
@@ -780,8 +789,7 @@ def run_gb300(args):
         except Exception:
             probe = None
         sm_mhz = clocks.get("sm_mhz") or 2070.0
-        roof = fp64_alu_roofline(info, w, t_max, args.steps, sm_count, sm_mhz, probe, roof,
-                                 roof["traffic"])
+        roof = fp64_alu_roofline(info, w, t_max, args.steps, sm_count, sm_mhz, probe, roof)
     dm.dg_free(ctx)
     del host
 

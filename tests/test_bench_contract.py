@@ -72,12 +72,38 @@ def test_roofline_arithmetic():
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(174.0 * info.n_nodes)
     assert r["achieved"] == pytest.approx(174.0 * info.n_nodes / launch_s / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / peak)
-    assert r["traffic"] == pytest.approx(bench.PROFILED_TRAFFIC[(3, 4, "fp64")] * info.n_nodes)
+    assert r["traffic"] == pytest.approx(bench.PROFILED_TRAFFIC[(3, 4, "fp64")][0] * info.n_nodes)
+    # every traffic figure names the profile summary it comes from
+    assert r["traffic_source"].startswith("ncu capture, profiles/")
+    src = r["traffic_source"].split(", ", 1)[1].split(":")[0]
+    assert os.path.exists(os.path.join(ROOT, src)), src
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    # no capture for this configuration, or the inline schedule: traffic null
-    assert bench._traffic({"dim": 2, "order": 3}, "fp64", info) is None
+    # no capture for this configuration, or the inline / column schedule: traffic null
+    assert bench._traffic({"dim": 2, "order": 3}, "fp64", info) == (None, None)
     inline = types.SimpleNamespace(n_fields=7, n_nodes=10, launches_per_stage=1)
-    assert bench._traffic({"dim": 3, "order": 4}, "fp64", inline) is None
+    assert bench._traffic({"dim": 3, "order": 4}, "fp64", inline) == (None, None)
+
+
+def test_fp64_alu_roofline():
+    """The float64 form's roofline: algorithmic flops per node (the items sum
+    to the total) x nodes over the mean stage time, against 152 SMs x 2 FP64
+    FMA per clock x 2 flop x the sampled clock."""
+    sys.path.insert(0, ROOT)
+    import importlib
+    import types
+    bench = importlib.import_module("bench")
+    fpn, items = bench.fp64_flops_per_node(3, 4, 7, 1)
+    assert fpn == pytest.approx(sum(items.values()))
+    assert items["volume"] == 2 * 3 * 7 * 5 and items["lift"] == 4 * 3 * 7
+    info = types.SimpleNamespace(n_fields=7, n_nodes=16_384_000, launches_per_stage=2)
+    hbm = bench._roofline(info, 8, 0.5, 10, 6705.5, "measured", (None, None))
+    r = bench.fp64_alu_roofline(info, {"dim": 3, "order": 4, "rain": 1}, 0.5, 10, 152, 2070.0, 1.25, hbm)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+    assert r["achieved"] == pytest.approx(fpn * info.n_nodes / (0.5 / 40) / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["hbm"]["frac"] == pytest.approx(hbm["frac"])
+    assert r["fp64_fma_probe"]["frac_of_probe"] == pytest.approx(r["achieved"] / 1.25)
 
 
 def test_whole_job_rate_is_weak_scaling():
