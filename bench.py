@@ -455,10 +455,10 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto
 PROFILED_TRAFFIC = {
     (3, 4, "fp64"): (411.8, "profiles/k_face_k_stage_rain3d_q4_fp64.md: 32x32x32 Q4, "
                             "k_face 117.6 + k_stage 294.2 B/node"),
-    (3, 3, "fp32_bulk"): (237.8, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
-                                 "k_face 74.5 + k_stage 163.3 B/node"),
-    (3, 3, "fp32_pert"): (237.8, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
-                                 "k_face 74.5 + k_stage 163.3 B/node"),
+    (3, 3, "fp32_bulk"): (238.0, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
+                                 "k_face 74.7 + k_stage 163.3 B/node"),
+    (3, 3, "fp32_pert"): (238.1, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
+                                 "k_face 74.8 + k_stage 163.3 B/node"),
 }
 
 

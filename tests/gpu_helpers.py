@@ -85,3 +85,48 @@ def flux_scale(prob, U, elements=None):
     return np.array([max(max(np.abs(fl[j][f]).max() for j in range(mesh.dim)),
                          lam * np.abs(Ue[f]).max(), pmax if f in prob.i_m else 0.0) * fac
                      for f in range(prob.nf)])
+
+
+def cone_dilate(mesh, cols, r):
+    """Element columns (ix, iy) within r elements of cols (square, periodic)."""
+    nx, ny = mesh.n[0], mesh.n[1]
+    out = set()
+    for ix, iy in cols:
+        for dx in range(-r, r + 1):
+            for dy in range(-r, r + 1):
+                out.add(((ix + dx) % nx, (iy + dy) % ny))
+    return out
+
+
+def cone_elements(mesh, cols):
+    nx, ny, nz = mesh.n
+    return np.array(sorted(ix + nx * (iy + ny * iz) for ix, iy in cols for iz in range(nz)),
+                    dtype=np.int64)
+
+
+def oracle_cone_steps(prob, U, dt, nsteps, cols, inplace=False):
+    """nsteps SSPRK(4,3) steps of the oracle (3-D), exact on the element
+    columns cols = [(ix, iy), ...]: a stage couples an element to its face
+    neighbours only, so stage s is evaluated on cols dilated by the number
+    of stages after it, and the columns' values equal those of the full run
+    (tests/test_oracle_dg.py checks that).  inplace: advance U itself (no
+    copy of a full-size state); the start of each step is kept only on that
+    step's largest set."""
+    mesh = prob.mesh
+    total = 4 * nsteps
+    V = U if inplace else U.copy()
+    s = 0
+    for _ in range(nsteps):
+        el0 = cone_elements(mesh, cone_dilate(mesh, cols, total - 1 - s))
+        u0 = V[:, el0].copy()
+        for k in range(4):
+            el = cone_elements(mesh, cone_dilate(mesh, cols, total - 1 - s))
+            L = dg.rhs(prob, V, elements=el)
+            # the Shu-Osher stages of dg.ssprk43_step, term by term
+            if k == 2:
+                V[:, el] = ((2.0 / 3.0) * u0[:, np.searchsorted(el0, el)] + (1.0 / 3.0) * V[:, el]
+                            + (dt / 6.0) * L)
+            else:
+                V[:, el] = V[:, el] + 0.5 * dt * L
+            s += 1
+    return V

@@ -546,3 +546,23 @@ def test_floored_tangent_equals_the_exact_one_above_the_floor():
     t1 = dg.rhs(floored, U + 1j * h * v).imag / h
     scale = np.abs(t0).reshape(exact.nf, -1).max(axis=1)
     assert np.all(np.abs(t1 - t0).reshape(exact.nf, -1).max(axis=1) <= 1e-12 * scale)
+
+
+def test_cone_steps_equal_the_full_run_on_their_columns():
+    """The full-size GPU test follows sampled element columns with the oracle
+    on their domain of dependence only (tests/gpu_helpers.oracle_cone_steps):
+    on a small periodic mesh that gives the full run's values on the columns,
+    to the rounding of the subset matrix products."""
+    from tests.gpu_helpers import cone_elements, oracle_cone_steps, oracle_problem, perturbed_state
+    prob, _ = oracle_problem(3, (12, 11, 3), (12e3, 11e3, 3e3), 2, (True, True, False), True)
+    U = perturbed_state(prob, 3)
+    dt = dg.cfl_dt(prob, U, 0.05)
+    cols = [(5, 5), (0, 10)]
+    Vc = oracle_cone_steps(prob, U, dt, 1, cols)
+    Vf = dg.run(prob, U, dt, 1)
+    sel = cone_elements(prob.mesh, cols)
+    for f in range(prob.nf):
+        assert np.abs(Vc[f][sel] - Vf[f][sel]).max() <= 1e-15 * np.abs(Vf[f]).max(), f
+    # and outside the cone of the last stage the values are stale: the
+    # construction really evaluates only the dependence domain
+    assert not np.array_equal(Vc, Vf)
