@@ -579,10 +579,13 @@ def measure_ensemble(torch, dm, inputs, args, world, dist):
             ks = sorted(set(m["order"] for m in members))
             return {
                 "workload": "ensemble: %d 2-D warm-rain bubbles, meshes %dx%d..%dx%d, orders %s, "
-                            "FP32-bulk, one persistent launch per stage in a CUDA graph"
+                            "FP32-bulk, one step per CUDA graph, autotuned schedule: %s"
                             % (len(members), min(m["n"][0] for m in members),
                                min(m["n"][1] for m in members), max(m["n"][0] for m in members),
-                               max(m["n"][1] for m in members), ks),
+                               max(m["n"][1] for m in members), ks,
+                               "each member's face-pass step as a parallel branch"
+                               if best["schedule"] == "branches"
+                               else "one persistent launch per stage"),
                 "dofs": dofs, "value": whole_job_rate(world, dofs * STAGES, ms / 1000.0), "unit": UNIT,
                 "ms_per_step": ms, "autotuned": best, "candidates": len(table)}
         finally:

@@ -350,11 +350,16 @@ int dg_set_stabilisation(dg_ctx *ctx, const dg_stabilisation *s);
 
 /* ---- Batched ensemble (not in the paper, which runs one case at a time) ----
  * Many independent 2-D meshes (any sizes, orders 1..5, rain on or off),
- * FP32-bulk, advanced together: each SSPRK(4,3) stage is one persistent
- * launch whose CTAs take element tiles of any member from an atomic work
- * counter and run the single-mesh stage code for that member's order; one
- * step (counter resets + four stage launches) is captured in a CUDA graph
- * and replayed.  Results are bitwise those of dg_step on each member. */
+ * FP32-bulk, advanced together.  One step is captured in a CUDA graph and
+ * replayed, in one of two schedules:
+ *  - persistent (dg_ensemble_configure): each SSPRK(4,3) stage is one
+ *    persistent launch whose CTAs take element tiles of any member from an
+ *    atomic work counter and run the single-mesh stage code for that
+ *    member's order, with the face fluxes evaluated in the tile;
+ *  - branches (dg_ensemble_configure_branches): each member's step is
+ *    dg_step's own launches (face pass, then stage, four times), and the
+ *    members form parallel branches of the graph.
+ * Results are bitwise those of dg_step on each member in both. */
 typedef struct dg_ensemble dg_ensemble;
 
 /* Create n members (cfgs[i].dim == 2, precision DG_FP32_BULK or DG_FP32_PERT) and build
@@ -384,14 +389,24 @@ long long dg_ensemble_dofs(const dg_ensemble *ens);
 int dg_ensemble_configure(dg_ensemble *ens, const double *dt, int blocks_per_sm, int item_order,
                           int regs, int tiles_per_item);
 
-/* The persistent grid size and the number of work items (element tiles)
- * of the captured step. */
+/* Set the members' time steps dt[n] (s, host) and capture the branch
+ * schedule: members are dealt, largest first, to `lanes` (>= 1; capped at
+ * n) parallel branches, each member to the branch with the fewest DOFs so
+ * far; a branch steps its members one after another.  Every member must
+ * use the face pass (created with DG_FACES_AUTO or DG_FACES_PASS), else
+ * DG_EINVAL.  Re-derives each member's split and traces if needed.
+ * Synchronises.  Errors: DG_EINVAL, DG_ECUDA. */
+int dg_ensemble_configure_branches(dg_ensemble *ens, const double *dt, int lanes);
+
+/* Persistent schedule: the grid size and the number of work items (element
+ * tiles) of the captured step.  Branch schedule: the number of branches and
+ * the number of members. */
 int dg_ensemble_launch_shape(const dg_ensemble *ens, int *grid, int *n_items);
 
 /* Replay the captured step nsteps times.  dg_ensemble_step synchronises and
  * returns the worst member status (DG_ENONPHYS before DG_ENOCONV);
  * dg_ensemble_step_async only enqueues.  DG_ESTATE before
- * dg_ensemble_configure. */
+ * dg_ensemble_configure or dg_ensemble_configure_branches. */
 int dg_ensemble_step(dg_ensemble *ens, int nsteps);
 int dg_ensemble_step_async(dg_ensemble *ens, int nsteps);
 

@@ -572,8 +572,6 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
             c->ref32.dliftm_s[j][a] = (float)v[2];
             c->ref32.dliftp_s[j][a] = (float)v[3];
         }
-    c->ref64.scaled = 1;
-    c->ref32.scaled = 1;
 
     // z-levels
     c->z_node.resize(M.nzlev_node);

@@ -122,13 +122,12 @@ struct RefData {
     Real dmat[6][6];
     Real dlm[6], dlp[6];
     Real dliftm[6], dliftp[6];
-    // scaled != 0: dhat_s[j] = (2/h_j) dhat of this mesh, so that the volume
-    // contraction needs no separate scaling (read from the mesh's own kernel
-    // arguments, also where the other tables are shared between meshes)
+    // dhat_s[j] = (2/h_j) dhat of this mesh, so that the volume contraction
+    // needs no separate scaling (read from the mesh's own kernel arguments,
+    // also where the other tables are shared between meshes)
     Real dhat_s[3][6][6];
     Real liftm_s[3][6], liftp_s[3][6];    // (2/h_j) l_a(-+1)/w_a
     Real dliftm_s[3][6], dliftp_s[3][6];  // (2/h_j)^2 l_a'(-+1)/w_a
-    int scaled;
 };
 
 template <typename Real>
@@ -238,6 +237,67 @@ template <int D, int P1>
 __device__ __forceinline__ int face_q_vert(int j, int q) {
     if (D == 2) return q;           // j == 0: remaining direction is the vertical
     return q / P1;                  // j = 0 or 1: remaining (., vertical)
+}
+
+// A CTA's copy of the mesh's scaled reference tables, per direction j:
+// dhat_s[j][a][0 .. P1) for each a, then liftm_s[j], liftp_s[j], dliftm_s[j],
+// dliftp_s[j].  A thread indexes them by its own a_j; in shared memory the
+// threads of a warp read their different entries in one access, where the
+// kernel-parameter bank serves one address at a time.  The float64 tile
+// reads them here (measured -1.4 % per step); the float32 tile, whose
+// shared-memory pipe is the busier one, from the parameter bank.
+template <class S>
+struct Coef {
+    static constexpr int ROWS = S::P1 * S::P1;
+    static constexpr int LM = ROWS, LP = ROWS + S::P1, DLM = ROWS + 2 * S::P1, DLP = ROWS + 3 * S::P1;
+    static constexpr int BLK = (ROWS + 4 * S::P1 + 3) / 4 * 4;   // whole 16-byte groups (float)
+    static constexpr int N = S::D * BLK;
+};
+
+template <class S, typename Real>
+__device__ __forceinline__ void coef_fill(const RefData<Real> &r, Real *s_cf) {
+    using C = Coef<S>;
+    for (int i = threadIdx.x; i < C::N; i += blockDim.x) {
+        const int j = i / C::BLK, k = i - j * C::BLK;
+        Real v = Real(0);
+        if (k < C::LM) v = r.dhat_s[j][k / S::P1][k % S::P1];
+        else if (k < C::LP) v = r.liftm_s[j][k - C::LM];
+        else if (k < C::DLM) v = r.liftp_s[j][k - C::LP];
+        else if (k < C::DLP) v = r.dliftm_s[j][k - C::DLM];
+        else if (k < C::DLP + S::P1) v = r.dliftp_s[j][k - C::DLP];
+        s_cf[i] = v;
+    }
+}
+
+// Volume term of Eq. (3.2), sum factorised, at node a of local element el:
+// R_a += sum_i dhat_s[j][a_j][i] F_j(line node i) for every direction j, from
+// the nodal fluxes s_fl [D][NF][STR]; coefficients from s_cf (Coef, float64)
+// or from the kernel arguments (float32)
+template <class S, typename Real, int STR>
+__device__ __forceinline__ void volume_term(const KArgs<Real> &A, const Real *s_fl,
+                                            const Real *s_cf, int el, int a, Real *R) {
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) {
+        const int aj = digit<S::D, S::P1>(a, j);
+        const int st = stride_of<S::P1>(j);
+        const int b0 = el * S::NP + a - aj * st;
+        Real c[S::P1];
+#pragma unroll
+        for (int i = 0; i < S::P1; ++i) {
+            if constexpr (sizeof(Real) == sizeof(double))
+                c[i] = s_cf[j * Coef<S>::BLK + aj * S::P1 + i];
+            else
+                c[i] = A.ref.dhat_s[j][aj][i];
+        }
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) {
+            const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
+            Real acc = R[f];
+#pragma unroll
+            for (int i = 0; i < S::P1; ++i) acc = fma(c[i], fl[i * st], acc);
+            R[f] = acc;
+        }
+    }
 }
 
 __device__ __forceinline__ void elem_multi(const MeshData &M, int e, int &i0, int &i1, int &i2) {
@@ -1227,12 +1287,12 @@ constexpr int MODE_STAGE = 1;
 // Shared memory of a stage tile: nodal fluxes s_fl [D][NF][EPB NP], node
 // values for the traces s_tr [NTR][EPB NP], outward face fluxes s_fh
 // [EPB][2D][NFP][NFP1] (with diffusion NFP = 2 NF: the fluxes, then the
-// symmetry terms), per-element indices and, with diffusion, the element's
-// vertex coefficients [EPB][2][2^D] and its alpha sums [EPB][2].  s_tr is
-// needed before the volume phase only when the float32 inline form
-// interpolates its own traces in the face phase, or with diffusion (the
-// derivatives of the node values); otherwise it is filled after the volume
-// phase and shares s_fl.
+// symmetry terms), per-element indices, with diffusion the element's vertex
+// coefficients [EPB][2][2^D] and its alpha sums [EPB][2], and (float64) the
+// coefficient tables s_cf (Coef).  s_tr is needed before the volume phase
+// only when the float32 inline form interpolates its own traces in the face
+// phase, or with diffusion (the derivatives of the node values); otherwise
+// it is filled after the volume phase and shares s_fl.
 template <class S, typename Real, bool PF, bool DIFF = false>
 __host__ __device__ constexpr bool tr_shares_fl() {
     return (PF || sizeof(Real) == sizeof(double)) && !DIFF;
@@ -1248,12 +1308,19 @@ __host__ __device__ constexpr size_t stage_fh_offset() {
              S::EPB * S::NP) + 15) / 16 * 16;
 }
 
+// byte offset of the coefficient tables s_cf (Coef; 16-byte aligned)
+template <class S, typename Real, bool PF, bool DIFF>
+__host__ __device__ constexpr size_t stage_cf_offset() {
+    constexpr size_t fh = (size_t)S::EPB * S::NFACE * (DIFF ? 2 * S::NF : S::NF) * S::NFP1;
+    return (stage_fh_offset<S, Real, PF, DIFF>() + sizeof(Real) * fh +
+            sizeof(int) * 16 * (size_t)S::EPB +  // per element: 2D neighbours, vertical index
+            (DIFF ? sizeof(Real) * (size_t)S::EPB * (2 * S::NCORNER + 2) : 0) + 15) / 16 * 16;
+}
+
 template <class S, typename Real, bool PF = false, bool DIFF = false>
 constexpr size_t stage_smem_bytes() {
-    constexpr size_t fh = (size_t)S::EPB * S::NFACE * (DIFF ? 2 * S::NF : S::NF) * S::NFP1;
-    return stage_fh_offset<S, Real, PF, DIFF>() + sizeof(Real) * fh +
-           sizeof(int) * 16 * (size_t)S::EPB +  // per element: 2D neighbours, vertical index
-           (DIFF ? sizeof(Real) * (size_t)S::EPB * (2 * S::NCORNER + 2) : 0);
+    return stage_cf_offset<S, Real, PF, DIFF>() +
+           (sizeof(Real) == sizeof(double) ? sizeof(Real) * (size_t)Coef<S>::N : 0);
 }
 
 // completes the asynchronous copies issued by this thread
@@ -1589,6 +1656,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     int *s_info = reinterpret_cast<int *>(s_fh + S::EPB * EB);                            // [EPB][16]
     Real *s_al = reinterpret_cast<Real *>(s_info + 16 * S::EPB);        // DIFF: [EPB][2][NCORNER]
     Real *s_red = s_al + S::EPB * 2 * S::NCORNER;                       // DIFF: [EPB][2]
+    Real *s_cf = reinterpret_cast<Real *>(smem_raw + stage_cf_offset<S, Real, PF, DIFF>());
     const MeshData &M = A.M;
     const int ne = M.ne;
     const size_t nodes = (size_t)ne * S::NP;
@@ -1616,6 +1684,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     // face pass: copy the tile's face values to shared memory while the
     // nodal phases run (one contiguous block per face)
     if (PF) cp_async_faces<S, Real, NFP>(A.fbuf, A.ftab, s_fh, bidx, min(S::EPB, ne - bidx * S::EPB));
+
+    if (sizeof(Real) == sizeof(double)) coef_fill<S, Real>(A.ref, s_cf);
 
     // per element: neighbours across the 2D faces (inline faces) and the
     // vertical index
@@ -1712,38 +1782,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     }
 
     // ---- phase 2a: volume term, sum factorised: R_a += (2/h_j) sum_i dhat[a_j][i] F_j(i)
-    if (valid && A.ref.scaled) {
-#pragma unroll
-        for (int j = 0; j < S::D; ++j) {
-            const int aj = digit<S::D, S::P1>(a, j);
-            const int st = stride_of<S::P1>(j);
-            const int b0 = el * S::NP + a - aj * st;
-#pragma unroll
-            for (int f = 0; f < S::NF; ++f) {
-                const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
-                Real acc = R[f];
-#pragma unroll
-                for (int i = 0; i < S::P1; ++i) acc = fma(A.ref.dhat_s[j][aj][i], fl[i * st], acc);
-                R[f] = acc;
-            }
-        }
-    } else if (valid) {
-#pragma unroll
-        for (int j = 0; j < S::D; ++j) {
-            const int aj = digit<S::D, S::P1>(a, j);
-            const int st = stride_of<S::P1>(j);
-            const int b0 = el * S::NP + a - aj * st;
-            const Real sc = mconst<Real>(M.two_over_h[j], M.two_over_h_f[j]);
-#pragma unroll
-            for (int f = 0; f < S::NF; ++f) {
-                const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
-                Real acc = Real(0);
-#pragma unroll
-                for (int i = 0; i < S::P1; ++i) acc = fma(ref.dhat[aj][i], fl[i * st], acc);
-                R[f] = fma(sc, acc, R[f]);
-            }
-        }
-    }
+    if (valid) volume_term<S, Real, STR>(A, s_fl, s_cf, el, a, R);
 
     // ---- phase 2b: Lax-Friedrichs flux at every face point of the CTA's elements
     if (PF) {
@@ -1782,12 +1821,17 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         for (int j = 0; j < S::D; ++j) {
             const int aj = digit<S::D, S::P1>(a, j);
             const int q = face_q<S::D, S::P1>(a, j);
-            const Real sc = mconst<Real>(M.two_over_h[j], M.two_over_h_f[j]);
             const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * NFP) * S::NFP1 + q;
             const Real *fp = s_fh + ((el * S::NFACE + 2 * j + 1) * NFP) * S::NFP1 + q;
-            const bool scl = A.ref.scaled != 0;
-            const Real cm = scl ? A.ref.liftm_s[j][aj] : sc * ref.liftm[aj];
-            const Real cp = scl ? A.ref.liftp_s[j][aj] : sc * ref.liftp[aj];
+            const Real *cf = s_cf + j * Coef<S>::BLK;
+            Real cm, cp;
+            if constexpr (sizeof(Real) == sizeof(double)) {
+                cm = cf[Coef<S>::LM + aj];
+                cp = cf[Coef<S>::LP + aj];
+            } else {
+                cm = A.ref.liftm_s[j][aj];
+                cp = A.ref.liftp_s[j][aj];
+            }
             // the low face holds the outward flux (inline) or G along +e_j,
             // which is minus this element's outward flux (face pass):
             // fma(-c, -G, r) = fma(c, G, r) exactly, so both schedules round
@@ -1801,8 +1845,14 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
                 // symmetry term of Eq. (3.7): + (2/h_j)^2 l_a'(s)/w_a S on both faces
                 const Real *sm = fm + S::NF * S::NFP1;
                 const Real *sp = fp + S::NF * S::NFP1;
-                const Real dm = scl ? A.ref.dliftm_s[j][aj] : sc * sc * ref.dliftm[aj];
-                const Real dp = scl ? A.ref.dliftp_s[j][aj] : sc * sc * ref.dliftp[aj];
+                Real dm, dp;
+                if constexpr (sizeof(Real) == sizeof(double)) {
+                    dm = cf[Coef<S>::DLM + aj];
+                    dp = cf[Coef<S>::DLP + aj];
+                } else {
+                    dm = A.ref.dliftm_s[j][aj];
+                    dp = A.ref.dliftp_s[j][aj];
+                }
 #pragma unroll
                 for (int f = 0; f < S::NF; ++f)
                     R[f] = fma(dm, sm[f * S::NFP1], fma(dp, sp[f * S::NFP1], R[f]));

@@ -171,6 +171,7 @@ struct dg_ensemble {
     int sm_count = 0;
     int grid = 0;
     long long dofs = 0;
+    int lanes = 0;                   // > 0: the branch schedule with this many lanes
 };
 
 namespace {
@@ -286,6 +287,103 @@ int build(dg_ensemble *E) {
     return DG_OK;
 }
 
+// Branch schedule: member i's step is dg_step_async on its own context (the
+// single-mesh face pass and stage kernels), issued on lane l(i); the lanes
+// are parallel branches of one captured graph, so members of different
+// lanes run concurrently and members of one lane one after another.
+// Members go, largest first, to the lane with the fewest DOFs so far.
+int build_branches(dg_ensemble *E, int lanes) {
+    destroy_graph(E);
+    lanes = std::max(1, std::min(lanes, E->n));
+    std::vector<int> order(E->n);
+    for (int i = 0; i < E->n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return E->members[a]->nodes * E->members[a]->nf > E->members[b]->nodes * E->members[b]->nf;
+    });
+    std::vector<long long> load(lanes, 0);
+    std::vector<std::vector<int>> lane(lanes);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane[l].push_back(i);
+        load[l] += E->members[i]->nodes * E->members[i]->nf;
+    }
+    std::vector<cudaStream_t> ls(lanes, nullptr);
+    std::vector<cudaEvent_t> join(lanes, nullptr);
+    cudaEvent_t fork = nullptr;
+    int st = DG_OK;
+    for (int l = 0; l < lanes && st == DG_OK; ++l) {
+        if (cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join[l], cudaEventDisableTiming) != cudaSuccess)
+            st = DG_ECUDA;
+    }
+    if (st == DG_OK && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) st = DG_ECUDA;
+    // relaxed capture: a member's first launch of a kernel sets its
+    // shared-memory attribute, which is not a stream operation
+    bool capturing = false;
+    if (st == DG_OK) {
+        if (cudaStreamBeginCapture(E->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) st = DG_ECUDA;
+        else capturing = true;
+    }
+    if (st == DG_OK && cudaEventRecord(fork, E->stream) != cudaSuccess) st = DG_ECUDA;
+    for (int l = 0; l < lanes && st == DG_OK; ++l) {
+        if (cudaStreamWaitEvent(ls[l], fork, 0) != cudaSuccess) {
+            st = DG_ECUDA;
+            break;
+        }
+        for (int i : lane[l]) {
+            dg_ctx *c = E->members[i];
+            const cudaStream_t own = c->stream;
+            c->stream = ls[l];
+            st = dg_step_async(c, E->dt[i], 1);
+            c->stream = own;
+            if (st != DG_OK) break;
+        }
+        if (st == DG_OK && (cudaEventRecord(join[l], ls[l]) != cudaSuccess ||
+                            cudaStreamWaitEvent(E->stream, join[l], 0) != cudaSuccess))
+            st = DG_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    if (capturing) {
+        const cudaError_t end = cudaStreamEndCapture(E->stream, &g);
+        if (st == DG_OK && end != cudaSuccess) st = DG_ECUDA;
+    }
+    if (st == DG_OK) {
+        E->graph = g;
+        g = nullptr;
+        if (cudaGraphInstantiate(&E->exec, E->graph, 0) != cudaSuccess) st = DG_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    if (fork) cudaEventDestroy(fork);
+    for (int l = 0; l < lanes; ++l) {
+        if (join[l]) cudaEventDestroy(join[l]);
+        if (ls[l]) cudaStreamDestroy(ls[l]);
+    }
+    if (st != DG_OK) {
+        destroy_graph(E);
+        return st;
+    }
+    E->lanes = lanes;
+    E->grid = lanes;
+    E->n_items = E->n;
+    return DG_OK;
+}
+
+// dt[i] and, for every member, its split and traces of U^n in trace buffer 0
+int set_dt_and_prepare(dg_ensemble *E, const double *dt) {
+    for (int i = 0; i < E->n; ++i)
+        if (!(dt[i] > 0.0)) return DG_EINVAL;
+    for (int i = 0; i < E->n; ++i) E->dt[i] = dt[i];
+    for (dg_ctx *c : E->members) {
+        if (!c->derived_valid || c->parity != 0) {
+            const int st = ctx_prepare(c, c->U[0], 0);
+            if (st != DG_OK) return st;
+            c->parity = 0;
+            c->derived_valid = true;
+        }
+    }
+    return DG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -369,24 +467,25 @@ int dg_ensemble_configure(dg_ensemble *E, const double *dt, int blocks_per_sm, i
     if (!E || !dt || blocks_per_sm < 1 || item_order < 0 || item_order > 2) return DG_EINVAL;
     if (regs != 0 && regs != 1) return DG_EINVAL;
     if (tiles_per_item < 1 || tiles_per_item > 64) return DG_EINVAL;
+    const int st = set_dt_and_prepare(E, dt);
+    if (st != DG_OK) return st;
     E->regs = regs;
     E->tiles_per_item = tiles_per_item;
-    for (int i = 0; i < E->n; ++i) {
-        if (!(dt[i] > 0.0)) return DG_EINVAL;
-        E->dt[i] = dt[i];
-    }
     E->blocks_per_sm = blocks_per_sm;
     E->item_order = item_order;
-    // each member starts a step with the split and traces of U^n in trace buffer 0
-    for (dg_ctx *c : E->members) {
-        if (!c->derived_valid || c->parity != 0) {
-            const int st = ctx_prepare(c, c->U[0], 0);
-            if (st != DG_OK) return st;
-            c->parity = 0;
-            c->derived_valid = true;
-        }
-    }
+    E->lanes = 0;
     return build(E);
+}
+
+int dg_ensemble_configure_branches(dg_ensemble *E, const double *dt, int lanes) {
+    if (!E || !dt || lanes < 1) return DG_EINVAL;
+    for (dg_ctx *c : E->members)
+        if (!c->face_pass) return DG_EINVAL;
+    const int st = set_dt_and_prepare(E, dt);
+    if (st != DG_OK) return st;
+    const int bs = build_branches(E, lanes);
+    if (bs != DG_OK) return bs;
+    return cudaStreamSynchronize(E->stream) == cudaSuccess ? DG_OK : DG_ECUDA;
 }
 
 int dg_ensemble_step_async(dg_ensemble *E, int nsteps) {

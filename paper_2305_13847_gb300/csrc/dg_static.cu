@@ -171,6 +171,13 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
     M.newton_cap = kMaxNewton;
     if (reference_tables(g.order, A.ref) != DG_OK) return DG_EINVAL;
+    // the volume and lift tables scaled by 2/h_j of this mesh
+    for (int j = 0; j < 3; ++j)
+        for (int a = 0; a < 6; ++a) {
+            for (int i = 0; i < 6; ++i) A.ref.dhat_s[j][a][i] = M.two_over_h[j] * A.ref.dhat[a][i];
+            A.ref.liftm_s[j][a] = M.two_over_h[j] * A.ref.liftm[a];
+            A.ref.liftp_s[j][a] = M.two_over_h[j] * A.ref.liftp[a];
+        }
 
     A.rvs_tab = reinterpret_cast<const double *>(scratch);
     A.flags = reinterpret_cast<unsigned long long *>(scratch + kTableBytes);

@@ -105,6 +105,7 @@ SIGNATURES = [
     ("dg_ensemble_member", _I, [_VP, _I, ctypes.POINTER(_VP)]),
     ("dg_ensemble_dofs", ctypes.c_longlong, [_VP]),
     ("dg_ensemble_configure", _I, [_VP, _VP, _I, _I, _I, _I]),
+    ("dg_ensemble_configure_branches", _I, [_VP, _VP, _I]),
     ("dg_ensemble_launch_shape", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("dg_ensemble_step", _I, [_VP, _I]),
     ("dg_ensemble_step_async", _I, [_VP, _I]),
@@ -375,6 +376,12 @@ def dg_ensemble_configure(ens, dt, blocks_per_sm, item_order, regs, tiles_per_it
     dt = np.ascontiguousarray(dt, dtype=np.float64)
     _check(lib().dg_ensemble_configure(ens, _addr(dt), int(blocks_per_sm), int(item_order), int(regs),
                                        int(tiles_per_item)), "dg_ensemble_configure")
+
+
+def dg_ensemble_configure_branches(ens, dt, lanes):
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    _check(lib().dg_ensemble_configure_branches(ens, _addr(dt), int(lanes)),
+           "dg_ensemble_configure_branches")
 
 
 def dg_ensemble_launch_shape(ens):

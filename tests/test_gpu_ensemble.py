@@ -1,7 +1,7 @@
 """Batched ensemble: every member of an uneven ensemble (orders 1-5, rain on
-and off) against the float64 oracle; the persistent multi-order launch gives
-bitwise the result of stepping every member on its own (same tile code);
-the autotuner runs."""
+and off) against the float64 oracle; the persistent multi-order launch and
+the branch schedule give bitwise the result of stepping every member on its
+own; the autotuner runs."""
 import json
 import os
 
@@ -110,6 +110,67 @@ def test_ensemble_matches_members_stepped_alone():
             dm.dg_ensemble_free(ens)
 
 
+def _states(ens, n):
+    out = []
+    for i in range(n):
+        ctx = dm.dg_ensemble_member(ens, i)
+        info = dm.dg_get_info(ctx)
+        U = np.empty(info.n_fields * info.n_nodes, dtype=np.float32)
+        dm.dg_get_state(ctx, U, dm.DG_HOST)
+        out.append(U)
+    return out
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 7, 64])
+def test_branches_match_members_stepped_alone(lanes):
+    """The branch schedule (every member's dg_step launches as a branch of
+    one graph, `lanes` branches) gives bitwise dg_step on every member, also
+    after switching from the persistent schedule and back."""
+    ms = _members()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ens = ensemble.open_ensemble(ms, stream)
+        try:
+            dts = ensemble.member_dt(ens, ms)
+            dm.dg_ensemble_configure_branches(ens, dts, lanes)
+            assert dm.dg_ensemble_launch_shape(ens) == (min(lanes, len(ms)), len(ms))
+            dm.dg_ensemble_step(ens, 2)
+            dm.dg_ensemble_configure(ens, dts, 2, 1, 0, 1)
+            dm.dg_ensemble_step(ens, 1)
+            dm.dg_ensemble_configure_branches(ens, dts, lanes)
+            dm.dg_ensemble_step(ens, 1)
+            Ue = _states(ens, len(ms))
+            for i, m in enumerate(ms):
+                ctx = workloads.open_workload(m, stream=stream)
+                try:
+                    dm.dg_step(ctx, dts[i], 4)
+                    info = dm.dg_get_info(ctx)
+                    Us = np.empty(info.n_fields * info.n_nodes, dtype=np.float32)
+                    dm.dg_get_state(ctx, Us, dm.DG_HOST)
+                finally:
+                    dm.dg_free(ctx)
+                assert np.array_equal(Ue[i], Us), (i, np.abs(Ue[i] - Us).max())
+        finally:
+            dm.dg_ensemble_free(ens)
+
+
+def test_branches_need_the_face_pass():
+    ms = _members()[:2]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        cfgs = [workloads.config_for(m, faces=dm.DG_FACES_INLINE) for m in ms]
+        bubs = [workloads.bubble_for(m) for m in ms]
+        ens = dm.dg_ensemble_create(cfgs, bubs, stream)
+        try:
+            dts = ensemble.member_dt(ens, ms)
+            with pytest.raises(RuntimeError):
+                dm.dg_ensemble_configure_branches(ens, dts, 2)
+            with pytest.raises(RuntimeError):
+                dm.dg_ensemble_step(ens, 1)
+        finally:
+            dm.dg_ensemble_free(ens)
+
+
 def test_autotuner_writes_table(tmp_path):
     ms = _members()
     stream = torch.cuda.Stream()
@@ -120,9 +181,10 @@ def test_autotuner_writes_table(tmp_path):
             path = os.path.join(str(tmp_path), "tune.json")
             best, table = ensemble.autotune(ens, dts, stream, steps=1, json_path=path,
                                             blocks_per_sm=(1, 2), orders=(0, 1), regs=(0, 1),
-                                            tiles_per_item=(1, 4))
-            assert len(table) == 16
-            assert {t["tiles_per_item"] for t in table} == {1, 4}
+                                            tiles_per_item=(1, 4), lanes=(2, 7))
+            assert len(table) == 18
+            assert {t["tiles_per_item"] for t in table if t["schedule"] == "persistent"} == {1, 4}
+            assert {t["lanes"] for t in table if t["schedule"] == "branches"} == {2, 7}
             d = json.load(open(path))
             assert d["best"] == best and d["dofs"] == dm.dg_ensemble_dofs(ens)
             dm.dg_ensemble_step(ens, 1)
