@@ -269,6 +269,40 @@ __device__ __forceinline__ void coef_fill(const RefData<Real> &r, Real *s_cf) {
     }
 }
 
+// Nodal-flux words per node and direction.  float32 stores the fields as
+// interleaved pairs (2p, 2p + 1), the last pair padded when n_f is odd,
+// [D][(n_f + 1) / 2][STR][2]: the volume term then runs on 64-bit shared
+// loads and paired fmas (fma.rn.f32x2, each lane the scalar fma).  float64
+// keeps [D][n_f][STR].
+template <class S, typename Real>
+__host__ __device__ constexpr int fl_words() {
+    return sizeof(Real) == sizeof(float) ? 2 * ((S::NF + 1) / 2) : S::NF;
+}
+
+// index of field f of direction j at tile node t in the nodal fluxes
+template <class S, typename Real, int STR>
+__device__ __forceinline__ int fl_index(int j, int f, int t) {
+    if constexpr (sizeof(Real) == sizeof(float))
+        return ((j * ((S::NF + 1) / 2) + (f >> 1)) * STR + t) * 2 + (f & 1);
+    else
+        return (j * S::NF + f) * STR + t;
+}
+
+// the fluxes F[0 .. n_f) of direction j at tile node t
+template <class S, typename Real, int STR>
+__device__ __forceinline__ void fl_store(Real *s_fl, int j, int t, const Real *F) {
+    if constexpr (sizeof(Real) == sizeof(float)) {
+        constexpr int NPR = (S::NF + 1) / 2;
+        float2 *fl2 = reinterpret_cast<float2 *>(s_fl);
+#pragma unroll
+        for (int p = 0; p < NPR; ++p)
+            fl2[(j * NPR + p) * STR + t] = make_float2(F[2 * p], 2 * p + 1 < S::NF ? F[2 * p + 1] : 0.0f);
+    } else {
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) s_fl[(j * S::NF + f) * STR + t] = F[f];
+    }
+}
+
 // Volume term of Eq. (3.2), sum factorised, at node a of local element el:
 // R_a += sum_i dhat_s[j][a_j][i] F_j(line node i) for every direction j, from
 // the nodal fluxes s_fl [D][NF][STR]; coefficients from s_cf (Coef, float64)
@@ -281,21 +315,38 @@ __device__ __forceinline__ void volume_term(const KArgs<Real> &A, const Real *s_
         const int aj = digit<S::D, S::P1>(a, j);
         const int st = stride_of<S::P1>(j);
         const int b0 = el * S::NP + a - aj * st;
-        Real c[S::P1];
+        if constexpr (sizeof(Real) == sizeof(double)) {
+            Real c[S::P1];
 #pragma unroll
-        for (int i = 0; i < S::P1; ++i) {
-            if constexpr (sizeof(Real) == sizeof(double))
-                c[i] = s_cf[j * Coef<S>::BLK + aj * S::P1 + i];
-            else
-                c[i] = A.ref.dhat_s[j][aj][i];
-        }
+            for (int i = 0; i < S::P1; ++i) c[i] = s_cf[j * Coef<S>::BLK + aj * S::P1 + i];
 #pragma unroll
-        for (int f = 0; f < S::NF; ++f) {
-            const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
-            Real acc = R[f];
+            for (int f = 0; f < S::NF; ++f) {
+                const Real *fl = s_fl + (j * S::NF + f) * STR + b0;
+                Real acc = R[f];
 #pragma unroll
-            for (int i = 0; i < S::P1; ++i) acc = fma(c[i], fl[i * st], acc);
-            R[f] = acc;
+                for (int i = 0; i < S::P1; ++i) acc = fma(c[i], fl[i * st], acc);
+                R[f] = acc;
+            }
+        } else {
+            // field pairs: lane x is field 2p, lane y field 2p + 1, each the
+            // same fma chain as one field at a time
+            constexpr int NPR = (S::NF + 1) / 2;
+            const float2 *fl2 = reinterpret_cast<const float2 *>(s_fl);
+            float2 c[S::P1];
+#pragma unroll
+            for (int i = 0; i < S::P1; ++i) {
+                const float ci = A.ref.dhat_s[j][aj][i];
+                c[i] = make_float2(ci, ci);
+            }
+#pragma unroll
+            for (int p = 0; p < NPR; ++p) {
+                const float2 *fl = fl2 + (j * NPR + p) * STR + b0;
+                float2 acc = make_float2(R[2 * p], 2 * p + 1 < S::NF ? R[2 * p + 1] : 0.0f);
+#pragma unroll
+                for (int i = 0; i < S::P1; ++i) acc = __ffma2_rn(c[i], fl[i * st], acc);
+                R[2 * p] = acc.x;
+                if (2 * p + 1 < S::NF) R[2 * p + 1] = acc.y;
+            }
         }
     }
 }
@@ -1284,7 +1335,7 @@ __global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
 constexpr int MODE_RHS = 0;
 constexpr int MODE_STAGE = 1;
 
-// Shared memory of a stage tile: nodal fluxes s_fl [D][NF][EPB NP], node
+// Shared memory of a stage tile: nodal fluxes s_fl (fl_index), node
 // values for the traces s_tr [NTR][EPB NP], outward face fluxes s_fh
 // [EPB][2D][NFP][NFP1] (with diffusion NFP = 2 NF: the fluxes, then the
 // symmetry terms), per-element indices, with diffusion the element's vertex
@@ -1301,10 +1352,10 @@ __host__ __device__ constexpr bool tr_shares_fl() {
 // byte offset of s_fh (16-byte aligned for the asynchronous copy of the face fluxes)
 template <class S, typename Real, bool PF, bool DIFF>
 __host__ __device__ constexpr size_t stage_fh_offset() {
+    constexpr size_t FL = (size_t)S::D * fl_words<S, Real>();
     return ((sizeof(Real) * (tr_shares_fl<S, Real, PF, DIFF>()
-                                 ? ((size_t)S::D * S::NF > (size_t)S::NTR ? (size_t)S::D * S::NF
-                                                                          : (size_t)S::NTR)
-                                 : (size_t)S::D * S::NF + S::NTR) *
+                                 ? (FL > (size_t)S::NTR ? FL : (size_t)S::NTR)
+                                 : FL + S::NTR) *
              S::EPB * S::NP) + 15) / 16 * 16;
 }
 
@@ -1646,12 +1697,10 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     static_assert(!DIFF || PF, "artificial diffusion runs with the face pass");
     constexpr int STR = S::EPB * S::NP;
     constexpr bool SHARE = tr_shares_fl<S, Real, PF, DIFF>();
-    constexpr int FLTR = SHARE ? (S::D * S::NF > S::NTR ? S::D * S::NF : S::NTR) * STR
-                               : (S::D * S::NF + S::NTR) * STR;
     constexpr int NFP = DIFF ? 2 * S::NF : S::NF;             // per face: fluxes [, symmetry terms]
     constexpr int EB = S::NFACE * NFP * S::NFP1;              // face values of one element
-    Real *s_fl = reinterpret_cast<Real *>(smem_raw);          // [D][NF][STR]
-    Real *s_tr = SHARE ? s_fl : s_fl + S::D * S::NF * STR;    // [NTR][STR]
+    Real *s_fl = reinterpret_cast<Real *>(smem_raw);          // nodal fluxes (fl_index)
+    Real *s_tr = SHARE ? s_fl : s_fl + S::D * fl_words<S, Real>() * STR;   // [NTR][STR]
     Real *s_fh = reinterpret_cast<Real *>(smem_raw + stage_fh_offset<S, Real, PF, DIFF>());  // [EPB][EB]
     int *s_info = reinterpret_cast<int *>(s_fh + S::EPB * EB);                            // [EPB][16]
     Real *s_al = reinterpret_cast<Real *>(s_info + 16 * S::EPB);        // DIFF: [EPB][2][NCORNER]
@@ -1724,8 +1773,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         for (int j = 0; j < S::D; ++j) {
             Real F[S::NF];
             flux_dir<S, Real>(P, j, F);
-#pragma unroll
-            for (int f = 0; f < S::NF; ++f) s_fl[(j * S::NF + f) * STR + t] = F[f];
+            fl_store<S, Real, STR>(s_fl, j, t, F);
         }
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) R[f] = Real(0);
@@ -1774,7 +1822,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 #pragma unroll
                     for (int i = 0; i < S::P1; ++i) du = fma(ref.dmat[aj][i], v[i * st], du);
                     const Real al = (S::RAIN && f == 2) ? ar : au;
-                    s_fl[(j * S::NF + f) * STR + t] -= al * (sc * du);
+                    s_fl[fl_index<S, Real, STR>(j, f, t)] -= al * (sc * du);
                 }
             }
         }
@@ -1900,6 +1948,14 @@ template <class S, typename Real, int MODE, bool PF, bool DIFF>
 __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     stage_block<S, Real, MODE, PF, DIFF>(A, A.ref, blockIdx.x, smem_raw);
+}
+
+// The float32 face-pass tile of 256 threads with its register budget sized
+// for five CTAs per SM (48 registers), as many as its shared memory holds
+template <class S, int MODE>
+__global__ void __launch_bounds__(S::NT, 5) k_stage_f32pf(KArgs<float> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_block<S, float, MODE, true, false>(A, A.ref, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

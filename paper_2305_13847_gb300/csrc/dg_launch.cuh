@@ -63,18 +63,28 @@ struct Impl {
         return diff ? launch_prepare<true>(A, st) : launch_prepare<false>(A, st);
     }
 
+    // the stage kernel of one schedule: float32 face-pass tiles of 256
+    // threads take the variant with the five-CTA register budget
+    template <int MODE, bool PF, bool DIFF>
+    static constexpr auto stage_kernel() {
+        if constexpr (std::is_same<Real, float>::value && PF && !DIFF && S::NT == 256)
+            return &k_stage_f32pf<S, MODE>;
+        else
+            return &k_stage<S, Real, MODE, PF, DIFF>;
+    }
+
     template <int MODE, bool PF, bool DIFF>
     static cudaError_t launch_stage(const KArgs<Real> &A, cudaStream_t st) {
         constexpr size_t smem = DIFF ? stage_smem_diff : (PF ? stage_smem_pf : stage_smem);
+        const auto kern = stage_kernel<MODE, PF, DIFF>();
         static bool attr = false;
         if (!attr) {
-            cudaError_t err = cudaFuncSetAttribute(k_stage<S, Real, MODE, PF, DIFF>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
+            cudaError_t err =
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (err != cudaSuccess) return err;
             attr = true;
         }
-        k_stage<S, Real, MODE, PF, DIFF><<<blocks(A), S::NT, smem, st>>>(A);
+        kern<<<blocks(A), S::NT, smem, st>>>(A);
         return cudaGetLastError();
     }
 
