@@ -369,8 +369,9 @@ __global__ void __launch_bounds__(ColShape<S>::NT, ColShape<S>::MINB) k_column(K
                 Real unew[S::NF];
 #pragma unroll
                 for (int f = 0; f < S::NF; ++f) {
-                    // one explicit fma: every stage kernel rounds the update alike
-                    Real v = fma(A.gdt, R[f], A.beta * u[f]);
+                    // one explicit fma: every stage kernel rounds the update alike;
+                    // beta u is u itself when beta = 1 (three stages in four)
+                    Real v = fma(A.gdt, R[f], is_one(A.beta) ? u[f] : A.beta * u[f]);
                     if (nonzero(A.alpha)) v = fma(A.alpha, A.Un[f * nodes + gi], v);
                     unew[f] = v;
                 }

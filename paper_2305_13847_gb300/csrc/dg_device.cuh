@@ -1914,8 +1914,9 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             Real un[S::NF];
 #pragma unroll
             for (int f = 0; f < S::NF; ++f) {
-                // one explicit fma: every stage kernel rounds the update alike
-                Real v = fma(A.gdt, R[f], A.beta * u[f]);
+                // one explicit fma: every stage kernel rounds the update alike;
+                // beta u is u itself when beta = 1 (three stages in four)
+                Real v = fma(A.gdt, R[f], is_one(A.beta) ? u[f] : A.beta * u[f]);
                 if (nonzero(A.alpha)) v = fma(A.alpha, A.Un[f * nodes + gi], v);
                 un[f] = v;
             }

@@ -168,6 +168,12 @@ __device__ __forceinline__ bool nonzero(double x) {
 }
 __device__ __forceinline__ bool nonzero(float x) { return x != 0.0f; }
 
+// x == 1 exactly, on the bit pattern
+__device__ __forceinline__ bool is_one(double x) {
+    return __double_as_longlong(x) == 0x3ff0000000000000LL;
+}
+__device__ __forceinline__ bool is_one(float x) { return x == 1.0f; }
+
 // the larger of two non-negative values (wave speeds): on the bit pattern
 __device__ __forceinline__ double max_nonneg(double a, double b) {
     return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
