@@ -175,8 +175,18 @@ int dg_set_base_state(dg_ctx *ctx, const double *node_tab, const double *face_ta
 int dg_init_bubble(dg_ctx *ctx, const dg_bubble *spec, const double *noise, int where);
 
 /* Copy a state (ABI layout, the context's storage type) into / out of the
- * context.  where = DG_HOST or DG_DEVICE.  dg_set_state makes the derived
- * fields stale; dg_get_state with DG_HOST synchronises. */
+ * context.  where = DG_HOST or DG_DEVICE.  dg_set_state from DG_HOST with
+ * the base state already set uploads in 8 chunks of whole element tiles on
+ * a second stream of the context and splits each chunk (Eq. (2.8), the
+ * derived fields and face traces the next step starts from) while the next
+ * one uploads; otherwise it copies on the context's stream and the next
+ * dg_step splits the state first.  Either way the results of later calls
+ * are the same.  Both are asynchronous except dg_get_state with DG_HOST,
+ * which synchronises; the host buffer of a DG_HOST upload must stay
+ * unchanged until the stream has passed the call (pinned memory for an
+ * asynchronous copy).  The split's Newton and non-physical counters
+ * accumulate into dg_check_status as in dg_step.  Errors: DG_EINVAL,
+ * DG_ESTATE (get before any set), DG_ECUDA. */
 int dg_set_state(dg_ctx *ctx, const void *U, int where);
 int dg_get_state(dg_ctx *ctx, void *U, int where);
 

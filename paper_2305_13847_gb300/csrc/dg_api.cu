@@ -225,18 +225,69 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     return A;
 }
 
+// split and traces of state U into trace buffer tb; ntiles > 0: only the
+// element tiles [tile0, tile0 + ntiles)
 template <typename Real>
-int do_prepare(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, const void *U, int tb) {
+int do_prepare(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, const void *U, int tb,
+               int tile0, int ntiles) {
     KArgs<Real> A = base_args<Real>(c, ref);
     A.Uin = (const Real *)U;
     A.trace_out = (Real *)c->trace[tb];
     A.dtrace_out = (Real *)c->dtrace[tb];
+    A.tile0 = tile0;
+    A.ntiles = ntiles;
     return cuda_status(L->prepare(A, c->diff, c->stream));
 }
 
-int prepare(dg_ctx *c, const void *U, int tb) {
-    return c->fp32 ? do_prepare<float>(c, c->L32, c->ref32, U, tb)
-                   : do_prepare<double>(c, c->L64, c->ref64, U, tb);
+int prepare(dg_ctx *c, const void *U, int tb, int tile0 = 0, int ntiles = 0) {
+    return c->fp32 ? do_prepare<float>(c, c->L32, c->ref32, U, tb, tile0, ntiles)
+                   : do_prepare<double>(c, c->L64, c->ref64, U, tb, tile0, ntiles);
+}
+
+// Upload of a host state in kUpChunks chunks of whole element tiles: the
+// copies of chunk i (one per field) run on up_stream while the stream
+// splits chunk i - 1 (k_prepare over its tiles), so the split of an
+// uploaded state hides behind the copy.  Leaves the split and the traces
+// of the new state in trace buffer 0, as dg_step's own prepare would.
+constexpr int kUpChunks = 8;
+
+int upload_and_prepare(dg_ctx *c, const void *host) {
+    if (!c->up_stream) {
+        if (cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return DG_ECUDA;
+        for (cudaEvent_t &e : c->up_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DG_ECUDA;
+    }
+    // nothing on the stream may still read U[0] when the copies overwrite it
+    if (cudaEventRecord(c->up_ev[kUpChunks], c->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->up_stream, c->up_ev[kUpChunks], 0) != cudaSuccess)
+        return DG_ECUDA;
+    const long long tiles = (c->ne + c->epb - 1) / c->epb;
+    const size_t fstride = (size_t)c->nodes * c->rsz;   // bytes of one field
+    const size_t ebytes = (size_t)c->np * c->rsz;       // bytes of one element in a field
+    for (int k = 0; k < kUpChunks; ++k) {
+        const long long t0 = tiles * k / kUpChunks, t1 = tiles * (k + 1) / kUpChunks;
+        const long long e0 = std::min(c->ne, t0 * c->epb), e1 = std::min(c->ne, t1 * c->epb);
+        if (e1 > e0) {
+            for (int f = 0; f < c->nf; ++f) {
+                const size_t off = (size_t)f * fstride + (size_t)e0 * ebytes;
+                if (cudaMemcpyAsync((char *)c->U[0] + off, (const char *)host + off,
+                                    (size_t)(e1 - e0) * ebytes, cudaMemcpyHostToDevice,
+                                    c->up_stream) != cudaSuccess)
+                    return DG_ECUDA;
+            }
+        }
+        if (cudaEventRecord(c->up_ev[k], c->up_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(c->stream, c->up_ev[k], 0) != cudaSuccess)
+            return DG_ECUDA;
+        if (t1 > t0) {
+            const int st = prepare(c, c->U[0], 0, (int)t0, (int)(t1 - t0));
+            if (st != DG_OK) return st;
+        }
+    }
+    c->parity = 0;
+    c->derived_valid = true;
+    return DG_OK;
 }
 
 // last: the stage that ends a time step (the sponge layer acts there);
@@ -645,6 +696,12 @@ void dg_free(dg_ctx *c) {
     {
         DeviceGuard dg(c->device);
         cudaStreamSynchronize(c->stream);
+        if (c->up_stream) {
+            cudaStreamSynchronize(c->up_stream);
+            cudaStreamDestroy(c->up_stream);
+            for (cudaEvent_t e : c->up_ev)
+                if (e) cudaEventDestroy(e);
+        }
         if (c->fp32) {
             release(c);
         } else {
@@ -753,14 +810,24 @@ int dg_init_bubble(dg_ctx *c, const dg_bubble *b, const double *noise, int where
 int dg_set_state(dg_ctx *c, const void *U, int where) {
     if (!c || !U || (where != DG_HOST && where != DG_DEVICE)) return DG_EINVAL;
     DeviceGuard dg(c->device);
+    c->derived_valid = false;
+    if (reset_fallout(c) != DG_OK) return DG_ECUDA;
+    if (where == DG_HOST && c->base_set) {
+        // the split of the new state overlaps its upload
+        const int st = upload_and_prepare(c, U);
+        if (st != DG_OK) {
+            c->derived_valid = false;
+            return st;
+        }
+        c->state_set = true;
+        return DG_OK;
+    }
     const size_t bytes = (size_t)c->nodes * c->nf * c->rsz;
     cudaError_t e = cudaMemcpyAsync(c->U[0], U, bytes,
                                     where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                                     c->stream);
     if (e != cudaSuccess) return DG_ECUDA;
-    if (reset_fallout(c) != DG_OK) return DG_ECUDA;
     c->state_set = true;
-    c->derived_valid = false;
     return DG_OK;
 }
 

@@ -53,6 +53,10 @@ struct dg_ctx {
     double *ubar_part = nullptr, *tadj = nullptr;
     int nred = 0;
     std::vector<double> z_node, z_face;
+    // host uploads (dg_set_state): the copies of one chunk go to up_stream
+    // while the stream splits the chunk before (created on first use)
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_ev[9] = {};
     bool base_set = false, state_set = false, derived_valid = false;
     int parity = 0;  // trace buffer holding the traces of U^n
     size_t device_bytes = 0;

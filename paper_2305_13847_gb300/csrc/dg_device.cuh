@@ -162,6 +162,9 @@ struct KArgs {
     // weight in the step (dt/6, dt/6, dt/6, dt/2); null when not accumulating
     double *fallout;
     double fall_w;
+    // k_prepare over element tiles [tile0, tile0 + ntiles) (ntiles 0: all),
+    // so that an upload can be split while its chunks arrive
+    int tile0, ntiles;
 };
 
 // float64 value of a storage-type value (widen: integer pipe)
@@ -1310,7 +1313,8 @@ __global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
     Real *s_red = s_tr + S::NTR * S::EPB * S::NP;    // [EPB][2]
     const int t = threadIdx.x;
     const int el = t / S::NP, a = t - el * S::NP;
-    const int e = blockIdx.x * S::EPB + el;
+    const int bidx = blockIdx.x + A.tile0;
+    const int e = bidx * S::EPB + el;
     const bool valid = (t < S::EPB * S::NP) && (e < A.M.ne);
     if (DIFF) {
         if (t < 2 * S::EPB) s_red[t] = Real(0);
@@ -1325,8 +1329,8 @@ __global__ void __launch_bounds__(S::NT) k_prepare(KArgs<Real> A) {
         split_and_store<S, Real, DIFF>(A, u, e, a, vert_index<S::D>(A.M, e), s_tr, t, s_red);
     }
     __syncthreads();
-    if (DIFF) alpha_store<S, Real>(A, s_red, blockIdx.x);
-    write_traces<S, Real, DIFF>(A, A.ref, s_tr, A.trace_out, blockIdx.x);
+    if (DIFF) alpha_store<S, Real>(A, s_red, bidx);
+    write_traces<S, Real, DIFF>(A, A.ref, s_tr, A.trace_out, bidx);
 }
 
 // ---------------------------------------------------------------------------

@@ -55,7 +55,7 @@ struct Impl {
             if (err != cudaSuccess) return err;
             attr = true;
         }
-        k_prepare<S, Real, DIFF><<<blocks(A), S::NT, prep_smem, st>>>(A);
+        k_prepare<S, Real, DIFF><<<A.ntiles > 0 ? A.ntiles : blocks(A), S::NT, prep_smem, st>>>(A);
         return cudaGetLastError();
     }
 

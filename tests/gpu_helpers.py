@@ -19,16 +19,23 @@ def oracle_problem(dim, n, L, order, periodic, rain, qt0=0.015, g=9.81):
     return dg.Problem(mesh, node, face, rain=rain, g=g), extra
 
 
-def library_context(prob, precision=dm.DG_FP64, stream=None, faces=dm.DG_FACES_AUTO):
+def library_context(prob, precision=dm.DG_FP64, stream=None, faces=dm.DG_FACES_AUTO, base=True):
+    """A library context of the oracle problem's mesh; with base, its base state set."""
     mesh = prob.mesh
     mask = sum(1 << j for j, p in enumerate(mesh.periodic[:-1]) if p)
     cfg = dm.make_config(mesh.dim, mesh.n, mesh.L, mesh.k, mask, prob.rain, precision, prob.g,
                          prob.rho_w or 0.0, faces)
     ctx = dm.dg_init_mesh(cfg, stream)
+    if base:
+        library_base(ctx, prob)
+    return ctx
+
+
+def library_base(ctx, prob):
+    """Set the oracle problem's base state (node and face levels) on a context."""
     node = np.stack([prob.base_node[k] for k in BASE_KEYS])
     face = np.stack([prob.base_face[k] for k in BASE_KEYS])
     dm.dg_set_base_state(ctx, node, face)
-    return ctx
 
 
 def perturbed_state(prob, seed, amplitude=2.0, rain_amp=1e-4):

@@ -15,8 +15,8 @@ from oracle import dg, initial
 from paper_2305_13847_gb300 import dgmoist as dm
 from paper_2305_13847_gb300 import inputs
 from paper_2305_13847_gb300 import workloads
-from tests.gpu_helpers import (flux_scale, library_context, oracle_problem, perturbed_state,
-                               to_device)
+from tests.gpu_helpers import (flux_scale, library_base, library_context, oracle_problem,
+                               perturbed_state, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -429,3 +429,39 @@ def test_fallout_matches_oracle_and_closes_the_water_budget(case, precision, fac
         assert dm.dg_reduce(ctx)[8] == 0.0
     finally:
         dm.dg_free(ctx)
+
+
+@pytest.mark.parametrize("precision", [dm.DG_FP64, dm.DG_FP32_BULK, dm.DG_FP32_PERT])
+@pytest.mark.parametrize("name", ["rain3d_q4_ragged", "rain2d_q1", "single_elem_3d_q3"])
+def test_host_upload_splits_in_chunks_like_dg_step(name, precision):
+    """dg_set_state from host memory splits the state chunk by chunk while it
+    uploads (whole element tiles per chunk, fewer tiles than chunks on the
+    small meshes).  The steps that follow, the fall-out and the Newton
+    counters equal those after a device-side set_state, whose split dg_step
+    takes itself; a host upload before the base state is set stays a plain
+    copy."""
+    prob, U = _setup(name)
+    dt = dg.cfl_dt(prob, U, 0.05)
+    fp64 = precision == dm.DG_FP64
+    host = np.ascontiguousarray(U if fp64 else U.astype(np.float32))
+    outs = []
+    for where in ("host", "device", "host_before_base"):
+        ctx = library_context(prob, precision=precision, base=(where != "host_before_base"))
+        try:
+            if where == "device":
+                dm.dg_set_state(ctx, to_device(host, torch.float64 if fp64 else torch.float32),
+                                dm.DG_DEVICE)
+            else:
+                dm.dg_set_state(ctx, host, dm.DG_HOST)
+            if where == "host_before_base":
+                library_base(ctx, prob)
+            dm.dg_step(ctx, dt, 2)
+            S = np.empty_like(host)
+            dm.dg_get_state(ctx, S, dm.DG_HOST)
+            st, counts = dm.dg_check_status(ctx)
+            outs.append((S, dm.dg_reduce(ctx)[8], st, counts.tolist()))
+        finally:
+            dm.dg_free(ctx)
+    for S, fall, st, counts in outs[1:]:
+        assert np.array_equal(outs[0][0], S)
+        assert (fall, st, counts) == outs[0][1:]
