@@ -211,6 +211,16 @@ int dg_rhs(dg_ctx *ctx, const void *U, void *dUdt);
  * failed during the call (the state is still advanced). */
 int dg_step(dg_ctx *ctx, double dt, int nsteps);
 
+/* dg_step followed by dg_get_state(ctx, U, DG_HOST), with the download
+ * overlapping the last stage: the stage kernel of the final stage runs in
+ * 8 chunks of whole element tiles, and each chunk's values are copied to
+ * U (host, ABI layout, the storage type; pinned memory for a copy that
+ * overlaps) on the context's second stream as soon as the chunk is done.
+ * The state and U equal those of dg_step + dg_get_state bitwise.
+ * nsteps >= 1.  Synchronises; returns dg_step's status.  Errors:
+ * DG_EINVAL, DG_ESTATE, DG_ECUDA, DG_ENOCONV, DG_ENONPHYS. */
+int dg_step_to_host(dg_ctx *ctx, double dt, int nsteps, void *U);
+
 /* Same as dg_step but enqueues only: no synchronisation and no status
  * check (read it later with dg_check_status). */
 int dg_step_async(dg_ctx *ctx, double dt, int nsteps);

@@ -225,6 +225,41 @@ KArgs<Real> base_args(const dg_ctx *c, const RefData<Real> &ref) {
     return A;
 }
 
+// Host transfers in kChunks chunks of whole element tiles (the stage and
+// prepare tiles), on the context's second stream up_stream
+constexpr int kChunks = 8;
+
+int ensure_up_stream(dg_ctx *c) {
+    if (c->up_stream) return DG_OK;
+    if (cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking) != cudaSuccess) return DG_ECUDA;
+    for (cudaEvent_t &e : c->up_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DG_ECUDA;
+    return DG_OK;
+}
+
+// element tiles [t0, t1) of chunk k
+void chunk_tiles(const dg_ctx *c, int k, long long &t0, long long &t1) {
+    const long long tiles = (c->ne + c->epb - 1) / c->epb;
+    t0 = tiles * k / kChunks;
+    t1 = tiles * (k + 1) / kChunks;
+}
+
+// the state values of chunk k's elements, one copy per field, on up_stream
+int copy_chunk(dg_ctx *c, int k, void *dst, const void *src, cudaMemcpyKind kind) {
+    long long t0, t1;
+    chunk_tiles(c, k, t0, t1);
+    const long long e0 = std::min(c->ne, t0 * c->epb), e1 = std::min(c->ne, t1 * c->epb);
+    const size_t fstride = (size_t)c->nodes * c->rsz;   // bytes of one field
+    const size_t ebytes = (size_t)c->np * c->rsz;       // bytes of one element in a field
+    for (int f = 0; f < c->nf && e1 > e0; ++f) {
+        const size_t off = (size_t)f * fstride + (size_t)e0 * ebytes;
+        if (cudaMemcpyAsync((char *)dst + off, (const char *)src + off, (size_t)(e1 - e0) * ebytes, kind,
+                            c->up_stream) != cudaSuccess)
+            return DG_ECUDA;
+    }
+    return DG_OK;
+}
+
 // split and traces of state U into trace buffer tb; ntiles > 0: only the
 // element tiles [tile0, tile0 + ntiles)
 template <typename Real>
@@ -244,39 +279,21 @@ int prepare(dg_ctx *c, const void *U, int tb, int tile0 = 0, int ntiles = 0) {
                    : do_prepare<double>(c, c->L64, c->ref64, U, tb, tile0, ntiles);
 }
 
-// Upload of a host state in kUpChunks chunks of whole element tiles: the
+// Upload of a host state in kChunks chunks of whole element tiles: the
 // copies of chunk i (one per field) run on up_stream while the stream
 // splits chunk i - 1 (k_prepare over its tiles), so the split of an
 // uploaded state hides behind the copy.  Leaves the split and the traces
 // of the new state in trace buffer 0, as dg_step's own prepare would.
-constexpr int kUpChunks = 8;
-
 int upload_and_prepare(dg_ctx *c, const void *host) {
-    if (!c->up_stream) {
-        if (cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking) != cudaSuccess)
-            return DG_ECUDA;
-        for (cudaEvent_t &e : c->up_ev)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return DG_ECUDA;
-    }
+    if (ensure_up_stream(c) != DG_OK) return DG_ECUDA;
     // nothing on the stream may still read U[0] when the copies overwrite it
-    if (cudaEventRecord(c->up_ev[kUpChunks], c->stream) != cudaSuccess ||
-        cudaStreamWaitEvent(c->up_stream, c->up_ev[kUpChunks], 0) != cudaSuccess)
+    if (cudaEventRecord(c->up_ev[kChunks], c->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c->up_stream, c->up_ev[kChunks], 0) != cudaSuccess)
         return DG_ECUDA;
-    const long long tiles = (c->ne + c->epb - 1) / c->epb;
-    const size_t fstride = (size_t)c->nodes * c->rsz;   // bytes of one field
-    const size_t ebytes = (size_t)c->np * c->rsz;       // bytes of one element in a field
-    for (int k = 0; k < kUpChunks; ++k) {
-        const long long t0 = tiles * k / kUpChunks, t1 = tiles * (k + 1) / kUpChunks;
-        const long long e0 = std::min(c->ne, t0 * c->epb), e1 = std::min(c->ne, t1 * c->epb);
-        if (e1 > e0) {
-            for (int f = 0; f < c->nf; ++f) {
-                const size_t off = (size_t)f * fstride + (size_t)e0 * ebytes;
-                if (cudaMemcpyAsync((char *)c->U[0] + off, (const char *)host + off,
-                                    (size_t)(e1 - e0) * ebytes, cudaMemcpyHostToDevice,
-                                    c->up_stream) != cudaSuccess)
-                    return DG_ECUDA;
-            }
-        }
+    for (int k = 0; k < kChunks; ++k) {
+        long long t0, t1;
+        chunk_tiles(c, k, t0, t1);
+        if (copy_chunk(c, k, c->U[0], host, cudaMemcpyHostToDevice) != DG_OK) return DG_ECUDA;
         if (cudaEventRecord(c->up_ev[k], c->up_stream) != cudaSuccess ||
             cudaStreamWaitEvent(c->stream, c->up_ev[k], 0) != cudaSuccess)
             return DG_ECUDA;
@@ -293,10 +310,13 @@ int upload_and_prepare(dg_ctx *c, const void *host) {
 // last: the stage that ends a time step (the sponge layer acts there);
 // fall_w: the stage's weight b_s dt in the step for the rain fall-out (0: the
 // stage adds nothing to it)
+// chunk_ev: launch the stage kernel in kChunks chunks of element tiles and
+// record chunk_ev[k] after chunk k (a download can follow chunk by chunk);
+// null: one launch
 template <typename Real>
 int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int mode, const void *Uin,
              const void *Un, void *Uout, int tin, double alpha, double beta, double gdt, bool last,
-             double fall_w) {
+             double fall_w, cudaEvent_t *chunk_ev) {
     KArgs<Real> A = base_args<Real>(c, ref);
     A.fall_w = fall_w;
     if (fall_w == 0.0 || mode != MODE_STAGE) A.fallout = nullptr;
@@ -320,15 +340,28 @@ int do_stage(dg_ctx *c, const Launchers<Real> *L, const RefData<Real> &ref, int 
         const int st = cuda_status(L->face(A, c->diff, c->stream));
         if (st != DG_OK) return st;
     }
-    return cuda_status(L->stage(A, mode, c->face_pass, c->diff, c->stream));
+    if (!chunk_ev) return cuda_status(L->stage(A, mode, c->face_pass, c->diff, c->stream));
+    for (int k = 0; k < kChunks; ++k) {
+        long long t0, t1;
+        chunk_tiles(c, k, t0, t1);
+        if (t1 > t0) {
+            A.tile0 = (int)t0;
+            A.ntiles = (int)(t1 - t0);
+            const int st = cuda_status(L->stage(A, mode, c->face_pass, c->diff, c->stream));
+            if (st != DG_OK) return st;
+        }
+        if (cudaEventRecord(chunk_ev[k], c->stream) != cudaSuccess) return DG_ECUDA;
+    }
+    return DG_OK;
 }
 
 int stage(dg_ctx *c, int mode, const void *Uin, const void *Un, void *Uout, int tin, double alpha,
-          double beta, double gdt, bool last = false, double fall_w = 0.0) {
+          double beta, double gdt, bool last = false, double fall_w = 0.0,
+          cudaEvent_t *chunk_ev = nullptr) {
     return c->fp32 ? do_stage<float>(c, c->L32, c->ref32, mode, Uin, Un, Uout, tin, alpha, beta, gdt,
-                                     last, fall_w)
+                                     last, fall_w, chunk_ev)
                    : do_stage<double>(c, c->L64, c->ref64, mode, Uin, Un, Uout, tin, alpha, beta, gdt,
-                                      last, fall_w);
+                                      last, fall_w, chunk_ev);
 }
 
 // the fall-out starts again from zero with every new state
@@ -909,10 +942,14 @@ int dg_rhs(dg_ctx *c, const void *U, void *dUdt) {
     return stage(c, MODE_RHS, U, U, dUdt, 0, 0.0, 1.0, 1.0);
 }
 
-int dg_step_async(dg_ctx *c, double dt, int nsteps) {
-    if (!c || nsteps < 0 || !std::isfinite(dt)) return DG_EINVAL;
-    if (!c->base_set || !c->state_set) return DG_ESTATE;
-    DeviceGuard dg(c->device);
+}  // extern "C"
+
+namespace {
+
+// nsteps SSPRK(4,3) steps on the context's stream; last_chunks: the final
+// stage of the final step runs in chunks and records these events (for a
+// download that follows it chunk by chunk)
+int step_impl(dg_ctx *c, double dt, int nsteps, cudaEvent_t *last_chunks) {
     int st = DG_OK;
     if (!c->derived_valid) {
         st = prepare(c, c->U[0], 0);
@@ -935,11 +972,50 @@ int dg_step_async(dg_ctx *c, double dt, int nsteps) {
         if (st == DG_OK)
             st = stage(c, MODE_STAGE, Uw, Un, Uw, p, 2.0 / 3.0, 1.0 / 3.0, dt / 6.0, false, dt / 6.0);
         p ^= 1;
-        if (st == DG_OK) st = stage(c, MODE_STAGE, Uw, Uw, Un, p, 0.0, 1.0, 0.5 * dt, true, 0.5 * dt);
+        if (st == DG_OK)
+            st = stage(c, MODE_STAGE, Uw, Uw, Un, p, 0.0, 1.0, 0.5 * dt, true, 0.5 * dt,
+                       n + 1 == nsteps ? last_chunks : nullptr);
         p ^= 1;
         c->parity = p;
     }
     return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_step_async(dg_ctx *c, double dt, int nsteps) {
+    if (!c || nsteps < 0 || !std::isfinite(dt)) return DG_EINVAL;
+    if (!c->base_set || !c->state_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    return step_impl(c, dt, nsteps, nullptr);
+}
+
+int dg_step_to_host(dg_ctx *c, double dt, int nsteps, void *U) {
+    if (!c || !U || nsteps < 1 || !std::isfinite(dt)) return DG_EINVAL;
+    if (!c->base_set || !c->state_set) return DG_ESTATE;
+    DeviceGuard dg(c->device);
+    if (ensure_up_stream(c) != DG_OK) return DG_ECUDA;
+    // the column march is one launch per stage: no chunks, the download follows
+    const bool chunked = !c->column;
+    int st = step_impl(c, dt, nsteps, chunked ? c->up_ev : nullptr);
+    if (st != DG_OK) return st;
+    if (chunked) {
+        for (int k = 0; k < kChunks; ++k) {
+            if (cudaStreamWaitEvent(c->up_stream, c->up_ev[k], 0) != cudaSuccess) return DG_ECUDA;
+            if (copy_chunk(c, k, U, c->U[0], cudaMemcpyDeviceToHost) != DG_OK) return DG_ECUDA;
+        }
+        // later work on the stream may overwrite U^n only after the download
+        if (cudaEventRecord(c->up_ev[kChunks], c->up_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(c->stream, c->up_ev[kChunks], 0) != cudaSuccess ||
+            cudaStreamSynchronize(c->up_stream) != cudaSuccess)
+            return DG_ECUDA;
+    } else if (cudaMemcpyAsync(U, c->U[0], (size_t)c->nodes * c->nf * c->rsz, cudaMemcpyDeviceToHost,
+                               c->stream) != cudaSuccess) {
+        return DG_ECUDA;
+    }
+    return dg_check_status(c, nullptr);
 }
 
 int dg_step(dg_ctx *c, double dt, int nsteps) {

@@ -162,8 +162,9 @@ struct KArgs {
     // weight in the step (dt/6, dt/6, dt/6, dt/2); null when not accumulating
     double *fallout;
     double fall_w;
-    // k_prepare over element tiles [tile0, tile0 + ntiles) (ntiles 0: all),
-    // so that an upload can be split while its chunks arrive
+    // k_prepare and k_stage over element tiles [tile0, tile0 + ntiles)
+    // (ntiles 0: all), so that an upload is split while its chunks arrive
+    // and a download starts while the last stage still runs
     int tile0, ntiles;
 };
 
@@ -1952,7 +1953,7 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
 template <class S, typename Real, int MODE, bool PF, bool DIFF>
 __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_block<S, Real, MODE, PF, DIFF>(A, A.ref, blockIdx.x, smem_raw);
+    stage_block<S, Real, MODE, PF, DIFF>(A, A.ref, blockIdx.x + A.tile0, smem_raw);
 }
 
 // The float32 face-pass tile of 256 threads with its register budget sized
@@ -1960,7 +1961,7 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
 template <class S, int MODE>
 __global__ void __launch_bounds__(S::NT, 5) k_stage_f32pf(KArgs<float> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_block<S, float, MODE, true, false>(A, A.ref, blockIdx.x, smem_raw);
+    stage_block<S, float, MODE, true, false>(A, A.ref, blockIdx.x + A.tile0, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -84,7 +84,7 @@ struct Impl {
             if (err != cudaSuccess) return err;
             attr = true;
         }
-        kern<<<blocks(A), S::NT, smem, st>>>(A);
+        kern<<<A.ntiles > 0 ? A.ntiles : blocks(A), S::NT, smem, st>>>(A);
         return cudaGetLastError();
     }
 

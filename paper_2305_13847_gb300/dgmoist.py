@@ -88,6 +88,7 @@ SIGNATURES = [
     ("dg_saturation_split", _I, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_longlong)]),
     ("dg_rhs", _I, [_VP, _VP, _VP]),
     ("dg_step", _I, [_VP, ctypes.c_double, _I]),
+    ("dg_step_to_host", _I, [_VP, ctypes.c_double, _I, _VP]),
     ("dg_step_async", _I, [_VP, ctypes.c_double, _I]),
     ("dg_check_status", _I, [_VP, _VP]),
     ("dg_set_newton_limit", _I, [_VP, _I]),
@@ -251,6 +252,10 @@ def dg_rhs(ctx, U, dUdt):
 
 def dg_step(ctx, dt, nsteps):
     _check(lib().dg_step(ctx, float(dt), int(nsteps)), "dg_step")
+
+
+def dg_step_to_host(ctx, dt, nsteps, U):
+    _check(lib().dg_step_to_host(ctx, float(dt), int(nsteps), _addr(U)), "dg_step_to_host")
 
 
 def dg_step_async(ctx, dt, nsteps):

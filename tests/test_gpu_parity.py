@@ -465,3 +465,40 @@ def test_host_upload_splits_in_chunks_like_dg_step(name, precision):
     for S, fall, st, counts in outs[1:]:
         assert np.array_equal(outs[0][0], S)
         assert (fall, st, counts) == outs[0][1:]
+
+
+@pytest.mark.parametrize("precision,faces", [(dm.DG_FP64, dm.DG_FACES_PASS),
+                                             (dm.DG_FP64, dm.DG_FACES_INLINE),
+                                             (dm.DG_FP32_BULK, dm.DG_FACES_PASS),
+                                             (dm.DG_FP32_PERT, dm.DG_FACES_COLUMN)])
+@pytest.mark.parametrize("name", ["rain3d_q4_ragged", "single_elem_3d_q3"])
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_step_to_host_equals_step_then_get_state(name, precision, faces, nsteps):
+    """dg_step_to_host runs the final stage in chunks of element tiles and
+    downloads each chunk as it completes; the host copy and the context's
+    state equal dg_step + dg_get_state bitwise, and the next step continues
+    from the same state."""
+    prob, U = _setup(name)
+    dt = dg.cfl_dt(prob, U, 0.05)
+    fp64 = precision == dm.DG_FP64
+    host = np.ascontiguousarray(U if fp64 else U.astype(np.float32))
+    outs = []
+    for fused in (True, False):
+        ctx = library_context(prob, precision=precision, faces=faces)
+        try:
+            dm.dg_set_state(ctx, host, dm.DG_HOST)
+            got = np.full_like(host, np.nan)
+            if fused:
+                dm.dg_step_to_host(ctx, dt, nsteps, got)
+            else:
+                dm.dg_step(ctx, dt, nsteps)
+                dm.dg_get_state(ctx, got, dm.DG_HOST)
+            dm.dg_step(ctx, dt, 1)
+            nxt = np.empty_like(host)
+            dm.dg_get_state(ctx, nxt, dm.DG_HOST)
+            outs.append((got, nxt, dm.dg_reduce(ctx)[8]))
+        finally:
+            dm.dg_free(ctx)
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
