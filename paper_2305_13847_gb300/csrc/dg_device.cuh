@@ -187,7 +187,10 @@ __device__ __forceinline__ void add_fallout(const KArgs<Real> &A, bool top, int 
 // ---------------------------------------------------------------------------
 // Compile-time layout of one (D, K, RAIN) configuration
 // ---------------------------------------------------------------------------
-template <int D_, int K_, bool RAIN_>
+// TT_: the threads a stage tile aims at, EPB = TT_ / NP elements (at least
+// one).  128 in 3-D: a warp that waits at a tile barrier holds up three
+// others, not seven (measured: float32 steps -5 % against 256).
+template <int D_, int K_, bool RAIN_, int TT_ = (D_ == 3 ? 128 : 256)>
 struct Shape {
     static constexpr int D = D_;
     static constexpr int K = K_;
@@ -201,7 +204,7 @@ struct Shape {
     static constexpr int IE = IM + D;             // energy field
     static constexpr int ND = RAIN ? 5 : 3;       // derived: T, rho_v, p' [, G_rm, v_r]
     static constexpr int NTR = NF + 3;            // traced: U, T, rho_v, p'
-    static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;   // elements per CTA
+    static constexpr int EPB = (TT_ / NP) > 0 ? (TT_ / NP) : 1;   // elements per CTA
     static constexpr int NT = ((EPB * NP + 31) / 32) * 32;          // threads per CTA
     static constexpr int VERT = D - 1;
     static constexpr int NCORNER = 1 << D;                          // element vertices
@@ -1956,10 +1959,10 @@ __global__ void __launch_bounds__(S::NT) k_stage(KArgs<Real> A) {
     stage_block<S, Real, MODE, PF, DIFF>(A, A.ref, blockIdx.x + A.tile0, smem_raw);
 }
 
-// The float32 face-pass tile of 256 threads with its register budget sized
-// for five CTAs per SM (48 registers), as many as its shared memory holds
+// The float32 face-pass tile (64, 128 or 256 threads) with its register
+// budget sized for 1280 threads per SM (48 registers)
 template <class S, int MODE>
-__global__ void __launch_bounds__(S::NT, 5) k_stage_f32pf(KArgs<float> A) {
+__global__ void __launch_bounds__(S::NT, 1280 / S::NT) k_stage_f32pf(KArgs<float> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     stage_block<S, float, MODE, true, false>(A, A.ref, blockIdx.x + A.tile0, smem_raw);
 }

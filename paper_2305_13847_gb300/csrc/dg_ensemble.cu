@@ -34,7 +34,7 @@ struct EnsMember {
 };
 
 template <int K, bool RAIN>
-struct EnsShape : Shape<2, K, RAIN> {};
+struct EnsShape : Shape<2, K, RAIN, 256> {};
 
 template <class S>
 constexpr size_t ens_smem() { return stage_smem_bytes<S, float>(); }

@@ -63,11 +63,12 @@ struct Impl {
         return diff ? launch_prepare<true>(A, st) : launch_prepare<false>(A, st);
     }
 
-    // the stage kernel of one schedule: float32 face-pass tiles of 256
-    // threads take the variant with the five-CTA register budget
+    // the stage kernel of one schedule: float32 face-pass tiles of 64, 128
+    // or 256 threads take the variant with the 48-register budget
     template <int MODE, bool PF, bool DIFF>
     static constexpr auto stage_kernel() {
-        if constexpr (std::is_same<Real, float>::value && PF && !DIFF && S::NT == 256)
+        if constexpr (std::is_same<Real, float>::value && PF && !DIFF &&
+                      (S::NT == 64 || S::NT == 128 || S::NT == 256))
             return &k_stage_f32pf<S, MODE>;
         else
             return &k_stage<S, Real, MODE, PF, DIFF>;
