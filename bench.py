@@ -453,10 +453,10 @@ def _open(dm, workloads, inputs, name, precision, stream, mesh=None, faces="auto
 # (-> traffic null) for any other configuration or schedule.  A capture
 # must be retaken whenever one of the two kernels changes.
 PROFILED_TRAFFIC = {
-    (3, 4, "fp64"): (410.8, "profiles/k_face_k_stage_rain3d_q4_fp64.md: 32x32x32 Q4, "
-                            "k_face 117.6 + k_stage 293.2 B/node"),
-    (3, 3, "fp32_bulk"): (237.6, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
-                                 "k_face 74.7 + k_stage 162.9 B/node"),
+    (3, 4, "fp64"): (410.7, "profiles/k_face_k_stage_rain3d_q4_fp64.md: 32x32x32 Q4, "
+                            "k_face 117.6 + k_stage 293.1 B/node"),
+    (3, 3, "fp32_bulk"): (237.5, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
+                                 "k_face 74.6 + k_stage 162.9 B/node"),
     (3, 3, "fp32_pert"): (237.5, "profiles/k_face_k_stage_rain3d_q3_fp32.md: 64x64x32 Q3, "
                                  "k_face 74.7 + k_stage 162.8 B/node"),
 }
