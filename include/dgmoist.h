@@ -452,12 +452,17 @@ void dg_ensemble_free(dg_ensemble *ens);
  *                  pow(x, -1/8) (INV_ROOT8), the closed form
  *                  e_s(T) / (R_v T) with exp and log (RHO_VS; RHO_VS_F32 takes
  *                  the float32-rounded temperature, the overload the float32
- *                  pre-solve uses), or for COMPARE the bits of the plain
+ *                  pre-solve uses; RHO_VS_BULK, at the float32-rounded
+ *                  temperature too, is the value-only evaluation of the
+ *                  FP32-bulk split, its curvature terms in float32), or for
+ *                  COMPARE the bits of the plain
  *                  float64 compares x > 0, x > 1.5, x < 1.5, |x| <= 1.5,
  *                  isfinite(x), max(|x|, 1.5) against those of the library's
  *                  bit-pattern compares;
- *   out[2n .. 4n)  for RHO_VS / RHO_VS_F32 the derivative d rho_vs / dT, the
- *                  library's and the closed form's; 0 otherwise.
+ *   out[2n .. 4n)  for RHO_VS / RHO_VS_F32 / RHO_VS_BULK the derivative
+ *                  d rho_vs / dT, the library's (RHO_VS_BULK: the float32
+ *                  derivative that split forms) and the closed form's; 0
+ *                  otherwise.
  * Uses ctx's rho_vs table and stream; synchronises.  Errors: DG_EINVAL
  * (bad fn or n, or a device other than ctx's current); DG_ECUDA. */
 #define DG_MATH_NARROW 0
@@ -470,6 +475,7 @@ void dg_ensemble_free(dg_ensemble *ens);
 #define DG_MATH_RHO_VS 7
 #define DG_MATH_RHO_VS_F32 8
 #define DG_MATH_COMPARE 9
+#define DG_MATH_RHO_VS_BULK 10
 int dg_selftest_math(dg_ctx *ctx, int fn, const double *x, double *out, long long n);
 
 /* Float64 FMA throughput probe (a measurement aid, not part of the method):

@@ -438,6 +438,33 @@ __device__ __forceinline__ double rho_vs_tab(float t, const double *__restrict__
     return fma(d, fma(d, fma(d, fma(d, fma(d, c45.y, c45.x), c23.y), c23.x), c01.y), c01.x);
 }
 
+// float64 rho_vs at a float32 temperature t, value only, for the FP32-bulk
+// split: c_0 + c_1 d in float64 and the curvature d^2 (c_2 + c_3 d + c_4 d^2)
+// in float32.  The curvature is at most 6.4e-7 of rho_vs (at 150 K; 3e-8 at
+// 280 K) and c_5 d^5 below 1e-17, so float32 arithmetic on coefficients
+// truncated to float32 leaves below 3e-13 relative (1e-14 above 250 K): two
+// float64 fmas instead of the five of the full series.  All of c_0 .. c_4 are
+// positive and within the float32 normal range over the table.
+__device__ __forceinline__ double rho_vs_bulk(float t, const double *__restrict__ tab) {
+    if (!(t >= (float)kTabT0 && t <= (float)(kTabT1 - 1.0))) {
+        double d1;
+        return rho_vs_tab(widen(t), tab, d1);
+    }
+    const int i = __float2int_rn((t - (float)kTabT0) * (float)kTabInvStep);
+    const float df = t - ((float)kTabT0 + (float)i * (float)(1.0 / kTabInvStep));   // exact
+    const double2 *e = reinterpret_cast<const double2 *>(tab + (size_t)kTabStride * i);
+    const double2 c01 = __ldg(e), c23 = __ldg(e + 1);
+    const float c4 = trunc_f32(__ldg(tab + (size_t)kTabStride * i + 4));
+    const float q = fmaf(df, fmaf(df, c4, trunc_f32(c23.y)), trunc_f32(c23.x)) * (df * df);
+    return fma(widen(df), c01.y, c01.x) + widen(q);
+}
+
+// d rho_vs / dT = rho_vs ((a-1)/T + b/T^2) in float32, from a float32 rho_vs
+// and 1/T (the FP32-bulk split's Newton derivative and Taylor step)
+__device__ __forceinline__ float drho_vs_f32(float rvs, float invT) {
+    return rvs * invT * ((float)(kEsA - 1.0) + (float)kEsB * invT);
+}
+
 struct SplitResult {
     double T, rv, deficit;  // deficit = rho_vs(T) - rho_v (0 at saturation)
     bool converged;
@@ -641,13 +668,23 @@ __device__ __forceinline__ NodeDerived node_derived(double rd, double rm, double
     return o;
 }
 
+// T_u = T_ref + X / C_u in float64 from its float32 estimate tuf and
+// rcu ~ 1/C_u: with t0 = tuf (exact), the residual X - C_u (t0 - T_ref) is
+// C_u times the estimate's error (~1e-5 K), and its float32 quotient
+// completes T_u to ~1e-11 K (C_u and three float64 operations instead of a
+// float64 reciprocal)
+__device__ __forceinline__ double t_unsaturated(double X, double cu, float tuf, float rcu) {
+    const double t0 = widen(tuf);
+    return t0 + widen(narrow(fma(-cu, t0 - kTref, X)) * rcu);
+}
+
 // Split of the FP32-bulk form: the state is float32; the temperature recovery
 // from the total energy (the cancellation-prone balance E - |m|^2/(2 rho) -
 // rho_m L') and the Newton solve for the saturated vapour density run in
 // float64.  Newton iterates in float32 from T_u to ~1e-7, then one float64
-// Newton correction with the float64 rho_vs (table) gives T to ~1e-13 and
-// rho_v = rho_vs(T) to the same order, so vapour is never supersaturated by
-// more than ~1e-12 relative.  Rain sources and v_r are bulk (float32)
+// Newton correction with the float64 rho_vs (table, rho_vs_bulk) gives T to
+// ~1e-13 and rho_v = rho_vs(T) to ~1e-12, so vapour is never supersaturated
+// by more than ~1e-12 relative.  Rain sources and v_r are bulk (float32)
 // arithmetic.
 template <bool RAIN>
 __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im, int ie, int d,
@@ -667,18 +704,20 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
     const double rm = brm + widen(u[1]);
     const double rr = RAIN ? widen(u[2]) : 0.0;
     const double re = (bE + widen(u[ie])) - widen(0.5f * msq * __frcp_rn(rhof));
-    // T_u = T_ref + X / C_u with X in float64; the float32 T_u decides
-    // saturation and starts the pre-solve, the float64 one is formed only
-    // where T = T_u (unsaturated) or the decision is close
-    const double X = fma(-rm, kLprime, re);
+    // T_u = T_ref + X / C_u, X = E_int - rho_m L'.  The float32 T_u (from the
+    // float32 X, within ~1e-5 K) decides saturation and starts the pre-solve;
+    // X and T_u in float64 are formed only where T = T_u (unsaturated) or the
+    // decision is close
+    const float ref = narrow(re);
     const float cuf = (float)kCvd * rdf + (float)kCvv * rmf + (float)kCl * rrf;
-    const float tuf = fmaf(narrow(X), __frcp_rn(cuf), (float)kTref);
+    const float rcu = __frcp_rn(cuf);
+    const float tuf = fmaf(fmaf(-rmf, (float)kLprime, ref), rcu, (float)kTref);
     const float rvs32 = rho_vs_f32(tuf);
     bool sat;
     double tu = 0.0;
     const bool close = fabsf(rmf - rvs32) <= 1e-5f * rmf || !(tuf > 0.0f);
     if (close) {
-        tu = fma(X, recip(fma(kCvd, rd, fma(kCvv, rm, kCl * rr))), kTref);
+        tu = t_unsaturated(fma(-rm, kLprime, re), fma(kCvd, rd, fma(kCvv, rm, kCl * rr)), tuf, rcu);
         double d1u;
         sat = rm > rho_vs_tab(tu, tab, d1u);      // close call: decide in float64
     } else {
@@ -687,7 +726,9 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
     float deficit = 0.0f, rvf, Tf;
     o.conv = true;
     if (!sat) {
-        if (!close) tu = fma(X, recip(fma(kCvd, rd, fma(kCvv, rm, kCl * rr))), kTref);
+        if (!close)
+            tu = t_unsaturated(fma(-rm, kLprime, re), fma(kCvd, rd, fma(kCvv, rm, kCl * rr)), tuf,
+                               rcu);
         o.T = tu;
         o.rv = rm;
         Tf = narrow(tu);
@@ -696,10 +737,9 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
     } else {
         // explicit fma: a contraction left to the compiler may differ between
         // the stage kernel and the ensemble's tile functions
-        const float cdf = fmaf((float)kCvd, rdf, (float)kCl * (rmf + rrf)), ref = narrow(re);
+        const float cdf = fmaf((float)kCvd, rdf, (float)kCl * (rmf + rrf));
         const float tref = (float)kTref;
         const float clv = (float)(kCvv - kCl), lp = (float)kLprime;
-        const float am1 = (float)(kEsA - 1.0), bb = (float)kEsB;
         // start at this node's temperature of the previous stage when there
         // is one (not below T_u, which lies below the saturated root)
         float t = Tprev > tuf ? Tprev : tuf;
@@ -707,8 +747,7 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
         const int n32 = M.newton_cap < 40 ? M.newton_cap : 40;
         for (int it = 0; it < n32; ++it) {
             const float rvs = rho_vs_f32(t);
-            const float it_ = __frcp_rn(t);
-            const float drvs = rvs * it_ * (am1 + bb * it_);
+            const float drvs = drho_vs_f32(rvs, __frcp_rn(t));
             const float heat = cdf + clv * rvs;
             const float h = heat * (t - tref) + rvs * lp - ref;
             const float dh = heat + (clv * (t - tref) + lp) * drvs;
@@ -721,19 +760,21 @@ __device__ __forceinline__ NodeDerived node_derived_bulk(const float *u, int im,
                 break;
             }
         }
-        // one float64 Newton correction of T with the float64 rho_vs
-        double drvs64;
+        // one float64 Newton correction of T: the residual H(t) in float64
+        // with the float64 rho_vs(t), the step H/H' in float32 (|dT| is below
+        // ~3e-5 K, so its float32 rounding moves T by < 1e-11 K), and
+        // rho_v = rho_vs(t) - rho_vs'(t) dT with the float32 derivative (the
+        // product is below 2e-6 of rho_vs, so < 1e-12 relative)
         const double T32 = widen(t);
-        const double rvs = rho_vs_tab(t, tab, drvs64);
+        const double rvs = rho_vs_bulk(t, tab);
         const double cdry = fma(kCvd, rd, kCl * (rm + rr));
         const double h = fma(fma(kCvv - kCl, rvs, cdry), T32 - kTref, fma(rvs, kLprime, -re));
-        const float rvsf = narrow(rvs), itf = __frcp_rn(t);
-        const float drvs = rvsf * itf * (am1 + bb * itf);
+        const float rvsf = narrow(rvs);
+        const float drvs = drho_vs_f32(rvsf, __frcp_rn(t));
         const float dh = cdf + clv * rvsf + (clv * (t - tref) + lp) * drvs;
         const float dT = narrow(h) / dh;
-        const double dT64 = widen(dT);
-        o.T = T32 - dT64;
-        o.rv = fma(-drvs64, dT64, rvs);
+        o.T = T32 - widen(dT);
+        o.rv = rvs - widen(drvs * dT);
         Tf = narrow(o.T);
         rvf = narrow(o.rv);
         o.conv = conv && fabsf(dT) <= 1e-4f * t;

@@ -55,6 +55,14 @@ __device__ __forceinline__ float narrow(double x) {
     return __uint_as_float((hi & 0x80000000u) | bits);
 }
 
+// float32 value of a positive float64 x in the float32 normal range, the
+// mantissa truncated (relative error below 2^-23): three integer operations,
+// for coefficients whose float32 rounding is not needed exactly
+__device__ __forceinline__ float trunc_f32(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    return __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
+}
+
 // float64 value of a float32 (exact), from the bit pattern; subnormals, NaN
 // and infinities go to the hardware conversion
 __device__ __forceinline__ double widen(float f) {

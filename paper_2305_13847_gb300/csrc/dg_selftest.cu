@@ -72,6 +72,18 @@ __global__ void k_selftest_math(int fn, const double *__restrict__ x, double *__
                 ref2 = ref * invT * ((kEsA - 1.0) + kEsB * invT);
                 break;
             }
+            case DG_MATH_RHO_VS_BULK: {
+                // the FP32-bulk split's value-only table evaluation and its
+                // float32 derivative, at the float32 temperature
+                const float tf = __double2float_rn(v);
+                const double T = (double)tf;
+                ours = rho_vs_bulk(tf, tab);
+                ours2 = (double)drho_vs_f32(__double2float_rn(ours), 1.0f / tf);
+                const double invT = 1.0 / T;
+                ref = rho_vs(T, invT);
+                ref2 = ref * invT * ((kEsA - 1.0) + kEsB * invT);
+                break;
+            }
             default: {
                 // DG_MATH_COMPARE: the bit-pattern compares against the
                 // constant 1.5 and zero; bit k of ours / ref is compare k
@@ -96,7 +108,7 @@ __global__ void k_selftest_math(int fn, const double *__restrict__ x, double *__
 }  // namespace
 
 extern "C" int dg_selftest_math(dg_ctx *c, int fn, const double *x, double *out, long long n) {
-    if (!c || !x || !out || n < 1 || fn < DG_MATH_NARROW || fn > DG_MATH_COMPARE) return DG_EINVAL;
+    if (!c || !x || !out || n < 1 || fn < DG_MATH_NARROW || fn > DG_MATH_RHO_VS_BULK) return DG_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return DG_EINVAL;
     const long long blocks = (n + 255) / 256;

@@ -227,3 +227,35 @@ def test_rho_vs_table_against_the_closed_form(ctx):
         T32 = Tt.astype(np.float32).astype(np.float64)
         out = (T32 < 150.0) | (T32 > 399.0)
         assert same_bits(ours[out], ref[out]).all()
+
+
+def test_rho_vs_bulk_evaluation_against_the_closed_form(ctx):
+    """The FP32-bulk split's value-only rho_vs (c_0 + c_1 d in float64, the
+    curvature d^2 (c_2 + c_3 d + c_4 d^2) in float32 on coefficients truncated
+    to float32) and its float32 derivative.  The curvature is at most 6.4e-7 of
+    rho_vs at 150 K, so the float32 part adds at most ~1e-13 relative there
+    (~7e-15 above 250 K) to the table's 64 ulp; the derivative carries a few
+    float32 roundings.  Outside the table: the closed form itself."""
+    T = np.concatenate([150.0 + 249.0 * inputs.uniform(131, np.arange(20000)),
+                        150.0 + np.arange(0, 249 * 128 + 1, 101) / 128.0,
+                        150.0 + (np.arange(0, 249 * 128, 83) + 0.5) / 128.0,
+                        [150.0, 399.0, 149.9, 120.0, 450.0]])
+    ours, ref, d_ours, d_ref = run(ctx, "rho_vs_bulk", T)
+    Tt = T.astype(np.float32).astype(np.float64)
+    cl, cpv, rv, lref, tref, eref = (Decimal("4218"), Decimal("1850"), Decimal("461.51"),
+                                     Decimal("2.835e6"), Decimal("273.15"), Decimal("610.7"))
+    a = (cpv - cl) / rv
+    b = (lref - (cpv - cl) * tref) / rv
+    ex = np.array([float(eref * (Decimal(float(t)) / tref) ** a *
+                         (b * (1 / tref - 1 / Decimal(float(t)))).exp() / (rv * Decimal(float(t))))
+                   for t in Tt])
+    rel = np.abs(ours - ex) / ex
+    warm = Tt >= 250.0
+    stats = ("worst %.2e at %r K" % (rel.max(), Tt[np.argmax(rel)]),
+             "above 250 K %.2e" % rel[warm].max())
+    assert rel.max() <= 2e-13, stats
+    assert rel[warm].max() <= 3e-14, stats
+    rel_d = np.abs(d_ours - d_ref) / np.abs(d_ref)
+    assert rel_d.max() <= 1e-6, rel_d.max()
+    out = (Tt < 150.0) | (Tt > 399.0)
+    assert same_bits(ours[out], ref[out]).all()
