@@ -236,6 +236,8 @@ def _host_cpu():
 # set-up (3-D warm rain, Q3, white noise) on a 16 x 16 x 8 mesh, 200 steps
 ERR_MESH = (16, 16, 8)
 ERR_STEPS = 200
+# steps of the DG_FP64_FFC leg's comparison with the float64 form
+FFC_ERR_STEPS = 20
 
 
 def cpu_leg_main(tmpdir):
@@ -842,6 +844,43 @@ def run_gb300(args):
                                       ("fp32_pert", "rain3d_q3_fp32", None, "fp32_pert")):
             guarded(key, lambda: measure_form(name, mesh, form))
 
+    # the float64 form with float-float contractions (DG_FP64_FFC) on the
+    # headline workload, and its difference from the float64 form after the
+    # same steps from the same initial state (whole mesh)
+    def measure_ffc():
+        w4, ctx4, info4, dt4 = _open(dm, workloads, inputs, WORKLOAD, "fp64_ffc", stream, args.mesh,
+                                     args.faces)
+        try:
+            t4, _ = _measure(torch, dm, ctx4, info4, dt4, args.steps, args.warmup, stream, barrier,
+                             dist)
+        finally:
+            dm.dg_free(ctx4)
+        states = []
+        for form in ("fp64", "fp64_ffc"):
+            w5, ctx5, info5, dt5 = _open(dm, workloads, inputs, WORKLOAD, form, stream, args.mesh,
+                                         args.faces)
+            try:
+                dm.dg_step(ctx5, dt5, FFC_ERR_STEPS)
+                U5 = torch.empty((info5.n_fields, info5.n_elem, info5.nodes_per_elem),
+                                 dtype=torch.float64, device="cuda")
+                dm.dg_get_state(ctx5, U5, dm.DG_DEVICE)
+                states.append(U5)
+            finally:
+                dm.dg_free(ctx5)
+        rel = [float(torch.linalg.vector_norm(states[1][f] - states[0][f]) /
+                     torch.linalg.vector_norm(states[0][f])) for f in range(info4.n_fields)]
+        return {
+            "workload": "%s: %s hex, Q%d, 7 fields, %d DOFs, float64 state and arithmetic, volume "
+                        "term and lift as compensated float32-pair sums"
+                        % (WORKLOAD, "x".join(map(str, w4["n"])), w4["order"], info4.n_dofs),
+            "value": whole_job_rate(world, info4.n_dofs * STAGES * args.steps, t4), "unit": UNIT,
+            "ms_per_step": 1000.0 * t4 / args.steps,
+            "vs_fp64": (1000.0 * t_max / args.steps) / (1000.0 * t4 / args.steps),
+            "diff_vs_fp64": {"steps": FFC_ERR_STEPS, "rel_l2_max": max(rel), "rel_l2": rel}}
+
+    if args.precision == "fp64" and args.workload == WORKLOAD and not args.no_ffc:
+        guarded("fp64_ffc", measure_ffc)
+
     # the float32 forms' error against float64: (i) on the 16 x 16 x 8 mesh
     # against the oracle (the comparison happens in the CPU leg), (ii) at full
     # size against the library's float64 form on sampled elements
@@ -963,9 +1002,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk", "fp32_pert"])
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "fp32_bulk", "fp32_pert", "fp64_ffc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32-bulk measurements")
+    ap.add_argument("--no-ffc", action="store_true",
+                    help="skip the float64 form with float-float contractions")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint measurement")

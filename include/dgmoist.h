@@ -27,8 +27,8 @@
  *     of the total energy (Section 2.3, Eq. (2.11)).
  *   - "ABI layout" of a state: U[f][e][a], f the field, e = i0 + n0 (i1 + n1 i2)
  *     the element, a = a0 + (k+1)(a1 + (k+1) a2) the node (first index
- *     fastest).  Element storage type: double for DG_FP64, float for
- *     DG_FP32_BULK.
+ *     fastest).  Element storage type: double for DG_FP64 and DG_FP64_FFC,
+ *     float for DG_FP32_BULK and DG_FP32_PERT.
  *   - Base (hydrostatic) state tables, Section 2.3: rho_d, rho_m, E, p at the
  *     node z-levels (index i_vert (k+1) + a_vert, n_vert (k+1) levels) and at
  *     the face z-levels (index i_vert, n_vert + 1 levels), as float64.
@@ -68,6 +68,7 @@ extern "C" {
 #define DG_FP64 0
 #define DG_FP32_BULK 1
 #define DG_FP32_PERT 2
+#define DG_FP64_FFC 3
 
 #define DG_HOST 0
 #define DG_DEVICE 1
@@ -89,7 +90,15 @@ typedef struct dg_config {
                            DG_FP32_PERT: float throughout, the split solved in
                            the perturbation variables T - T_bar, rho_v - rho_v_bar
                            against a float64 split of the base state (no
-                           cancellation, so float32 suffices there) */
+                           cancellation, so float32 suffices there);
+                           DG_FP64_FFC: float64 state and arithmetic as
+                           DG_FP64, except that the stage kernel's volume
+                           term and lift (the sum-factorised contractions of
+                           Eq. (3.2) and the facet term of Eq. (3.3)) are
+                           compensated float32-pair sums (error-free
+                           transformations, ~2^-48 relative to the sum of the
+                           terms' magnitudes) on the float32 pipe, which runs
+                           64x the float64 rate on GB300; not in the paper */
     double g;           /* gravity in m/s^2 (the paper does not print it; 9.81 usual) */
     double rho_w;       /* water density in the rain speed: <= 0 takes the paper's
                            rho_w = rho_v + rho_c + rho_r; > 0 a constant (kg/m^3) */
@@ -144,7 +153,7 @@ typedef struct dg_bubble {
  * device state (two copies), derived fields and face-trace buffers.
  * Errors: DG_EINVAL for out-of-range fields or a mesh whose
  * n_nodes * n_fields exceeds 2^31 - 1; DG_ENOTIMPL for DG_FACES_COLUMN with
- * DG_FP64; DG_ENOMEM; DG_ECUDA. */
+ * DG_FP64 or DG_FP64_FFC; DG_ENOMEM; DG_ECUDA. */
 int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream);
 
 /* Release everything owned by ctx (NULL is ignored). */

@@ -198,6 +198,25 @@ void column(const std::vector<double> &z, double theta, double p_s, double qt0, 
 
 }  // namespace
 
+namespace dgm {
+// The float64 reference tables of order k with the volume derivative and
+// lift coefficients scaled by 2/h_j of a mesh: the tables every float64 stage
+// kernel takes (dg_init_mesh, dg_rhs_noalloc).
+RefData<double> scaled_ref64(int order, const double two_over_h[3]) {
+    RefData<double> r = make_ref<double>(order);
+    for (int j = 0; j < 3; ++j)
+        for (int a = 0; a < 6; ++a) {
+            for (int i = 0; i < 6; ++i) r.dhat_s[j][a][i] = two_over_h[j] * r.dhat[a][i];
+            const double sc = two_over_h[j];
+            r.liftm_s[j][a] = sc * r.liftm[a];
+            r.liftp_s[j][a] = sc * r.liftp[a];
+            r.dliftm_s[j][a] = sc * sc * r.dliftm[a];
+            r.dliftp_s[j][a] = sc * sc * r.dliftp[a];
+        }
+    return r;
+}
+}  // namespace dgm
+
 #include "dg_ctx.h"
 
 namespace {
@@ -561,7 +580,8 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     const dg_config &g = *cfg;
     if (g.dim != 2 && g.dim != 3) return DG_EINVAL;
     if (g.order < 1 || g.order > 5) return DG_EINVAL;
-    if (g.precision != DG_FP64 && g.precision != DG_FP32_BULK && g.precision != DG_FP32_PERT)
+    if (g.precision != DG_FP64 && g.precision != DG_FP32_BULK && g.precision != DG_FP32_PERT &&
+        g.precision != DG_FP64_FFC)
         return DG_EINVAL;
     if (g.rain != 0 && g.rain != 1) return DG_EINVAL;
     if (g.faces != DG_FACES_AUTO && g.faces != DG_FACES_INLINE && g.faces != DG_FACES_PASS &&
@@ -577,7 +597,8 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     const int np = g.dim == 2 ? p1 * p1 : p1 * p1 * p1;
     const int nf = (g.rain ? 4 : 3) + g.dim;
     if (ne * np * (long long)(nf + 3) * 2 > 2147483647LL) return DG_EINVAL;
-    if (g.faces == DG_FACES_COLUMN && g.precision == DG_FP64) return DG_ENOTIMPL;
+    if (g.faces == DG_FACES_COLUMN && (g.precision == DG_FP64 || g.precision == DG_FP64_FFC))
+        return DG_ENOTIMPL;
 
     dg_ctx *c = new (std::nothrow) dg_ctx();
     if (!c) return DG_ENOMEM;
@@ -594,7 +615,10 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
         c->nf = c->L32->nf; c->np = c->L32->np; c->nfp1 = c->L32->nfp1;
         c->nd = c->L32->nd; c->ntr = c->L32->ntr; c->epb = c->L32->epb;
     } else {
-        c->L64 = g.dim == 2 ? launchers_d2_f64(g.order, g.rain) : launchers_d3_f64(g.order, g.rain);
+        if (g.precision == DG_FP64_FFC)
+            c->L64 = g.dim == 2 ? launchers_d2_f64ff(g.order, g.rain) : launchers_d3_f64ff(g.order, g.rain);
+        else
+            c->L64 = g.dim == 2 ? launchers_d2_f64(g.order, g.rain) : launchers_d3_f64(g.order, g.rain);
         c->LA = g.dim == 2 ? adj_launchers_d2(g.order, g.rain) : adj_launchers_d3(g.order, g.rain);
         c->nf = c->L64->nf; c->np = c->L64->np; c->nfp1 = c->L64->nfp1;
         c->nd = c->L64->nd; c->ntr = c->L64->ntr; c->epb = c->L64->epb;
@@ -632,29 +656,17 @@ int dg_init_mesh(dg_ctx **out, const dg_config *cfg, void *cuda_stream) {
     c->column = g.faces == DG_FACES_COLUMN;
     const long long fbuf_len = set_face_layout(c, nf);
     mesh_float_copies(M);
-    c->ref64 = make_ref<double>(g.order);
+    // the volume derivative and lift tables pre-scaled by 2/h_j of this
+    // mesh, float64 and their float32 roundings
+    c->ref64 = scaled_ref64(g.order, M.two_over_h);
     c->ref32 = make_ref<float>(g.order);
-    // the volume derivative tables pre-scaled by 2/h_j of this mesh
-    for (int j = 0; j < 3; ++j)
-        for (int a = 0; a < 6; ++a)
-            for (int i = 0; i < 6; ++i) {
-                const double v = M.two_over_h[j] * c->ref64.dhat[a][i];
-                c->ref64.dhat_s[j][a][i] = v;
-                c->ref32.dhat_s[j][a][i] = (float)v;
-            }
     for (int j = 0; j < 3; ++j)
         for (int a = 0; a < 6; ++a) {
-            const double sc = M.two_over_h[j];
-            const double v[4] = {sc * c->ref64.liftm[a], sc * c->ref64.liftp[a],
-                                 sc * sc * c->ref64.dliftm[a], sc * sc * c->ref64.dliftp[a]};
-            c->ref64.liftm_s[j][a] = v[0];
-            c->ref64.liftp_s[j][a] = v[1];
-            c->ref64.dliftm_s[j][a] = v[2];
-            c->ref64.dliftp_s[j][a] = v[3];
-            c->ref32.liftm_s[j][a] = (float)v[0];
-            c->ref32.liftp_s[j][a] = (float)v[1];
-            c->ref32.dliftm_s[j][a] = (float)v[2];
-            c->ref32.dliftp_s[j][a] = (float)v[3];
+            for (int i = 0; i < 6; ++i) c->ref32.dhat_s[j][a][i] = (float)c->ref64.dhat_s[j][a][i];
+            c->ref32.liftm_s[j][a] = (float)c->ref64.liftm_s[j][a];
+            c->ref32.liftp_s[j][a] = (float)c->ref64.liftp_s[j][a];
+            c->ref32.dliftm_s[j][a] = (float)c->ref64.dliftm_s[j][a];
+            c->ref32.dliftp_s[j][a] = (float)c->ref64.dliftp_s[j][a];
         }
 
     // z-levels

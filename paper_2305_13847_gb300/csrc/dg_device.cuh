@@ -190,11 +190,14 @@ __device__ __forceinline__ void add_fallout(const KArgs<Real> &A, bool top, int 
 // TT_: the threads a stage tile aims at, EPB = TT_ / NP elements (at least
 // one).  128 in 3-D: a warp that waits at a tile barrier holds up three
 // others, not seven (measured: float32 steps -5 % against 256).
-template <int D_, int K_, bool RAIN_, int TT_ = (D_ == 3 ? 128 : 256)>
+// FF_: float64 storage type with the stage kernel's volume and lift
+// contractions as compensated float32-pair sums (DG_FP64_FFC, dg_math.cuh)
+template <int D_, int K_, bool RAIN_, int TT_ = (D_ == 3 ? 128 : 256), bool FF_ = false>
 struct Shape {
     static constexpr int D = D_;
     static constexpr int K = K_;
     static constexpr bool RAIN = RAIN_;
+    static constexpr bool FF = FF_;
     static constexpr int P1 = K + 1;
     static constexpr int NP = ipow(P1, D);        // nodes per element
     static constexpr int NFP1 = ipow(P1, D - 1);  // points per face
@@ -354,6 +357,72 @@ __device__ __forceinline__ void volume_term(const KArgs<Real> &A, const Real *s_
                 R[2 * p] = acc.x;
                 if (2 * p + 1 < S::NF) R[2 * p + 1] = acc.y;
             }
+        }
+    }
+}
+
+// ---- float-float contractions of the float64 form (DG_FP64_FFC) ----------
+// The coefficient tables of Coef as float32 pairs (ff_split of the float64
+// entries), in the same slots.
+template <class S>
+__device__ __forceinline__ void coef_fill_ff(const RefData<double> &r, float2 *s_cf) {
+    using C = Coef<S>;
+    for (int i = threadIdx.x; i < C::N; i += blockDim.x) {
+        const int j = i / C::BLK, k = i - j * C::BLK;
+        double v = 0.0;
+        if (k < C::LM) v = r.dhat_s[j][k / S::P1][k % S::P1];
+        else if (k < C::LP) v = r.liftm_s[j][k - C::LM];
+        else if (k < C::DLM) v = r.liftp_s[j][k - C::LP];
+        else if (k < C::DLP) v = r.dliftm_s[j][k - C::DLM];
+        else if (k < C::DLP + S::P1) v = r.dliftp_s[j][k - C::DLP];
+        s_cf[i] = ff_split(v);
+    }
+}
+
+// Volume term of Eq. (3.2) as in volume_term, every product and sum as a
+// compensated float32-pair operation: (Rs, Re) += sum_i dhat_s[j][a_j][i]
+// F_j(line node i), the nodal fluxes fl2 [D][NF][STR] and coefficients as
+// pairs, in the same order of terms as the float64 form.
+template <class S, int STR>
+__device__ __forceinline__ void volume_term_ff(const float2 *fl2, const float2 *cf2, int el, int a,
+                                               float *Rs, float *Re) {
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) {
+        const int aj = digit<S::D, S::P1>(a, j);
+        const int st = stride_of<S::P1>(j);
+        const int b0 = el * S::NP + a - aj * st;
+        float2 c[S::P1];
+#pragma unroll
+        for (int i = 0; i < S::P1; ++i) c[i] = cf2[j * Coef<S>::BLK + aj * S::P1 + i];
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) {
+            const float2 *fl = fl2 + (j * S::NF + f) * STR + b0;
+#pragma unroll
+            for (int i = 0; i < S::P1; ++i) ff_madd(c[i], fl[i * st], Rs[f], Re[f]);
+        }
+    }
+}
+
+// Lift of the face fluxes (phase 3 of the stage tile) with float32 pairs:
+// (Rs, Re) -= (2/h_j) l_a(+1)/w_a Fhat(j, +) and += (2/h_j) l_a(-1)/w_a times
+// the low face's value (the outward flux inline, G along +e_j with the face
+// pass, hence the sign), the high face first as in the float64 form.
+template <class S, bool PF>
+__device__ __forceinline__ void lift_ff(const float2 *fh2, const float2 *cf2, int el, int a,
+                                        float *Rs, float *Re) {
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) {
+        const int aj = digit<S::D, S::P1>(a, j);
+        const int q = face_q<S::D, S::P1>(a, j);
+        const float2 *fm = fh2 + ((el * S::NFACE + 2 * j) * S::NF) * S::NFP1 + q;
+        const float2 *fp = fh2 + ((el * S::NFACE + 2 * j + 1) * S::NF) * S::NFP1 + q;
+        const float2 cm = cf2[j * Coef<S>::BLK + Coef<S>::LM + aj];
+        const float2 cp = ff_neg(cf2[j * Coef<S>::BLK + Coef<S>::LP + aj]);
+        const float2 cmo = PF ? cm : ff_neg(cm);
+#pragma unroll
+        for (int f = 0; f < S::NF; ++f) {
+            ff_madd(cp, fp[f * S::NFP1], Rs[f], Re[f]);
+            ff_madd(cmo, fm[f * S::NFP1], Rs[f], Re[f]);
         }
     }
 }
@@ -1748,6 +1817,11 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     constexpr bool SHARE = tr_shares_fl<S, Real, PF, DIFF>();
     constexpr int NFP = DIFF ? 2 * S::NF : S::NF;             // per face: fluxes [, symmetry terms]
     constexpr int EB = S::NFACE * NFP * S::NFP1;              // face values of one element
+    // float64 form with float-float contractions: nodal fluxes, coefficient
+    // tables and face fluxes held as float32 pairs in the float64 slots, the
+    // tendencies accumulated as pairs (Rs, Re) through the volume term and the
+    // lift, then formed in float64 for the stage update
+    constexpr bool FFC = S::FF && sizeof(Real) == sizeof(double) && !DIFF;
     Real *s_fl = reinterpret_cast<Real *>(smem_raw);          // nodal fluxes (fl_index)
     Real *s_tr = SHARE ? s_fl : s_fl + S::D * fl_words<S, Real>() * STR;   // [NTR][STR]
     Real *s_fh = reinterpret_cast<Real *>(smem_raw + stage_fh_offset<S, Real, PF, DIFF>());  // [EPB][EB]
@@ -1783,7 +1857,10 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     // nodal phases run (one contiguous block per face)
     if (PF) cp_async_faces<S, Real, NFP>(A.fbuf, A.ftab, s_fh, bidx, min(S::EPB, ne - bidx * S::EPB));
 
-    if (sizeof(Real) == sizeof(double)) coef_fill<S, Real>(A.ref, s_cf);
+    if constexpr (FFC)
+        coef_fill_ff<S>(A.ref, reinterpret_cast<float2 *>(s_cf));
+    else if (sizeof(Real) == sizeof(double))
+        coef_fill<S, Real>(A.ref, s_cf);
 
     // per element: neighbours across the 2D faces (inline faces) and the
     // vertical index
@@ -1822,7 +1899,13 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         for (int j = 0; j < S::D; ++j) {
             Real F[S::NF];
             flux_dir<S, Real>(P, j, F);
-            fl_store<S, Real, STR>(s_fl, j, t, F);
+            if constexpr (FFC) {
+                float2 *fl2 = reinterpret_cast<float2 *>(s_fl);
+#pragma unroll
+                for (int f = 0; f < S::NF; ++f) fl2[(j * S::NF + f) * STR + t] = ff_split(to_f64(F[f]));
+            } else {
+                fl_store<S, Real, STR>(s_fl, j, t, F);
+            }
         }
 #pragma unroll
         for (int f = 0; f < S::NF; ++f) R[f] = Real(0);
@@ -1879,7 +1962,21 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     }
 
     // ---- phase 2a: volume term, sum factorised: R_a += (2/h_j) sum_i dhat[a_j][i] F_j(i)
-    if (valid) volume_term<S, Real, STR>(A, s_fl, s_cf, el, a, R);
+    float Rs[S::NF], Re[S::NF];
+    if constexpr (FFC) {
+        if (valid) {
+#pragma unroll
+            for (int f = 0; f < S::NF; ++f) {
+                const float2 r2 = ff_split(to_f64(R[f]));
+                Rs[f] = r2.x;
+                Re[f] = r2.y;
+            }
+            volume_term_ff<S, STR>(reinterpret_cast<const float2 *>(s_fl),
+                                   reinterpret_cast<const float2 *>(s_cf), el, a, Rs, Re);
+        }
+    } else {
+        if (valid) volume_term<S, Real, STR>(A, s_fl, s_cf, el, a, R);
+    }
 
     // ---- phase 2b: Lax-Friedrichs flux at every face point of the CTA's elements
     if (PF) {
@@ -1911,11 +2008,25 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
         }
     }
     __syncthreads();
+    if constexpr (FFC) {
+        // the tile's face fluxes as float32 pairs, in place (each thread
+        // rewrites the slots it reads)
+        const int nv = min(S::EPB, ne - bidx * S::EPB) * EB;
+        float2 *fh2 = reinterpret_cast<float2 *>(s_fh);
+        for (int i = t; i < nv; i += S::NT) fh2[i] = ff_split(to_f64(s_fh[i]));
+        __syncthreads();
+    }
 
     // ---- phase 3: lift the face fluxes, R_a -= (2/h_j) l_a(s)/w_a Fhat(j, s)
     if (valid) {
+        if constexpr (FFC) {
+            lift_ff<S, PF>(reinterpret_cast<const float2 *>(s_fh), reinterpret_cast<const float2 *>(s_cf),
+                           el, a, Rs, Re);
 #pragma unroll
-        for (int j = 0; j < S::D; ++j) {
+            for (int f = 0; f < S::NF; ++f) R[f] = ff_value(Rs[f], Re[f]);
+        }
+#pragma unroll
+        for (int j = 0; j < (FFC ? 0 : S::D); ++j) {
             const int aj = digit<S::D, S::P1>(a, j);
             const int q = face_q<S::D, S::P1>(a, j);
             const Real *fm = s_fh + ((el * S::NFACE + 2 * j) * NFP) * S::NFP1 + q;

@@ -188,6 +188,11 @@ const Launchers<double> *launchers_d2_f64(int K, int rain);
 const Launchers<double> *launchers_d3_f64(int K, int rain);
 const Launchers<float> *launchers_d2_f32(int K, int rain);
 const Launchers<float> *launchers_d3_f32(int K, int rain);
+// float64 reference tables with the coefficients scaled by 2/h_j (dg_api.cu)
+RefData<double> scaled_ref64(int order, const double two_over_h[3]);
+// float64 with float-float contractions (DG_FP64_FFC)
+const Launchers<double> *launchers_d2_f64ff(int K, int rain);
+const Launchers<double> *launchers_d3_f64ff(int K, int rain);
 
 }  // namespace dgm
 
@@ -200,6 +205,27 @@ const Launchers<float> *launchers_d3_f32(int K, int rain);
             {Impl<Shape<DIM, 3, false>, REAL>::table(), Impl<Shape<DIM, 3, true>, REAL>::table()}, \
             {Impl<Shape<DIM, 4, false>, REAL>::table(), Impl<Shape<DIM, 4, true>, REAL>::table()}, \
             {Impl<Shape<DIM, 5, false>, REAL>::table(), Impl<Shape<DIM, 5, true>, REAL>::table()}, \
+        };                                                                             \
+        if (K < 1 || K > 5) return nullptr;                                            \
+        return &t[K - 1][rain ? 1 : 0];                                                \
+    }                                                                                  \
+    }
+
+#define DGM_FF_SHAPE(DIM, K, RAIN) Shape<DIM, K, RAIN, (DIM == 3 ? 128 : 256), true>
+#define DGM_DEFINE_LAUNCHERS_FF(NAME, DIM)                                             \
+    namespace dgm {                                                                    \
+    const Launchers<double> *NAME(int K, int rain) {                                   \
+        static const Launchers<double> t[5][2] = {                                     \
+            {Impl<DGM_FF_SHAPE(DIM, 1, false), double>::table(),                       \
+             Impl<DGM_FF_SHAPE(DIM, 1, true), double>::table()},                       \
+            {Impl<DGM_FF_SHAPE(DIM, 2, false), double>::table(),                       \
+             Impl<DGM_FF_SHAPE(DIM, 2, true), double>::table()},                       \
+            {Impl<DGM_FF_SHAPE(DIM, 3, false), double>::table(),                       \
+             Impl<DGM_FF_SHAPE(DIM, 3, true), double>::table()},                       \
+            {Impl<DGM_FF_SHAPE(DIM, 4, false), double>::table(),                       \
+             Impl<DGM_FF_SHAPE(DIM, 4, true), double>::table()},                       \
+            {Impl<DGM_FF_SHAPE(DIM, 5, false), double>::table(),                       \
+             Impl<DGM_FF_SHAPE(DIM, 5, true), double>::table()},                       \
         };                                                                             \
         if (K < 1 || K > 5) return nullptr;                                            \
         return &t[K - 1][rain ? 1 : 0];                                                \

@@ -170,6 +170,48 @@ __device__ __forceinline__ double inv_root8(double r) {
     return fma(y * c, e, y) * sc;
 }
 
+// ---------------------------------------------------------------------------
+// Compensated float32-pair ("double-float") sums for the float64 form with
+// float-float contractions (DG_FP64_FFC).  GB300 issues float64 at 1/64 of
+// the float32 rate, so a linear contraction sum_i c_i x_i of float64 values
+// costs less as error-free float32 transformations (Dekker's product by fma,
+// Knuth's TwoSum) than as float64 fmas.
+//
+// ff_split(x) = (hi, lo): hi = x rounded to float32, lo = (x - hi) rounded
+// (x - hi is exact in float64), so |x - hi - lo| <= 2^-48 |x| for x in the
+// float32 exponent range (lo loses bits below ~1e-38, where no value of the
+// method's tendencies matters against its field's scale).
+// ff_madd(c, x, s, e): s + e += c x for pairs c, x.  The product c.hi x.hi is
+// split exactly by one fma, the cross terms c.hi x.lo + c.lo x.hi are added
+// to that error, c.lo x.lo (< 2^-48 |c x|) is dropped, and s + p is a TwoSum
+// whose rounding error goes to e.  The sum of n terms is then within about
+// n 2^-48 of sum |c_i x_i| (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005), Dot2), against n 2^-53 in
+// float64.  The _rn intrinsics keep the compiler from fusing the
+// transformation's multiplies and adds into fmas, which would break it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 ff_split(double x) {
+    const float hi = narrow(x);
+    return make_float2(hi, narrow(x - widen(hi)));
+}
+
+__device__ __forceinline__ void ff_madd(float2 c, float2 x, float &s, float &e) {
+    const float p = __fmul_rn(c.x, x.x);
+    float q = __fmaf_rn(c.x, x.x, -p);          // c.hi x.hi - p, exact
+    q = __fmaf_rn(c.x, x.y, q);
+    q = __fmaf_rn(c.y, x.x, q);
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(err, q));
+}
+
+// the float64 value of s + e (both exact in float64; one rounding)
+__device__ __forceinline__ double ff_value(float s, float e) { return widen(s) + widen(e); }
+
+__device__ __forceinline__ float2 ff_neg(float2 c) { return make_float2(-c.x, -c.y); }
+
 // x != 0 (either sign of zero is zero), for kernel parameters
 __device__ __forceinline__ bool nonzero(double x) {
     return (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0;

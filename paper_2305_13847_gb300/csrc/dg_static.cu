@@ -74,48 +74,6 @@ int scratch_on_current_device(unsigned char **out) {
     return DG_OK;
 }
 
-// Reference-element tables of the Q^k nodal basis at the Gauss points, from
-// the library's own Gauss rule (dg_gauss_legendre).
-int reference_tables(int order, RefData<double> &r) {
-    const int n = order + 1;
-    double x[6], w[6];
-    if (dg_gauss_legendre(n, x, w) != DG_OK) return DG_EINVAL;
-    std::memset(&r, 0, sizeof(r));
-    double bw[6];
-    for (int a = 0; a < n; ++a) {
-        double prod = 1.0;
-        for (int m = 0; m < n; ++m)
-            if (m != a) prod *= x[a] - x[m];
-        bw[a] = 1.0 / prod;
-    }
-    for (int a = 0; a < n; ++a) {
-        double lm = 1.0, lp = 1.0;
-        for (int m = 0; m < n; ++m) {
-            if (m == a) continue;
-            lm *= (-1.0 - x[m]) / (x[a] - x[m]);
-            lp *= (1.0 - x[m]) / (x[a] - x[m]);
-        }
-        r.lm[a] = lm;
-        r.lp[a] = lp;
-        r.liftm[a] = lm / w[a];
-        r.liftp[a] = lp / w[a];
-        r.xi[a] = x[a];
-        r.w[a] = w[a];
-    }
-    // dhat[a][i] = (w_i / w_a) l_a'(x_i); l_a'(x_i) by the barycentric formula
-    for (int i = 0; i < n; ++i) {
-        double diag = 0.0;
-        for (int a = 0; a < n; ++a) {
-            if (a == i) continue;
-            const double d = (bw[a] / bw[i]) / (x[i] - x[a]);
-            r.dhat[a][i] = w[i] / w[a] * d;
-            diag -= d;
-        }
-        r.dhat[i][i] = diag;
-    }
-    return DG_OK;
-}
-
 }  // namespace
 
 extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, const double *base_face,
@@ -170,14 +128,8 @@ extern "C" int dg_rhs_noalloc(const dg_config *cfg, const double *base_node, con
     M.jac = 1.0;
     for (int j = 0; j < g.dim; ++j) M.jac *= M.h[j] / 2.0;
     M.newton_cap = kMaxNewton;
-    if (reference_tables(g.order, A.ref) != DG_OK) return DG_EINVAL;
-    // the volume and lift tables scaled by 2/h_j of this mesh
-    for (int j = 0; j < 3; ++j)
-        for (int a = 0; a < 6; ++a) {
-            for (int i = 0; i < 6; ++i) A.ref.dhat_s[j][a][i] = M.two_over_h[j] * A.ref.dhat[a][i];
-            A.ref.liftm_s[j][a] = M.two_over_h[j] * A.ref.liftm[a];
-            A.ref.liftp_s[j][a] = M.two_over_h[j] * A.ref.liftp[a];
-        }
+    // the reference tables of dg_init_mesh (scaled by 2/h_j of this mesh)
+    A.ref = scaled_ref64(g.order, M.two_over_h);
 
     A.rvs_tab = reinterpret_cast<const double *>(scratch);
     A.flags = reinterpret_cast<unsigned long long *>(scratch + kTableBytes);

@@ -25,6 +25,7 @@ DG_ENOTIMPL = -7
 DG_FP64 = 0
 DG_FP32_BULK = 1
 DG_FP32_PERT = 2
+DG_FP64_FFC = 3
 DG_FACES_AUTO = 0
 DG_FACES_INLINE = 1
 DG_FACES_PASS = 2

@@ -8,7 +8,8 @@ from . import inputs
 
 
 def precision_code(name):
-    return {"fp64": dm.DG_FP64, "fp32_bulk": dm.DG_FP32_BULK, "fp32_pert": dm.DG_FP32_PERT}[name]
+    return {"fp64": dm.DG_FP64, "fp32_bulk": dm.DG_FP32_BULK, "fp32_pert": dm.DG_FP32_PERT,
+            "fp64_ffc": dm.DG_FP64_FFC}[name]
 
 
 def config_for(w, precision=None, g=9.81, rho_w=0.0, faces=0):
