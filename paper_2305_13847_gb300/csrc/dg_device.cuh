@@ -286,7 +286,7 @@ __device__ __forceinline__ void coef_fill(const RefData<Real> &r, Real *s_cf) {
 // keeps [D][n_f][STR].
 template <class S, typename Real>
 __host__ __device__ constexpr int fl_words() {
-    return sizeof(Real) == sizeof(float) ? 2 * ((S::NF + 1) / 2) : S::NF;
+    return (sizeof(Real) == sizeof(float) || S::FF) ? 2 * ((S::NF + 1) / 2) : S::NF;
 }
 
 // index of field f of direction j at tile node t in the nodal fluxes
@@ -380,12 +380,15 @@ __device__ __forceinline__ void coef_fill_ff(const RefData<double> &r, float2 *s
 }
 
 // Volume term of Eq. (3.2) as in volume_term, every product and sum as a
-// compensated float32-pair operation: (Rs, Re) += sum_i dhat_s[j][a_j][i]
-// F_j(line node i), the nodal fluxes fl2 [D][NF][STR] and coefficients as
-// pairs, in the same order of terms as the float64 form.
+// compensated float32-pair operation, two fields at a time: (Rs, Re)[p] +=
+// sum_i dhat_s[j][a_j][i] F_j(line node i) for the fields 2p (lane x) and
+// 2p + 1 (lane y).  fl4 [D][(NF + 1) / 2][STR] holds (hi_2p, hi_2p+1, lo_2p,
+// lo_2p+1) per node, the coefficients are pairs (coef_fill_ff); the terms of
+// each field are taken in the float64 form's order.
 template <class S, int STR>
-__device__ __forceinline__ void volume_term_ff(const float2 *fl2, const float2 *cf2, int el, int a,
-                                               float *Rs, float *Re) {
+__device__ __forceinline__ void volume_term_ff(const float4 *fl4, const float2 *cf2, int el, int a,
+                                               float2 *Rs, float2 *Re) {
+    constexpr int NPR = (S::NF + 1) / 2;
 #pragma unroll
     for (int j = 0; j < S::D; ++j) {
         const int aj = digit<S::D, S::P1>(a, j);
@@ -395,21 +398,26 @@ __device__ __forceinline__ void volume_term_ff(const float2 *fl2, const float2 *
 #pragma unroll
         for (int i = 0; i < S::P1; ++i) c[i] = cf2[j * Coef<S>::BLK + aj * S::P1 + i];
 #pragma unroll
-        for (int f = 0; f < S::NF; ++f) {
-            const float2 *fl = fl2 + (j * S::NF + f) * STR + b0;
+        for (int p = 0; p < NPR; ++p) {
+            const float4 *fl = fl4 + (j * NPR + p) * STR + b0;
 #pragma unroll
-            for (int i = 0; i < S::P1; ++i) ff_madd(c[i], fl[i * st], Rs[f], Re[f]);
+            for (int i = 0; i < S::P1; ++i) {
+                const float4 x = fl[i * st];
+                ff_madd2(c[i], make_float2(x.x, x.y), make_float2(x.z, x.w), Rs[p], Re[p]);
+            }
         }
     }
 }
 
-// Lift of the face fluxes (phase 3 of the stage tile) with float32 pairs:
-// (Rs, Re) -= (2/h_j) l_a(+1)/w_a Fhat(j, +) and += (2/h_j) l_a(-1)/w_a times
-// the low face's value (the outward flux inline, G along +e_j with the face
-// pass, hence the sign), the high face first as in the float64 form.
+// Lift of the face fluxes (phase 3 of the stage tile) with float32 pairs, two
+// fields at a time: (Rs, Re) -= (2/h_j) l_a(+1)/w_a Fhat(j, +) and += (2/h_j)
+// l_a(-1)/w_a times the low face's value (the outward flux inline, G along
+// +e_j with the face pass, hence the sign), the high face first as in the
+// float64 form.  fh2 holds the face fluxes as (hi, lo) per field.
 template <class S, bool PF>
 __device__ __forceinline__ void lift_ff(const float2 *fh2, const float2 *cf2, int el, int a,
-                                        float *Rs, float *Re) {
+                                        float2 *Rs, float2 *Re) {
+    constexpr int NPR = (S::NF + 1) / 2;
 #pragma unroll
     for (int j = 0; j < S::D; ++j) {
         const int aj = digit<S::D, S::P1>(a, j);
@@ -420,9 +428,13 @@ __device__ __forceinline__ void lift_ff(const float2 *fh2, const float2 *cf2, in
         const float2 cp = ff_neg(cf2[j * Coef<S>::BLK + Coef<S>::LP + aj]);
         const float2 cmo = PF ? cm : ff_neg(cm);
 #pragma unroll
-        for (int f = 0; f < S::NF; ++f) {
-            ff_madd(cp, fp[f * S::NFP1], Rs[f], Re[f]);
-            ff_madd(cmo, fm[f * S::NFP1], Rs[f], Re[f]);
+        for (int p = 0; p < NPR; ++p) {
+            const bool two = 2 * p + 1 < S::NF;
+            const float2 p0 = fp[2 * p * S::NFP1], m0 = fm[2 * p * S::NFP1];
+            const float2 p1 = two ? fp[(2 * p + 1) * S::NFP1] : make_float2(0.0f, 0.0f);
+            const float2 m1 = two ? fm[(2 * p + 1) * S::NFP1] : make_float2(0.0f, 0.0f);
+            ff_madd2(cp, make_float2(p0.x, p1.x), make_float2(p0.y, p1.y), Rs[p], Re[p]);
+            ff_madd2(cmo, make_float2(m0.x, m1.x), make_float2(m0.y, m1.y), Rs[p], Re[p]);
         }
     }
 }
@@ -1900,9 +1912,17 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             Real F[S::NF];
             flux_dir<S, Real>(P, j, F);
             if constexpr (FFC) {
-                float2 *fl2 = reinterpret_cast<float2 *>(s_fl);
+                // (hi, hi, lo, lo) of the field pairs (2p, 2p + 1), the last
+                // padded with zeros when n_f is odd
+                constexpr int NPR = (S::NF + 1) / 2;
+                float4 *fl4 = reinterpret_cast<float4 *>(s_fl);
 #pragma unroll
-                for (int f = 0; f < S::NF; ++f) fl2[(j * S::NF + f) * STR + t] = ff_split(to_f64(F[f]));
+                for (int p = 0; p < NPR; ++p) {
+                    const float2 v0 = ff_split(to_f64(F[2 * p]));
+                    const float2 v1 =
+                        2 * p + 1 < S::NF ? ff_split(to_f64(F[2 * p + 1])) : make_float2(0.0f, 0.0f);
+                    fl4[(j * NPR + p) * STR + t] = make_float4(v0.x, v1.x, v0.y, v1.y);
+                }
             } else {
                 fl_store<S, Real, STR>(s_fl, j, t, F);
             }
@@ -1962,16 +1982,19 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
     }
 
     // ---- phase 2a: volume term, sum factorised: R_a += (2/h_j) sum_i dhat[a_j][i] F_j(i)
-    float Rs[S::NF], Re[S::NF];
+    constexpr int NPR = (S::NF + 1) / 2;
+    float2 Rs[NPR], Re[NPR];     // FFC: the tendencies of the field pairs (2p, 2p + 1)
     if constexpr (FFC) {
         if (valid) {
 #pragma unroll
-            for (int f = 0; f < S::NF; ++f) {
-                const float2 r2 = ff_split(to_f64(R[f]));
-                Rs[f] = r2.x;
-                Re[f] = r2.y;
+            for (int p = 0; p < NPR; ++p) {
+                const float2 r0 = ff_split(to_f64(R[2 * p]));
+                const float2 r1 =
+                    2 * p + 1 < S::NF ? ff_split(to_f64(R[2 * p + 1])) : make_float2(0.0f, 0.0f);
+                Rs[p] = make_float2(r0.x, r1.x);
+                Re[p] = make_float2(r0.y, r1.y);
             }
-            volume_term_ff<S, STR>(reinterpret_cast<const float2 *>(s_fl),
+            volume_term_ff<S, STR>(reinterpret_cast<const float4 *>(s_fl),
                                    reinterpret_cast<const float2 *>(s_cf), el, a, Rs, Re);
         }
     } else {
@@ -2023,7 +2046,8 @@ __device__ __forceinline__ void stage_block(const KArgs<Real> &A, const RefData<
             lift_ff<S, PF>(reinterpret_cast<const float2 *>(s_fh), reinterpret_cast<const float2 *>(s_cf),
                            el, a, Rs, Re);
 #pragma unroll
-            for (int f = 0; f < S::NF; ++f) R[f] = ff_value(Rs[f], Re[f]);
+            for (int f = 0; f < S::NF; ++f)
+                R[f] = (f & 1) ? ff_value(Rs[f >> 1].y, Re[f >> 1].y) : ff_value(Rs[f >> 1].x, Re[f >> 1].x);
         }
 #pragma unroll
         for (int j = 0; j < (FFC ? 0 : S::D); ++j) {

@@ -207,6 +207,33 @@ __device__ __forceinline__ void ff_madd(float2 c, float2 x, float &s, float &e) 
     e = __fadd_rn(e, __fadd_rn(err, q));
 }
 
+// Two lanes at once on the paired float32 instructions (fma.rn.f32x2 and
+// friends): lane by lane the same operations as ff_madd, so the same
+// results.  The coefficient c = (c.hi, c.lo) is the same in both lanes; the
+// error terms are accumulated negated (r = p - c.hi x.hi - cross terms) so
+// that every fma takes the coefficient's negation instead of a negated sum.
+__device__ __forceinline__ float2 ff_sub2(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    ra = ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
+    rb = ((unsigned long long)__float_as_uint(b.y) << 32) | __float_as_uint(b.x);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return make_float2(__uint_as_float((unsigned)rd), __uint_as_float((unsigned)(rd >> 32)));
+}
+
+__device__ __forceinline__ void ff_madd2(float2 c, float2 xh, float2 xl, float2 &s, float2 &e) {
+    const float2 ch = make_float2(c.x, c.x), nh = make_float2(-c.x, -c.x),
+                 nl = make_float2(-c.y, -c.y);
+    const float2 p = __fmul2_rn(ch, xh);
+    float2 r = __ffma2_rn(nh, xh, p);           // p - c.hi x.hi, exact
+    r = __ffma2_rn(nh, xl, r);
+    r = __ffma2_rn(nl, xh, r);
+    const float2 t = __fadd2_rn(s, p);
+    const float2 bp = ff_sub2(t, s);
+    const float2 err = __fadd2_rn(ff_sub2(s, ff_sub2(t, bp)), ff_sub2(p, bp));
+    s = t;
+    e = __fadd2_rn(e, ff_sub2(err, r));
+}
+
 // the float64 value of s + e (both exact in float64; one rounding)
 __device__ __forceinline__ double ff_value(float s, float e) { return widen(s) + widen(e); }
 
