@@ -328,7 +328,9 @@ int dg_rhs_noalloc_status(long long counts[2], void *cuda_stream);
  * max(rho_r, 1e-12 kg/m^3), which keeps the linearisation of long runs
  * bounded and leaves it exact wherever rho_r >= 1e-12.  Uses the context's
  * derived-field and trace buffers (the next dg_step re-derives them).
- * DG_ENOTIMPL for DG_FP32_BULK contexts; asynchronous. */
+ * DG_ENOTIMPL for float32 contexts (DG_FP32_BULK, DG_FP32_PERT);
+ * asynchronous.  In a DG_FP64_FFC context the adjoint kernels are the
+ * float64 ones. */
 int dg_rhs_adjoint(dg_ctx *ctx, const void *U, const double *w, double *ubar);
 
 /* Adjoint of one SSPRK(4,3) step of size dt from the state U_n (device,
@@ -337,14 +339,17 @@ int dg_rhs_adjoint(dg_ctx *ctx, const void *U, const double *w, double *ubar);
  * stages are then reversed (Remark 3.1, Shu-Osher form) with dg_rhs_adjoint.
  * lam_np1, lam_n: device float64, ABI layout, distinct.  Allocates six
  * state-sized and one trace-sized scratch buffers in the context on first
- * use.  DG_ENOTIMPL for DG_FP32_BULK contexts; asynchronous. */
+ * use.  DG_ENOTIMPL for float32 contexts (DG_FP32_BULK, DG_FP32_PERT);
+ * asynchronous.  A DG_FP64_FFC context recomputes the stage states with its
+ * own stage kernel (float-float contractions). */
 int dg_adjoint_step(dg_ctx *ctx, double dt, const void *U_n, const double *lam_np1,
                     double *lam_n);
 
 /* Cloud-water functional J(U) = integral of rho_c = rho_m - rho_v over the
  * domain (Gauss rule of the DG space; rho_v from the split Eq. (2.8)) and
  * its gradient dJ/dU (device float64, ABI layout).  J is written to a host
- * double; the call synchronises.  DG_ENOTIMPL for DG_FP32_BULK contexts. */
+ * double; the call synchronises.  DG_ENOTIMPL for float32 contexts
+ * (DG_FP32_BULK, DG_FP32_PERT). */
 int dg_cloud_functional(dg_ctx *ctx, const void *U, double *J, double *dJdU);
 
 /* ---- Stabilisation: artificial diffusion and sponge layer ----------------

@@ -393,18 +393,19 @@ def _fallout_case(case):
 
 
 @pytest.mark.parametrize("faces", FACES)
-@pytest.mark.parametrize("precision", [dm.DG_FP64, dm.DG_FP32_BULK, dm.DG_FP32_PERT])
+@pytest.mark.parametrize("precision", [dm.DG_FP64, dm.DG_FP64_FFC, dm.DG_FP32_BULK, dm.DG_FP32_PERT])
 @pytest.mark.parametrize("case", ["walls2d", "wall_y_3d"])
 def test_fallout_matches_oracle_and_closes_the_water_budget(case, precision, faces):
     """dg_reduce's fall-out (out[8]) after 10 steps against the oracle's
     (dg.run_with_fallout: the wall outflow integrated by the same stages),
     and the library's own budget: the water perturbation (out[1]) plus the
     fall-out is constant.  Float64: fall-out to 1e-11 relative, budget to
-    1e-13 of the total water; float32 forms: 1e-5 and 2e-8 (the float32
-    state rounds the water densities by 6e-8 relative at every stage)."""
+    1e-13 of the total water (DG_FP64_FFC: 1e-12, its contractions round at
+    2^-48); float32 forms: 1e-5 and 2e-8 (the float32 state rounds the water
+    densities by 6e-8 relative at every stage)."""
     from tests.test_oracle_dg import water_total
     prob, U0 = _fallout_case(case)
-    fp64 = precision == dm.DG_FP64
+    fp64 = precision in (dm.DG_FP64, dm.DG_FP64_FFC)
     if not fp64:
         U0 = U0.astype(np.float32).astype(np.float64)
     dt = dg.cfl_dt(prob, U0, 0.05)
@@ -423,7 +424,8 @@ def test_fallout_matches_oracle_and_closes_the_water_budget(case, precision, fac
         r1 = dm.dg_reduce(ctx)
         assert Fo > 1e-3 * dg.mass_integral(prob, U0[prob.i_rr])
         assert abs(r1[8] - Fo) <= (1e-11 if fp64 else 1e-5) * abs(Fo), (r1[8], Fo)
-        assert abs(r1[1] + r1[8] - r0[1]) <= (1e-13 if fp64 else 2e-8) * W0
+        budget = 1e-12 if precision == dm.DG_FP64_FFC else (1e-13 if fp64 else 2e-8)
+        assert abs(r1[1] + r1[8] - r0[1]) <= budget * W0
         # a new state starts the fall-out again
         dm.dg_set_state(ctx, host, dm.DG_HOST)
         assert dm.dg_reduce(ctx)[8] == 0.0
@@ -431,7 +433,7 @@ def test_fallout_matches_oracle_and_closes_the_water_budget(case, precision, fac
         dm.dg_free(ctx)
 
 
-@pytest.mark.parametrize("precision", [dm.DG_FP64, dm.DG_FP32_BULK, dm.DG_FP32_PERT])
+@pytest.mark.parametrize("precision", [dm.DG_FP64, dm.DG_FP64_FFC, dm.DG_FP32_BULK, dm.DG_FP32_PERT])
 @pytest.mark.parametrize("name", ["rain3d_q4_ragged", "rain2d_q1", "single_elem_3d_q3"])
 def test_host_upload_splits_in_chunks_like_dg_step(name, precision):
     """dg_set_state from host memory splits the state chunk by chunk while it
@@ -442,7 +444,7 @@ def test_host_upload_splits_in_chunks_like_dg_step(name, precision):
     copy."""
     prob, U = _setup(name)
     dt = dg.cfl_dt(prob, U, 0.05)
-    fp64 = precision == dm.DG_FP64
+    fp64 = precision in (dm.DG_FP64, dm.DG_FP64_FFC)
     host = np.ascontiguousarray(U if fp64 else U.astype(np.float32))
     outs = []
     for where in ("host", "device", "host_before_base"):
@@ -469,6 +471,7 @@ def test_host_upload_splits_in_chunks_like_dg_step(name, precision):
 
 @pytest.mark.parametrize("precision,faces", [(dm.DG_FP64, dm.DG_FACES_PASS),
                                              (dm.DG_FP64, dm.DG_FACES_INLINE),
+                                             (dm.DG_FP64_FFC, dm.DG_FACES_PASS),
                                              (dm.DG_FP32_BULK, dm.DG_FACES_PASS),
                                              (dm.DG_FP32_PERT, dm.DG_FACES_COLUMN)])
 @pytest.mark.parametrize("name", ["rain3d_q4_ragged", "single_elem_3d_q3"])
@@ -480,7 +483,7 @@ def test_step_to_host_equals_step_then_get_state(name, precision, faces, nsteps)
     from the same state."""
     prob, U = _setup(name)
     dt = dg.cfl_dt(prob, U, 0.05)
-    fp64 = precision == dm.DG_FP64
+    fp64 = precision in (dm.DG_FP64, dm.DG_FP64_FFC)
     host = np.ascontiguousarray(U if fp64 else U.astype(np.float32))
     outs = []
     for fused in (True, False):
