@@ -473,7 +473,10 @@ void dg_ensemble_free(dg_ensemble *ens);
  *                  float64 compares x > 0, x > 1.5, x < 1.5, |x| <= 1.5,
  *                  isfinite(x), max(|x|, 1.5) against those of the library's
  *                  bit-pattern compares;
- *   out[2n .. 4n)  for RHO_VS / RHO_VS_F32 / RHO_VS_BULK the derivative
+ *                  FF_SPLIT writes hi + lo of the float32 pair of
+ *                  DG_FP64_FFC (in float64) and, beside it, x itself;
+ *   out[2n .. 4n)  for FF_SPLIT the pair's hi and CUDA's float32 rounding
+ *                  of x; for RHO_VS / RHO_VS_F32 / RHO_VS_BULK the derivative
  *                  d rho_vs / dT, the library's (RHO_VS_BULK: the float32
  *                  derivative that split forms) and the closed form's; 0
  *                  otherwise.
@@ -490,6 +493,7 @@ void dg_ensemble_free(dg_ensemble *ens);
 #define DG_MATH_RHO_VS_F32 8
 #define DG_MATH_COMPARE 9
 #define DG_MATH_RHO_VS_BULK 10
+#define DG_MATH_FF_SPLIT 11
 int dg_selftest_math(dg_ctx *ctx, int fn, const double *x, double *out, long long n);
 
 /* Float64 FMA throughput probe (a measurement aid, not part of the method):

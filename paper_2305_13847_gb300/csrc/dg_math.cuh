@@ -177,22 +177,42 @@ __device__ __forceinline__ double inv_root8(double r) {
 // costs less as error-free float32 transformations (Dekker's product by fma,
 // Knuth's TwoSum) than as float64 fmas.
 //
-// ff_split(x) = (hi, lo): hi = x rounded to float32, lo = (x - hi) rounded
-// (x - hi is exact in float64), so |x - hi - lo| <= 2^-48 |x| for x in the
-// float32 exponent range (lo loses bits below ~1e-38, where no value of the
-// method's tendencies matters against its field's scale).
+// ff_split(x) = (hi, lo): hi = x rounded to float32 (as narrow), lo = x - hi
+// to 24 bits.  For x in the float32 normal range, x - hi is the float64
+// mantissa's dropped 29 bits (less 2^29 when hi rounded up) times
+// 2^(e - 1075), so lo is built from them by integer operations (leading bit,
+// shift, exponent; truncated) with no float64 subtraction.  Then
+// |x - hi - lo| <= 2^-47 |x| + 2^-126 (lo is flushed to zero below the
+// float32 normal range, which happens only for |x| below ~1e-28); other x
+// (zero, tiny, huge, not finite) take narrow(x - widen(hi)).
 // ff_madd(c, x, s, e): s + e += c x for pairs c, x.  The product c.hi x.hi is
 // split exactly by one fma, the cross terms c.hi x.lo + c.lo x.hi are added
 // to that error, c.lo x.lo (< 2^-48 |c x|) is dropped, and s + p is a TwoSum
 // whose rounding error goes to e.  The sum of n terms is then within about
-// n 2^-48 of sum |c_i x_i| (Ogita, Rump and Oishi, "Accurate sum and dot
+// n 2^-47 of sum |c_i x_i| (Ogita, Rump and Oishi, "Accurate sum and dot
 // product", SIAM J. Sci. Comput. 26 (2005), Dot2), against n 2^-53 in
 // float64.  The _rn intrinsics keep the compiler from fusing the
 // transformation's multiplies and adds into fmas, which would break it.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 ff_split(double x) {
-    const float hi = narrow(x);
-    return make_float2(hi, narrow(x - widen(hi)));
+    const unsigned hx = (unsigned)__double2hiint(x), lx = (unsigned)__double2loint(x);
+    const unsigned mag = hx & 0x7fffffffu, e = mag >> 20;
+    if (e - 897u >= 254u) {
+        const float h = narrow(x);
+        return make_float2(h, narrow(x - widen(h)));
+    }
+    const unsigned bits = ((mag - (896u << 20)) << 3) | (lx >> 29);
+    const unsigned rest = lx & 0x1fffffffu;                  // the dropped 29 bits
+    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (bits & 1u));
+    const unsigned sx = hx & 0x80000000u;
+    const float h = __uint_as_float(sx | (bits + (up ? 1u : 0u)));
+    const unsigned r = up ? 0x20000000u - rest : rest;      // |x - hi| / 2^(e - 1075)
+    const int lead = 31 - __clz((int)r);                    // -1 for r = 0
+    const int ef = lead + (int)e - 948;                     // float32 biased exponent of lo
+    if (r == 0u || ef < 1) return make_float2(h, 0.0f);
+    const unsigned m = lead >= 23 ? r >> (lead - 23) : r << (23 - lead);
+    return make_float2(h, __uint_as_float((up ? sx ^ 0x80000000u : sx) | ((unsigned)ef << 23) |
+                                          (m & 0x7fffffu)));
 }
 
 __device__ __forceinline__ void ff_madd(float2 c, float2 x, float &s, float &e) {

@@ -84,6 +84,16 @@ __global__ void k_selftest_math(int fn, const double *__restrict__ x, double *__
                 ref2 = ref * invT * ((kEsA - 1.0) + kEsB * invT);
                 break;
             }
+            case DG_MATH_FF_SPLIT: {
+                // the float32 pair of DG_FP64_FFC: hi + lo next to x, and hi
+                // next to the hardware conversion
+                const float2 p = ff_split(v);
+                ours = (double)p.x + (double)p.y;
+                ref = v;
+                ours2 = (double)p.x;
+                ref2 = (double)__double2float_rn(v);
+                break;
+            }
             default: {
                 // DG_MATH_COMPARE: the bit-pattern compares against the
                 // constant 1.5 and zero; bit k of ours / ref is compare k
@@ -108,7 +118,7 @@ __global__ void k_selftest_math(int fn, const double *__restrict__ x, double *__
 }  // namespace
 
 extern "C" int dg_selftest_math(dg_ctx *c, int fn, const double *x, double *out, long long n) {
-    if (!c || !x || !out || n < 1 || fn < DG_MATH_NARROW || fn > DG_MATH_RHO_VS_BULK) return DG_EINVAL;
+    if (!c || !x || !out || n < 1 || fn < DG_MATH_NARROW || fn > DG_MATH_FF_SPLIT) return DG_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) return DG_EINVAL;
     const long long blocks = (n + 255) / 256;

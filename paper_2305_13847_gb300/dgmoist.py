@@ -34,7 +34,7 @@ DG_HOST = 0
 DG_DEVICE = 1
 DG_NREDUCE = 9
 DG_MATH = {"narrow": 0, "widen": 1, "recip": 2, "rsqrt": 3, "sqrt": 4, "inv_root16": 5,
-           "inv_root8": 6, "rho_vs": 7, "rho_vs_f32": 8, "compare": 9, "rho_vs_bulk": 10}
+           "inv_root8": 6, "rho_vs": 7, "rho_vs_f32": 8, "compare": 9, "rho_vs_bulk": 10, "ff_split": 11}
 
 
 class DGError(RuntimeError):

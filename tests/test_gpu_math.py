@@ -259,3 +259,28 @@ def test_rho_vs_bulk_evaluation_against_the_closed_form(ctx):
     assert rel_d.max() <= 1e-6, rel_d.max()
     out = (Tt < 150.0) | (Tt > 399.0)
     assert same_bits(ours[out], ref[out]).all()
+
+
+def test_ff_split_pairs(ctx):
+    """The float32 pair (hi, lo) of DG_FP64_FFC's contractions: hi bitwise
+    CUDA's float32 rounding of x (ties, binade edges and the ends of the
+    float32 range included), and hi + lo within 2^-47 |x| + 2^-126 of x for
+    every x below the float32 maximum (lo is built from the dropped mantissa
+    bits by integer operations and truncated to 24 bits)."""
+    one = 1.0 + np.array([0.0, 2.0 ** -24, 3 * 2.0 ** -24, 2.0 ** -24 + 2.0 ** -52,
+                          2.0 ** -24 - 2.0 ** -53, 2.0 ** -23 - 2.0 ** -52])
+    x = np.concatenate([log_uniform(140, 20000, -149, 127, True), range_of_use(141, 4000),
+                        -range_of_use(142, 2000), one, -one, one * 2.0 ** 100, one * 2.0 ** -100,
+                        2.0 ** np.arange(-149, 128, 3.0),
+                        [0.0, -0.0, 2.0 ** -126, 2.0 ** -127, 1e-30, -1e-28, 3.4e38]])
+    x = np.concatenate([x, x.astype(np.float32).astype(np.float64)])
+    ours, ref, hi, hi_cuda = run(ctx, "ff_split", x)
+    assert same_bits(hi, hi_cuda).all()
+    fin = np.abs(x) <= np.float64(np.finfo(np.float32).max)
+    err = np.abs(ours[fin] - x[fin])
+    bound = 2.0 ** -47 * np.abs(x[fin]) + 2.0 ** -126
+    assert np.all(err <= bound), (err / bound).max()
+    # away from the flush threshold the pair carries 47 bits
+    big = fin & (np.abs(x) >= 1e-20)
+    rel = np.abs(ours[big] - x[big]) / np.abs(x[big])
+    assert rel.max() <= 2.0 ** -47, rel.max()
