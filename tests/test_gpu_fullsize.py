@@ -2,7 +2,8 @@
 
 The oracle builds each workload's state on the full mesh: the 3-D warm-rain
 bubble on 64x64x32 hexahedra at Q4 (float64) and on 128x128x64 at Q3 (the
-two float32 forms).  The library takes that state through its C interface.
+two float32 forms), and the float64 form with float-float contractions on
+the 64x64x32 mesh.  The library takes that state through its C interface.
 The library's face schedule is left at its default, as in the bench.
 
 * Right-hand side of the full mesh: compared with the oracle on sampled
@@ -18,8 +19,9 @@ The library's face schedule is left at its default, as in the bench.
   SSPRK(4,3) steps a column depends only on the columns within 4N elements
   (one face neighbour per stage), so the oracle follows those columns
   exactly by evaluating each stage on the target columns dilated by the
-  stages still to come.  Two steps: float64 within 1e-11 relative L2 per
-  field on the columns (momentum against the whole momentum vector), FP32-bulk
+  stages still to come.  Two steps: float64 (and its float-float
+  contraction form) within 1e-11 relative L2 per field on the columns
+  (momentum against the whole momentum vector), the two float32 forms
   within 1e-5.
 * Over steps, properties that hold at any size: dry mass is conserved, and
   so is the water plus the rain fall-out, to summation round-off; the face
@@ -39,6 +41,9 @@ from tests.gpu_helpers import (cone_elements, flux_scale, library_context, oracl
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+# forms whose state and non-linear arithmetic are float64
+FLOAT64_FORMS = (dm.DG_FP64, dm.DG_FP64_FFC)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -72,12 +77,13 @@ def _columns(mesh, w):
 
 @pytest.mark.parametrize("name,precision,tol", [
     ("rain3d_q4", dm.DG_FP64, 1e-12),
+    ("rain3d_q4", dm.DG_FP64_FFC, 1e-12),
     ("rain3d_q3_fp32", dm.DG_FP32_BULK, 2e-6),
     ("rain3d_q3_fp32", dm.DG_FP32_PERT, 2e-6),
 ])
 def test_full_size_rhs_sampled(name, precision, tol):
     w, prob, U = _problem(name)
-    dtype = torch.float64 if precision == dm.DG_FP64 else torch.float32
+    dtype = torch.float64 if precision in FLOAT64_FORMS else torch.float32
     if dtype == torch.float32:
         U = U.astype(np.float32).astype(np.float64)     # the state both sides see
     sel = _columns(prob.mesh, w)
@@ -149,11 +155,13 @@ def test_full_size_steps_conserve_dry_mass_and_schedules_agree():
 
 @pytest.mark.parametrize("name,precision,tol", [
     ("rain3d_q4", dm.DG_FP64, 1e-11),
+    ("rain3d_q4", dm.DG_FP64_FFC, 1e-11),
     ("rain3d_q3_fp32", dm.DG_FP32_BULK, 1e-5),
+    ("rain3d_q3_fp32", dm.DG_FP32_PERT, 1e-5),
 ])
 def test_full_size_steps_against_the_oracle_on_columns(name, precision, tol):
     w, prob, U = _problem(name)
-    fp64 = precision == dm.DG_FP64
+    fp64 = precision in FLOAT64_FORMS
     if not fp64:
         U = U.astype(np.float32).astype(np.float64)
     mesh = prob.mesh
